@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of the 3D Laplace FMM mat-vec on GB300.
+
+Workload: N = 4,194,304 Plummer-sphere points (scale 1, radii <= 10), equal
+charges 1/N, expansion order p = 8, mixed precision (FP32 P2P/M2L, FP64
+coarse M2M/L2L and per-target totals), leaf size 64.  One step = one pass of
+the whole hot path: root cube + Morton keys + radix sort + octree + U/V/W/X
+lists (fmm_plan_rebuild) and the mat-vec P2M/M2M/M2L/P2L/L2L/L2P/M2P/P2P +
+reduction (fmm_eval), producing potentials and gradients for all N targets.
+
+value      = N x ranks / (max over ranks of the mean device time per step)
+e2e        = the same through fmm_solve_host on pinned HOST buffers, with the
+             H2D copy of points+charges and the D2H copy of phi+grad inside
+             every timed step
+roofline   = the dominant pass, from CUDA events the library records on its
+             stream during the timed steps
+cpu_baseline = the CPU oracle (plain C, FP64, OpenMP) on a bounded sample of
+             the same distribution
+
+`--impl reference` times the oracle itself as the reference arm.
+Multi-GPU (torchrun): replicas only -- every rank solves its own problem,
+no collective on the data path.
+"""
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D Laplace FMM evals/s at N=4M at stated rel. error; fwd+adjoint vs plain FP64"
+UNIT = "evals/s"
+PASSES = ["keys+sort", "boxes", "lists", "P2M", "M2M", "M2L", "P2L", "L2L", "L2P", "M2P", "P2P",
+          "reduce"]
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4194304)
+    ap.add_argument("--order", type=int, default=8)
+    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-sample", type=int, default=131072,
+                    help="points in the oracle's CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ oracle
+def cpu_baseline(n_sample, order, leaf, gpu_phi_at=None):
+    """The CPU oracle (FP64 plan + FMM) on a bounded Plummer sample.  Also
+    returns the oracle's direct sum at `gpu_phi_at` targets of the full
+    problem (for the error statement)."""
+    import oracle
+    from paper_1602_02244_gb300 import workloads
+    xyz, q = workloads.plummer_problem(n_sample, 0)
+    t0 = time.perf_counter()
+    tree = oracle.Tree(xyz, leaf)
+    tree.eval(order, q, grad=True)
+    dt = time.perf_counter() - t0
+    out = {"value": n_sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "Plummer N=%d (same distribution, charges 1/N), p=%d, leaf %d: plan + FP64 "
+                     "FMM eval with gradients, %.1f s" % (n_sample, order, leaf, dt)}
+    ref = None
+    if gpu_phi_at is not None:
+        xyz_full, q_full, sel = gpu_phi_at
+        ref = oracle.direct(xyz_full, q_full, xyz_full[sel])
+    return out, ref
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1602_02244_gb300 import workloads
+    n = args.cpu_sample
+    xyz, q = workloads.plummer_problem(n, 0)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.Tree(xyz, args.leaf).eval(args.order, q)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.Tree(xyz, args.leaf).eval(args.order, q)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    val = n / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Plummer N=%d (bounded CPU sample of the N=4,194,304 problem), "
+                                   "p=%d, leaf %d, FP64" % (n, args.order, args.leaf)},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "Plummer N=%d per step: plan + FP64 FMM eval" % n},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours
+def algorithmic_work(plan):
+    """Per-step algorithmic work from the plan layout: P2P pairs (targets x
+    U-list sources) and M2L matvecs (|V| pairs)."""
+    e = plan.export()
+    cnt = e["box_count"].astype(np.int64)
+    u_off, u_idx = e["u_off"], e["u_idx"]
+    src_per_leaf = np.add.reduceat(cnt[u_idx], u_off[:-1]) if len(u_idx) else np.zeros(0)
+    rows = np.diff(u_off)
+    src = np.where(rows > 0, src_per_leaf, 0)
+    pairs = int(np.sum(cnt * src))
+    v_pairs = int(len(e["v_idx"]))
+    return pairs, v_pairs, e
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1602_02244_gb300 import binding, build, workloads
+    build.build()
+    L = binding.library()
+    L.fmm_kernel_launches.restype = ctypes.c_uint64
+    L.fmm_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.fmm_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int64)]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n, p, S = args.n, args.order, args.leaf
+    xyz_np, q_np = workloads.plummer_problem(n, rank)
+    X = torch.tensor(xyz_np, device=dev)
+    Q = torch.tensor(q_np, device=dev)
+    plan = binding.Plan(X, leaf_size=S, order=p, precision=args.precision)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    grad = torch.empty(n, 3, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.rebuild(X)
+        plan.eval(Q, out=(phi, grad))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    pairs, v_pairs, layout = algorithmic_work(plan)
+    sizes = plan.sizes()
+    ms_arr = (ctypes.c_double * 12)()
+    la_arr = (ctypes.c_int64 * 12)()
+    L.fmm_profile(plan._h, 1)
+    L.fmm_profile_read(plan._h, ms_arr, la_arr)  # reset
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    l0 = L.fmm_kernel_launches()
+    t_wall0 = time.perf_counter()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush (256 MB write), outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    launches = int(L.fmm_kernel_launches() - l0)
+    clk = clocks.stop()
+    L.fmm_profile_read(plan._h, ms_arr, la_arr)
+    L.fmm_profile(plan._h, 0)
+    pass_ms = {PASSES[i]: ms_arr[i] / args.steps for i in range(12)}
+    pass_launch = {PASSES[i]: la_arr[i] / args.steps for i in range(12)}
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world / (ms / 1e3)
+
+    # error statement: GPU result vs the direct sum on sampled targets
+    sel = workloads.sample_targets(n, 1024, 1)
+    phi_s = phi.cpu().numpy()[sel]
+    grad_s = grad.cpu().numpy()[sel]
+
+    # roofline of the dominant pass
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s
+    nc = (p + 1) ** 2
+    work = {"P2P": ("alu", 20.0 * pairs / 1e12, "TFLOP/s", fp32_peak),
+            "M2L": ("alu", 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s", fp32_peak)}
+    dom = max(pass_ms, key=pass_ms.get)
+    if dom in work:
+        bound, units, unit, peak = work[dom]
+        achieved = units / (pass_ms[dom] / 1e3)
+    else:
+        bound, unit, peak = "hbm", "GB/s", peaks.get("hbm_gbs", 6800.0)
+        achieved = None
+    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_source": "FP32: %d SMs x %d lanes x 2 flop x %.0f MHz" % (sms, FP32_LANES_PER_SM, max_mhz)
+            if bound == "alu" else "MEASURED_PEAKS.json hbm_gbs"}
+    other = {k: {"achieved": v[1] / (pass_ms[k] / 1e3), "unit": v[2], "frac": v[1] / (pass_ms[k] / 1e3) / v[3]}
+             for k, v in work.items() if pass_ms.get(k)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "Plummer N=%d, charges 1/N, p=%d, leaf %d, %s precision; step = "
+                                   "plan (keys, sort, octree, U/V/W/X lists) + eval (phi and grad)"
+                                   % (n, p, S, args.precision),
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "256 MB flush between steps; working set >> L2",
+                       "boxes": sizes["nboxes"], "levels": sizes["nlevels"], "U": sizes["nu"],
+                       "V": sizes["nv"], "W": sizes["nw"], "X": sizes["nx"],
+                       "p2p_pairs": pairs},
+            "clocks": clk, "gpu_launches": launches, "wall_s_timed": t_wall,
+            "pass_ms": pass_ms, "pass_launches": pass_launch, "roofline": roof,
+            "pass_roofline": other}
+
+    # plan-reused eval only (the paper's mat-vec application time)
+    L.fmm_profile(plan._h, 0)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.eval(Q, out=(phi, grad))
+    e1.record(stream)
+    e1.synchronize()
+    ms_eval = e0.elapsed_time(e1) / args.steps
+    line["eval_only"] = {"value": n / (ms_eval / 1e3), "unit": UNIT, "ms": ms_eval}
+
+    # forward + adjoint (dL/dq, dL/dx for L = sum w phi)
+    W = torch.tensor(workloads.rng(2).normal(size=n), device=dev)
+    plan.adjoint(W, Q, grad_q=grad)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.eval(Q, out=(phi, grad))
+        plan.adjoint(W, Q, grad_q=grad)
+    e1.record(stream)
+    e1.synchronize()
+    ms_fa = e0.elapsed_time(e1) / args.steps
+    line["fwd_adjoint"] = {"value": n / (ms_fa / 1e3), "unit": UNIT, "ms": ms_fa}
+
+    # end to end through the C-ABI on pinned host buffers
+    if not args.no_e2e:
+        hx = torch.tensor(xyz_np).pin_memory()
+        hq = torch.tensor(q_np).pin_memory()
+        hphi = torch.empty(n, dtype=torch.float64).pin_memory()
+        hg = torch.empty(n, 3, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            plan.solve_host_ptr(hx.data_ptr(), hq.data_ptr(), n, hphi.data_ptr(), hg.data_ptr())
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.solve_host_ptr(hx.data_ptr(), hq.data_ptr(), n, hphi.data_ptr(), hg.data_ptr())
+        t_e2e = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        line["e2e"] = {"value": n * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
+                       "d2h_bytes_per_step": 32 * n, "ms": 1e3 * t_e2e}
+
+    # plain FP64 GPU FMM on the same problem (same order), for comparison
+    if not args.no_fp64 and args.precision == "mixed":
+        plan64 = binding.Plan(X, leaf_size=S, order=p, precision="fp64")
+        phi64 = torch.empty_like(phi)
+        g64 = torch.empty_like(grad)
+        plan64.eval(Q, out=(phi64, g64))
+        barrier()
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            plan64.rebuild(X)
+            plan64.eval(Q, out=(phi64, g64))
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1) / reps
+        d64 = phi64.cpu().numpy()
+        line["fp64_same_order"] = {"value": n / (ms64 / 1e3), "unit": UNIT, "ms": ms64,
+                                   "mixed_speedup": ms64 / ms,
+                                   "mixed_vs_fp64_rel_l2": float(np.linalg.norm(phi.cpu().numpy() - d64)
+                                                                 / np.linalg.norm(d64))}
+        plan64.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, ref = cpu_baseline(args.cpu_sample, p, S, (xyz_np, q_np, sel))
+        line["cpu_baseline"] = cb
+        if ref is not None:
+            pd, gd = ref
+            line["rel_error_vs_direct"] = {
+                "phi": float(np.linalg.norm(phi_s - pd) / np.linalg.norm(pd)),
+                "grad": float(np.linalg.norm(grad_s - gd) / np.linalg.norm(gd)),
+                "targets": int(len(sel))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

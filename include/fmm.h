@@ -1,0 +1,161 @@
+/*
+ * fmm.h -- C-ABI of libfmm: the 3D Laplace (1/r) fast multipole mat-vec on
+ * one GB300 (sm_103a).
+ *
+ * Method (Yokota, Ibeid & Keyes, "Fast Multipole Method as a Matrix-Free
+ * Hierarchical Low-Rank Approximation"): the analytic FMM is a matrix-free
+ * H^2-matrix-vector product (§1, §2.4).  The paper separates the
+ * precalculation (hierarchy) from the application of the mat-vec (§4.1) and
+ * asks for a common interface between the hierarchical structure and the
+ * inner kernels (§5); this header mirrors that split:
+ *   fmm_plan_create  -- hierarchy: root cube, Morton keys (§3.1), radix sort,
+ *                       adaptive octree, interaction lists (§2.2).
+ *   fmm_eval         -- mat-vec: P2M, M2M, per-level M2L (§2.2: the dominant
+ *                       translation), P2L, L2L, L2P, M2P and the near-field
+ *                       direct sum (the dense diagonal blocks, §2.2).
+ *   fmm_adjoint      -- the transpose mat-vec and the coordinate gradient.
+ *
+ * Computed quantities (no 1/(4 pi) factor):
+ *   phi_i  = sum_{j != i} q_j / |x_i - x_j|
+ *   grad_i = grad phi(x_i) = -sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3
+ * Pairs at zero distance contribute nothing.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device;
+ *     h_* are host pointers.  The caller owns them.  Coordinates are FP64,
+ *     row-major N x 3 (x0,y0,z0,x1,...); gradients likewise.  Outputs are in
+ *     the caller's input order.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Work is stream-ordered and asynchronous unless stated otherwise.
+ *   - Every function returns an fmm_status; nothing throws across the ABI.
+ *     fmm_last_error_message() describes the last failure of this thread.
+ *   - A plan is not thread-safe; distinct plans are independent.
+ */
+#ifndef FMM_H
+#define FMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_plan_s *fmm_plan_t; /* opaque; owned by the library */
+
+typedef enum {
+  FMM_OK = 0,
+  FMM_ERR_INVALID_ARG = 1,     /* bad size, order, leaf size or NULL pointer  */
+  FMM_ERR_CUDA = 2,            /* a CUDA runtime call failed                  */
+  FMM_ERR_OOM = 3,             /* device allocation failed                    */
+  FMM_ERR_TIMEOUT = 4,         /* a bounded device-side wait gave up          */
+  FMM_ERR_NONFINITE_INPUT = 5, /* a coordinate is NaN or infinite             */
+  FMM_ERR_UNSUPPORTED = 6      /* valid request this build does not provide   */
+} fmm_status;
+
+typedef enum {
+  FMM_FP64 = 0,  /* every pass in FP64                                        */
+  FMM_MIXED = 1  /* P2M/M2L/L2P/M2P/P2L/P2P in FP32 with FP32 accumulation;
+                    M2M/L2L at the coarsest levels and the per-target
+                    reduction in FP64                                         */
+} fmm_precision;
+
+/* Options; a zero-initialised struct gives the defaults. */
+typedef struct {
+  int precision;          /* fmm_precision (default FMM_FP64)                 */
+  int coarse_fp64_levels; /* MIXED: M2M/L2L into levels <= this run in FP64;
+                             0 = default (3), negative = none                 */
+  int max_depth;          /* deepest level, 1..21; 0 = default (21)           */
+  int reserved[5];        /* must be zero                                     */
+} fmm_opts;
+
+/* Build a plan for n points (d_xyz: device, n x 3 FP64).
+ *   leaf_size : a box holding more than leaf_size points splits (>= 1);
+ *               a leaf exceeds it only at max_depth.
+ *   order     : expansion order p = largest harmonic degree, 0..20;
+ *               (p+1)^2 real coefficients per box.
+ * The plan copies what it needs from d_xyz; d_xyz may be freed afterwards.
+ * n == 0 gives a valid empty plan.  Synchronises `stream` (box counts per
+ * level are read back to size the lists).
+ * Errors: INVALID_ARG (n < 0, n >= 2^31, leaf_size < 1, order outside 0..20,
+ * bad opts, NULL out/d_xyz with n > 0), NONFINITE_INPUT, OOM, CUDA. */
+fmm_status fmm_plan_create(const double *d_xyz, int64_t n, int leaf_size, int order,
+                           const fmm_opts *opts, void *stream, fmm_plan_t *out);
+
+/* Rebuild an existing plan for new points (n may change), keeping its leaf
+ * size, order and options and reusing its device memory where it fits.
+ * Same errors and synchronisation as fmm_plan_create. */
+fmm_status fmm_plan_rebuild(fmm_plan_t plan, const double *d_xyz, int64_t n, void *stream);
+
+/* Move the points to d_xyz (same n, same input order) WITHOUT rebuilding
+ * the tree: box membership, centres and lists stay frozen.  Used to
+ * differentiate the frozen-plan FMM by finite differences.  Asynchronous. */
+fmm_status fmm_plan_set_points(fmm_plan_t plan, const double *d_xyz, void *stream);
+
+/* phi = A~ q, grad = grad phi.  d_q: n charges; d_phi: n outputs; d_grad:
+ * n x 3 or NULL (then gradients are not computed).  Asynchronous. */
+fmm_status fmm_eval(fmm_plan_t plan, const double *d_q, double *d_phi, double *d_grad,
+                    void *stream);
+
+/* Adjoint of L = sum_i w_i phi_i with respect to q and x (frozen plan):
+ *   d_dq[k]      = dL/dq_k = (A~^T w)_k = (A~ w)_k   (A~ is symmetric)
+ *   d_dx[3k+a]   = dL/dx_k = w_k grad phi^q_k + q_k grad phi^w_k.
+ * d_grad_q: the forward's gradient of phi^q (n x 3) or NULL, in which case
+ * it is recomputed (recompute instead of store).  d_dx may be NULL (then
+ * only d_dq is produced).  Asynchronous. */
+fmm_status fmm_adjoint(fmm_plan_t plan, const double *d_w, const double *d_q,
+                       const double *d_grad_q, double *d_dq, double *d_dx, void *stream);
+
+/* End-to-end call on HOST buffers: copies h_xyz (n x 3) and h_q (n) to the
+ * device, rebuilds `plan` for them, evaluates, and copies phi (n) and, if
+ * h_grad is not NULL, grad (n x 3) back.  Pinned host memory is fastest.
+ * Returns after the results are on the host. */
+fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_q, int64_t n,
+                          double *h_phi, double *h_grad, void *stream);
+
+/* Plan layout, for tests and inspection.  sizes[0..9] =
+ *   n, nboxes, nlevels, |U|, |V|, |W|, |X|, order, leaf_size, precision. */
+fmm_status fmm_plan_sizes(fmm_plan_t plan, int64_t sizes[10]);
+
+/* Copy one plan array to host memory (synchronous).  Arrays (element type,
+ * length in elements):
+ *   0 keys      (uint64, n)         sorted Morton keys
+ *   1 perm      (int32, n)          input index of the i-th sorted point
+ *   2 level_off (int32, nlevels+1)  first box of each level
+ *   3 box_key   (uint64, nboxes)    Morton key of the box's anchor at its level
+ *   4 box_level (int32, nboxes)
+ *   5 box_first (int32, nboxes)     first sorted point
+ *   6 box_count (int32, nboxes)
+ *   7 box_parent(int32, nboxes)     -1 for the root
+ *   8 box_child (int32, nboxes)     first child, -1 for a leaf
+ *   9 box_nchild(int32, nboxes)
+ *  10/11 U offsets (int32, nboxes+1) / sources (int32, |U|)
+ *  12/13 V, 14/15 W, 16/17 X likewise.
+ *  18 root cube (double, 4): lo_x, lo_y, lo_z, D.
+ * Boxes are numbered by (level, key); list sources ascend by box number.
+ * `bytes` must equal the array's size in bytes (INVALID_ARG otherwise). */
+fmm_status fmm_plan_export(fmm_plan_t plan, int which, void *h_dst, size_t bytes);
+
+/* Diagnostics: per-pass device time.  When enabled, the plan records CUDA
+ * events on its stream around each pass of fmm_plan_create/rebuild, fmm_eval
+ * and fmm_adjoint.  fmm_profile_read synchronises the plan's stream, returns
+ * the milliseconds and kernel launches accumulated per pass since the last
+ * read, and resets them.  Pass order: 0 keys+sort, 1 boxes, 2 lists,
+ * 3 P2M, 4 M2M, 5 M2L, 6 P2L, 7 L2L, 8 L2P, 9 M2P, 10 P2P, 11 reduce. */
+#define FMM_NPASS 12
+fmm_status fmm_profile(fmm_plan_t plan, int enable);
+fmm_status fmm_profile_read(fmm_plan_t plan, double ms[FMM_NPASS], int64_t launches[FMM_NPASS]);
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t fmm_kernel_launches(void);
+
+/* Release the plan and all its device memory (synchronises its stream). */
+fmm_status fmm_plan_destroy(fmm_plan_t plan);
+
+const char *fmm_status_string(fmm_status s);
+const char *fmm_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_H */

@@ -1,0 +1,196 @@
+// eval.cu -- the FMM mat-vec pass sequence on one stream (§1: matrix-free
+// H^2 mat-vec; §2.2 translation operators and near field):
+//   permute charges -> P2M -> M2M (deepest parents first) -> M2L over all
+//   levels >= 2 -> P2L -> L2L (top-down) -> L2P -> M2P -> P2P -> FP64
+//   per-target reduction and scatter to the caller's order.
+// FP64 mode runs every pass in FP64.  Mixed mode runs P2M/M2L/P2L/L2P/M2P/P2P
+// in FP32 and keeps FP64 only for M2M/L2L into the coarsest levels
+// (<= coarse_fp64_levels) and for the per-target totals.
+#include "eval_kernels.cuh"
+
+namespace fmm {
+
+namespace {
+
+void ensure_workspace(fmm_plan_impl &P, bool need64, bool need32) {
+  const size_t nc = (size_t)ncoef(P.order);
+  const size_t nb = (size_t)P.nboxes;
+  cudaStream_t s = P.stream;
+  P.far_acc.resize(4 * (size_t)P.n, s);
+  P.near_acc.resize(4 * (size_t)P.n, s);
+  if (need64) {
+    P.M64.resize(nb * nc, s);
+    P.L64.resize(nb * nc, s);
+  }
+  if (need32) {
+    P.M32.resize(nb * nc, s);
+    P.L32.resize(nb * nc, s);
+  }
+}
+
+void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad) {
+  const int p = P.order;
+  const int64_t n = P.n;
+  cudaStream_t s = P.stream;
+  ensure_workspace(P, true, false);
+  P.src64.resize(n, s);
+  {
+    PassScope ps_(P, kPassP2M);
+    launch_permute_charges<double>(n, P.perm.p, d_q, P.pl64.p, P.src64.p, s);
+    launch_p2m<double>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p,
+                       P.src64.p, P.D, P.M64.p, nullptr, -1, s);
+  }
+  for (int l = P.nlevels - 2; l >= 2; --l) {
+    PassScope ps_(P, kPassM2M);
+    launch_m2m<double, double, double, double>(p, P.level_off[l], P.level_off[l + 1] - P.level_off[l],
+                                               P.box_child.p, P.box_nchild.p, P.box_geo.p, P.M64.p,
+                                               P.ops.m2m64.p, P.M64.p, nullptr, s);
+  }
+  {
+    PassScope ps_(P, kPassM2L);
+    launch_m2l<double>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_order.p, P.v_off.p,
+                       P.v_idx.p, P.box_geo.p, P.M64.p, P.ops.m2l64.p, P.L64.p, s);
+  }
+  {
+    PassScope ps_(P, kPassP2L);
+    launch_p2l<double>(p, P.nxboxes, P.xboxes.p, P.x_off.p, P.x_idx.p, P.box_first.p, P.box_count.p,
+                       P.box_geo.p, P.src64.p, P.D, P.L64.p, s);
+  }
+  for (int l = 3; l < P.nlevels; ++l) {
+    PassScope ps_(P, kPassL2L);
+    launch_l2l<double, double, double, double, double>(
+        p, P.level_off[l], P.level_off[l + 1] - P.level_off[l], P.box_parent.p, P.box_geo.p, P.L64.p,
+        P.L64.p, P.ops.l2l64.p, P.L64.p, nullptr, s);
+  }
+  {
+    PassScope ps_(P, kPassL2P);
+    launch_l2p<double>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src64.p,
+                       P.D, P.L64.p, n, P.far_acc.p, s);
+  }
+  {
+    PassScope ps_(P, kPassM2P);
+    launch_m2p<double>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.box_first.p, P.box_count.p,
+                       P.box_geo.p, P.src64.p, P.D, P.M64.p, n, P.far_acc.p, s);
+  }
+  {
+    PassScope ps_(P, kPassP2P);
+    launch_p2p<double>(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
+                       P.box_geo.p, P.src64.p, P.D, n, P.near_acc.p, s);
+  }
+  {
+    PassScope ps_(P, kPassReduce);
+    launch_combine(n, P.perm.p, P.far_acc.p, P.near_acc.p, d_phi, d_grad, s);
+  }
+}
+
+void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad) {
+  const int p = P.order;
+  const int64_t n = P.n;
+  cudaStream_t s = P.stream;
+  const int lc = P.coarse_fp64_levels;  // M2M/L2L into levels <= lc in FP64
+  const bool coarse = lc >= 2;
+  ensure_workspace(P, coarse, true);
+  P.src32.resize(n, s);
+  {
+    PassScope ps_(P, kPassP2M);
+    launch_permute_charges<float>(n, P.perm.p, d_q, P.pl32.p, P.src32.p, s);
+    launch_p2m<float>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p,
+                      P.D, P.M32.p, coarse ? P.M64.p : nullptr, lc, s);
+  }
+  for (int l = P.nlevels - 2; l >= 2; --l) {
+    const int32_t b0 = P.level_off[l], nbl = P.level_off[l + 1] - b0;
+    PassScope ps_(P, kPassM2M);
+    if (l <= lc) {
+      if (l + 1 <= lc)
+        launch_m2m<double, double, double, double>(p, b0, nbl, P.box_child.p, P.box_nchild.p,
+                                                   P.box_geo.p, P.M64.p, P.ops.m2m64.p, P.M64.p,
+                                                   P.M32.p, s);
+      else
+        launch_m2m<float, double, double, double>(p, b0, nbl, P.box_child.p, P.box_nchild.p,
+                                                  P.box_geo.p, P.M32.p, P.ops.m2m64.p, P.M64.p,
+                                                  P.M32.p, s);
+    } else {
+      launch_m2m<float, float, float, float>(p, b0, nbl, P.box_child.p, P.box_nchild.p, P.box_geo.p,
+                                             P.M32.p, P.ops.m2m32.p, P.M32.p, nullptr, s);
+    }
+  }
+  {
+    PassScope ps_(P, kPassM2L);
+    launch_m2l<float>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_order.p, P.v_off.p,
+                      P.v_idx.p, P.box_geo.p, P.M32.p, P.ops.m2l32.p, P.L32.p, s);
+  }
+  {
+    PassScope ps_(P, kPassP2L);
+    launch_p2l<float>(p, P.nxboxes, P.xboxes.p, P.x_off.p, P.x_idx.p, P.box_first.p, P.box_count.p,
+                      P.box_geo.p, P.src32.p, P.D, P.L32.p, s);
+  }
+  const size_t nc = (size_t)ncoef(p);
+  if (coarse && P.nlevels > 2) {
+    const size_t b0 = (size_t)P.level_off[2], b1 = (size_t)P.level_off[3];
+    PassScope ps_(P, kPassL2L);
+    launch_to_f64<float>((int64_t)((b1 - b0) * nc), P.L32.p + b0 * nc, P.L64.p + b0 * nc, s);
+  }
+  for (int l = 3; l < P.nlevels; ++l) {
+    const int32_t b0 = P.level_off[l], nbl = P.level_off[l + 1] - b0;
+    PassScope ps_(P, kPassL2L);
+    if (l <= lc)
+      launch_l2l<float, double, double, double, double>(p, b0, nbl, P.box_parent.p, P.box_geo.p,
+                                                        P.L32.p, P.L64.p, P.ops.l2l64.p, P.L64.p,
+                                                        P.L32.p, s);
+    else
+      launch_l2l<float, float, float, float, float>(p, b0, nbl, P.box_parent.p, P.box_geo.p, P.L32.p,
+                                                    P.L32.p, P.ops.l2l32.p, P.L32.p, nullptr, s);
+  }
+  {
+    PassScope ps_(P, kPassL2P);
+    launch_l2p<float>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p,
+                      P.D, P.L32.p, n, P.far_acc.p, s);
+  }
+  {
+    PassScope ps_(P, kPassM2P);
+    launch_m2p<float>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.box_first.p, P.box_count.p,
+                      P.box_geo.p, P.src32.p, P.D, P.M32.p, n, P.far_acc.p, s);
+  }
+  {
+    PassScope ps_(P, kPassP2P);
+    launch_p2p<float>(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
+                      P.box_geo.p, P.src32.p, P.D, n, P.near_acc.p, s);
+  }
+  {
+    PassScope ps_(P, kPassReduce);
+    launch_combine(n, P.perm.p, P.far_acc.p, P.near_acc.p, d_phi, d_grad, s);
+  }
+}
+
+}  // namespace
+
+void eval_fmm(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad) {
+  if (P.n == 0) return;
+  build_operators(P);
+  if (P.precision == FMM_FP64) eval_fp64(P, d_q, d_phi, d_grad);
+  else eval_mixed(P, d_q, d_phi, d_grad);
+}
+
+void adjoint_fmm(fmm_plan_impl &P, const double *d_w, const double *d_q, const double *d_grad_q,
+                 double *d_dq, double *d_dx) {
+  const int64_t n = P.n;
+  if (n == 0) return;
+  cudaStream_t s = P.stream;
+  P.adj_grad_w.resize(3 * (size_t)n, s);
+  // dL/dq = A~^T w = A~ w (the truncated operator is symmetric)
+  eval_fmm(P, d_w, d_dq, d_dx ? P.adj_grad_w.p : nullptr);
+  if (!d_dx) return;
+  const double *gq = d_grad_q;
+  if (!gq) {  // recompute instead of store
+    P.adj_grad_q.resize(3 * (size_t)n, s);
+    P.adj_phi.resize((size_t)n, s);
+    eval_fmm(P, d_q, P.adj_phi.p, P.adj_grad_q.p);
+    gq = P.adj_grad_q.p;
+  }
+  {
+    PassScope ps_(P, kPassReduce);
+    launch_adjoint_dx(n, d_w, d_q, gq, P.adj_grad_w.p, d_dx, s);
+  }
+}
+
+}  // namespace fmm

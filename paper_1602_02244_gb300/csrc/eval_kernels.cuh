@@ -1,0 +1,65 @@
+// eval_kernels.cuh -- launchers of the evaluation passes.
+#pragma once
+#include "plan.cuh"
+
+namespace fmm {
+
+template <typename T>
+struct V4;
+template <>
+struct V4<double> {
+  using type = double4;
+};
+template <>
+struct V4<float> {
+  using type = float4;
+};
+
+template <typename T>
+void launch_permute_charges(int64_t n, const int32_t *perm, const double *q,
+                            const typename V4<T>::type *pl, typename V4<T>::type *src, cudaStream_t s);
+template <typename T>
+void launch_p2m(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                T *M, double *M64, int coarse, cudaStream_t s);
+template <typename T>
+void launch_p2l(int p, int64_t nx, const int32_t *xboxes, const int32_t *xoff, const int32_t *xidx,
+                const int32_t *first, const int32_t *count, const BoxGeo *geo,
+                const typename V4<T>::type *src, double D, T *L, cudaStream_t s);
+template <typename Tin, typename Tout, typename Top, typename Tacc>
+void launch_m2m(int p, int32_t b0, int32_t nbl, const int32_t *child, const int32_t *nchild,
+                const BoxGeo *geo, const Tin *Mc, const Top *ops, Tout *Mp, float *Mp32,
+                cudaStream_t s);
+template <typename Tself, typename Tpar, typename Tout, typename Top, typename Tacc>
+void launch_l2l(int p, int32_t b0, int32_t nbl, const int32_t *parent, const BoxGeo *geo,
+                const Tself *Lself, const Tpar *Lpar, const Top *ops, Tout *Lout, float *Lout32,
+                cudaStream_t s);
+template <typename Tin>
+void launch_to_f64(int64_t count, const Tin *in, double *out, cudaStream_t s);
+template <typename T>
+void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const T *L, int64_t n, double *far, cudaStream_t s);
+template <typename T>
+void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, const int32_t *widx,
+                const int32_t *first, const int32_t *count, const BoxGeo *geo,
+                const typename V4<T>::type *src, double D, const T *M, int64_t n, double *far,
+                cudaStream_t s);
+void launch_combine(int64_t n, const int32_t *perm, const double *far, const double *near,
+                    double *phi, double *grad, cudaStream_t s);
+void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double *gq,
+                       const double *gw, double *dx, cudaStream_t s);
+
+// m2l.cu
+template <typename T>
+void launch_m2l(int p, int64_t ntiles, const M2LTile *tiles, int tile, const int32_t *order,
+                const int32_t *voff, const int32_t *vidx, const BoxGeo *geo, const T *M,
+                const T *ops, T *L, cudaStream_t s);
+
+// p2p.cu
+template <typename T>
+void launch_p2p(int64_t nleaves, const int32_t *leaves, const int32_t *uoff, const int32_t *uidx,
+                const int32_t *first, const int32_t *count, const BoxGeo *geo,
+                const typename V4<T>::type *src, double D, int64_t n, double *near, cudaStream_t s);
+
+}  // namespace fmm

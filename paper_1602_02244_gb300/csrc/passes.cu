@@ -1,0 +1,516 @@
+// passes.cu -- the upward and downward passes of the FMM mat-vec (§1: the
+// analytic FMM as a matrix-free H^2 mat-vec; translation operators of §2.2):
+// P2M at leaves, M2M child -> parent, P2L over X lists, L2L parent -> child,
+// L2P at leaf targets, M2P over W lists, and the per-target reduction.
+//
+// Coefficients are scale-free and stored in the real basis described in
+// operators.cu.  Point data are leaf-local: (x - c_leaf, y - c_leaf,
+// z - c_leaf, q); box-to-box centre offsets come exactly from integer anchors.
+#include "eval_kernels.cuh"
+#include "harmonics.cuh"
+
+namespace fmm {
+
+namespace {
+
+__device__ __forceinline__ double center_delta(int32_t ia, int la, int32_t ib, int lb, double D) {
+  // (c_A - c_B) along one axis, exact: both centres are dyadic multiples of D
+  return ((double)ia + 0.5) * box_side(D, la) - ((double)ib + 0.5) * box_side(D, lb);
+}
+
+constexpr int kAccSlots = 14;  // ceil(441 / 32): coefficients per lane for p <= 20
+
+template <typename T>
+__global__ void k_permute_charges(int64_t n, const int32_t *__restrict__ perm,
+                                  const double *__restrict__ q, const typename V4<T>::type *pl,
+                                  typename V4<T>::type *__restrict__ src) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  typename V4<T>::type v = pl[i];
+  v.w = (T)q[perm[i]];
+  src[i] = v;
+}
+
+// P2M: M^_n^m = sum_j q_j conj(R_n^m((x_j - c)/a)); one warp per leaf, lanes
+// over points, a warp-private shared buffer transposes per-point harmonics
+// into per-coefficient sums.
+template <typename T>
+__global__ void k_p2m(int p, int64_t nleaves, const int32_t *__restrict__ leaves,
+                      const int32_t *__restrict__ first, const int32_t *__restrict__ count,
+                      const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
+                      double D, T *__restrict__ M, double *__restrict__ M64, int coarse) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nc = ncoef(p), pitch = 33, lane = threadIdx.x & 31;
+  T *buf = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * nc * pitch;
+  int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= nleaves) return;
+  const int32_t b = leaves[w];
+  const BoxGeo g = geo[b];
+  const T inva = (T)(1.0 / box_side(D, g.level));
+  T acc[kAccSlots];
+#pragma unroll
+  for (int t = 0; t < kAccSlots; ++t) acc[t] = T(0);
+  const int32_t f = first[b], c = count[b];
+  for (int32_t j0 = 0; j0 < c; j0 += 32) {
+    const int32_t j = j0 + lane;
+    if (j < c) {
+      const typename V4<T>::type s = src[f + j];
+      const T q = s.w;
+      regular_stream<T>(p, s.x * inva, s.y * inva, s.z * inva, [&](int n, int m, T re, T im) {
+        buf[cidx(n, m) * pitch + lane] = q * re;
+        if (m > 0) buf[cidx(n, -m) * pitch + lane] = -q * im;
+      });
+    } else {
+      for (int k = 0; k < nc; ++k) buf[k * pitch + lane] = T(0);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kAccSlots; ++t) {
+      const int k = lane + 32 * t;
+      if (k < nc) {
+        T s = T(0);
+        for (int jj = 0; jj < 32; ++jj) s += buf[k * pitch + jj];
+        acc[t] += s;
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int t = 0; t < kAccSlots; ++t) {
+    const int k = lane + 32 * t;
+    if (k < nc) {
+      M[(int64_t)b * nc + k] = acc[t];
+      if (M64 && g.level <= coarse) M64[(int64_t)b * nc + k] = (double)acc[t];
+    }
+  }
+}
+
+// P2L over X lists: L^_n^m(C) += sum_{A in X(C)} sum_{j in A} q_j conj(I_n^m((x_j - c_C)/a_C))
+template <typename T>
+__global__ void k_p2l(int p, int64_t nboxes_x, const int32_t *__restrict__ xboxes,
+                      const int32_t *__restrict__ xoff, const int32_t *__restrict__ xidx,
+                      const int32_t *__restrict__ first, const int32_t *__restrict__ count,
+                      const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
+                      double D, T *__restrict__ L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nc = ncoef(p), pitch = 33, lane = threadIdx.x & 31;
+  T *buf = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * nc * pitch;
+  int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= nboxes_x) return;
+  const int32_t C = xboxes[w];
+  const BoxGeo gc = geo[C];
+  const double ac = box_side(D, gc.level);
+  const T inva = (T)(1.0 / ac);
+  T acc[kAccSlots];
+#pragma unroll
+  for (int t = 0; t < kAccSlots; ++t) acc[t] = T(0);
+  for (int32_t e = xoff[C]; e < xoff[C + 1]; ++e) {
+    const int32_t A = xidx[e];
+    const BoxGeo ga = geo[A];
+    const T sx = (T)center_delta(ga.ix, ga.level, gc.ix, gc.level, D);
+    const T sy = (T)center_delta(ga.iy, ga.level, gc.iy, gc.level, D);
+    const T sz = (T)center_delta(ga.iz, ga.level, gc.iz, gc.level, D);
+    const int32_t f = first[A], c = count[A];
+    for (int32_t j0 = 0; j0 < c; j0 += 32) {
+      const int32_t j = j0 + lane;
+      if (j < c) {
+        const typename V4<T>::type s = src[f + j];
+        const T q = s.w;
+        irregular_stream<T>(p, (s.x + sx) * inva, (s.y + sy) * inva, (s.z + sz) * inva,
+                            [&](int n, int m, T re, T im) {
+                              buf[cidx(n, m) * pitch + lane] = q * re;
+                              if (m > 0) buf[cidx(n, -m) * pitch + lane] = -q * im;
+                            });
+      } else {
+        for (int k = 0; k < nc; ++k) buf[k * pitch + lane] = T(0);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kAccSlots; ++t) {
+        const int k = lane + 32 * t;
+        if (k < nc) {
+          T s = T(0);
+          for (int jj = 0; jj < 32; ++jj) s += buf[k * pitch + jj];
+          acc[t] += s;
+        }
+      }
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kAccSlots; ++t) {
+    const int k = lane + 32 * t;
+    if (k < nc) L[(int64_t)C * nc + k] += acc[t];
+  }
+}
+
+__device__ __forceinline__ int degree_of(int r) {
+  int n = (int)sqrtf((float)r);
+  while (n * n > r) --n;
+  while ((n + 1) * (n + 1) <= r) ++n;
+  return n;
+}
+
+__device__ __forceinline__ int octant(const BoxGeo &g) {
+  return (g.ix & 1) | ((g.iy & 1) << 1) | ((g.iz & 1) << 2);
+}
+
+// M2M into the parents of one level: thread per (parent, output coefficient);
+// output degree n uses inputs of degree <= n only.
+template <typename Tin, typename Tout, typename Top, typename Tacc>
+__global__ void k_m2m(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ child,
+                      const int32_t *__restrict__ nchild, const BoxGeo *__restrict__ geo,
+                      const Tin *__restrict__ Mc, const Top *__restrict__ ops, Tout *__restrict__ Mp,
+                      float *__restrict__ Mp32) {
+  const int nc = ncoef(p);
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nbl * nc) return;
+  const int32_t b = b0 + (int32_t)(t / nc);
+  const int r = (int)(t % nc);
+  const int nch = nchild[b];
+  if (nch == 0) return;
+  const int kmax = ncoef(degree_of(r));
+  Tacc acc = Tacc(0);
+  const int32_t c0 = child[b];
+  for (int32_t cc = c0; cc < c0 + nch; ++cc) {
+    const Top *row = ops + ((size_t)octant(geo[cc]) * nc + r) * nc;
+    const Tin *m = Mc + (int64_t)cc * nc;
+    for (int k = 0; k < kmax; ++k) acc += (Tacc)row[k] * (Tacc)m[k];
+  }
+  Mp[(int64_t)b * nc + r] = (Tout)acc;
+  if (Mp32) Mp32[(int64_t)b * nc + r] = (float)acc;
+}
+
+// L2L into the boxes of one level: L(child) = L_self(child) + T(octant) L(parent);
+// output degree n uses inputs of degree >= n only.
+template <typename Tself, typename Tpar, typename Tout, typename Top, typename Tacc>
+__global__ void k_l2l(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ parent,
+                      const BoxGeo *__restrict__ geo, const Tself *Lself, const Tpar *Lpar,
+                      const Top *__restrict__ ops, Tout *Lout, float *Lout32) {
+  const int nc = ncoef(p);
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nbl * nc) return;
+  const int32_t b = b0 + (int32_t)(t / nc);
+  const int r = (int)(t % nc);
+  const int32_t P = parent[b];
+  const int n = degree_of(r);
+  const Top *row = ops + ((size_t)octant(geo[b]) * nc + r) * nc;
+  const Tpar *lp = Lpar + (int64_t)P * nc;
+  Tacc acc = (Tacc)Lself[(int64_t)b * nc + r];
+  for (int k = n * n; k < nc; ++k) acc += (Tacc)row[k] * (Tacc)lp[k];
+  Lout[(int64_t)b * nc + r] = (Tout)acc;
+  if (Lout32) Lout32[(int64_t)b * nc + r] = (float)acc;
+}
+
+template <typename Tin>
+__global__ void k_to_f64(int64_t count, const Tin *__restrict__ in, double *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = (double)in[i];
+}
+
+// L2P: phi = (1/a) sum L^ R(u), grad = (1/a^2) sum L^ grad_u R(u), u = (x - c)/a.
+// With X_n^{-m} = (-1)^m conj(X_n^m) every sum over m is Re(m=0) + 2 Re(m>0);
+// the gradient uses d/dz R_n^m = R_{n-1}^m, d/dx R_n^m = (R_{n-1}^{m+1} - R_{n-1}^{m-1})/2,
+// d/dy R_n^m = -i (R_{n-1}^{m-1} + R_{n-1}^{m+1})/2, regrouped per R_n^m.
+template <typename T>
+__global__ void k_l2p(int p, const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
+                      const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
+                      const typename V4<T>::type *__restrict__ src, double D,
+                      const T *__restrict__ L, int64_t n, double *__restrict__ far) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Ls = reinterpret_cast<T *>(smem_raw);
+  const int nc = ncoef(p);
+  const int32_t b = leaves[blockIdx.x];
+  const BoxGeo g = geo[b];
+  const int32_t f = first[b], c = count[b];
+  if (g.level < 2) {  // no far field reaches levels 0 and 1
+    for (int32_t i = f + threadIdx.x; i < f + c; i += blockDim.x)
+      for (int a = 0; a < 4; ++a) far[a * n + i] = 0.0;
+    return;
+  }
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) Ls[k] = L[(int64_t)b * nc + k];
+  __syncthreads();
+  const double a = box_side(D, g.level);
+  const T inva = (T)(1.0 / a);
+  for (int32_t i = f + threadIdx.x; i < f + c; i += blockDim.x) {
+    const typename V4<T>::type s = src[i];
+    T phi = 0, gx = 0, gy = 0, gz = 0;
+    regular_stream<T>(p, s.x * inva, s.y * inva, s.z * inva, [&](int nn, int m, T re, T im) {
+      const T w = m ? T(2) : T(1);
+      T ar, ai;
+      cget(Ls, p, nn, m, ar, ai);
+      phi += w * (ar * re - ai * im);
+      if (nn < p) {
+        T br, bi, cr, ci;
+        cget(Ls, p, nn + 1, m, ar, ai);
+        gz += w * (ar * re - ai * im);
+        cget(Ls, p, nn + 1, m - 1, br, bi);
+        cget(Ls, p, nn + 1, m + 1, cr, ci);
+        const T gr = T(0.5) * (br - cr), gi = T(0.5) * (bi - ci);
+        gx += w * (gr * re - gi * im);
+        const T hr = T(0.5) * (bi + ci), hi = T(-0.5) * (br + cr);
+        gy += w * (hr * re - hi * im);
+      }
+    });
+    const double ia = 1.0 / a;
+    far[i] = (double)phi * ia;
+    far[n + i] = (double)gx * ia * ia;
+    far[2 * n + i] = (double)gy * ia * ia;
+    far[3 * n + i] = (double)gz * ia * ia;
+  }
+}
+
+// M2P over W lists: phi += (1/a_A) sum M^ I(u), u = (x - c_A)/a_A, gradient from
+// d/dz I_n^m = -I_{n+1}^m, d/dx I_n^m = (I_{n+1}^{m+1} - I_{n+1}^{m-1})/2,
+// d/dy I_n^m = -i (I_{n+1}^{m+1} + I_{n+1}^{m-1})/2, regrouped per I_n^m.
+template <typename T>
+__global__ void k_m2p(int p, const int32_t *__restrict__ wleaves, const int32_t *__restrict__ woff,
+                      const int32_t *__restrict__ widx, const int32_t *__restrict__ first,
+                      const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
+                      const typename V4<T>::type *__restrict__ src, double D,
+                      const T *__restrict__ M, int64_t n, double *__restrict__ far) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Ms = reinterpret_cast<T *>(smem_raw);
+  const int nc = ncoef(p);
+  const int32_t B = wleaves[blockIdx.x];
+  const BoxGeo gb = geo[B];
+  const int32_t f = first[B], c = count[B];
+  for (int32_t i0 = 0; i0 < c; i0 += blockDim.x) {
+    const int32_t i = f + i0 + threadIdx.x;
+    const bool act = i0 + (int32_t)threadIdx.x < c;
+    typename V4<T>::type s;
+    if (act) s = src[i];
+    double phi = 0, gx = 0, gy = 0, gz = 0;
+    for (int32_t e = woff[B]; e < woff[B + 1]; ++e) {
+      const int32_t A = widx[e];
+      __syncthreads();
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) Ms[k] = M[(int64_t)A * nc + k];
+      __syncthreads();
+      if (!act) continue;
+      const BoxGeo ga = geo[A];
+      const double aa = box_side(D, ga.level);
+      const T inva = (T)(1.0 / aa);
+      const T sx = (T)center_delta(gb.ix, gb.level, ga.ix, ga.level, D);
+      const T sy = (T)center_delta(gb.iy, gb.level, ga.iy, ga.level, D);
+      const T sz = (T)center_delta(gb.iz, gb.level, ga.iz, ga.level, D);
+      T fp = 0, fx = 0, fy = 0, fz = 0;
+      irregular_stream<T>(p + 1, (s.x + sx) * inva, (s.y + sy) * inva, (s.z + sz) * inva,
+                          [&](int nn, int m, T re, T im) {
+                            const T w = m ? T(2) : T(1);
+                            T ar, ai, br, bi, cr, ci;
+                            if (nn <= p) {
+                              cget(Ms, p, nn, m, ar, ai);
+                              fp += w * (ar * re - ai * im);
+                            }
+                            if (nn >= 1) {
+                              cget(Ms, p, nn - 1, m, ar, ai);
+                              fz -= w * (ar * re - ai * im);
+                              cget(Ms, p, nn - 1, m - 1, br, bi);
+                              cget(Ms, p, nn - 1, m + 1, cr, ci);
+                              const T gr = T(0.5) * (br - cr), gi = T(0.5) * (bi - ci);
+                              fx += w * (gr * re - gi * im);
+                              const T hr = T(0.5) * (bi + ci), hi = T(-0.5) * (br + cr);
+                              fy += w * (hr * re - hi * im);
+                            }
+                          });
+      const double ia = 1.0 / aa;
+      phi += (double)fp * ia;
+      gx += (double)fx * ia * ia;
+      gy += (double)fy * ia * ia;
+      gz += (double)fz * ia * ia;
+    }
+    if (act) {
+      far[i] += phi;
+      far[n + i] += gx;
+      far[2 * n + i] += gy;
+      far[3 * n + i] += gz;
+    }
+  }
+}
+
+// final per-target reduction in FP64 and scatter to the caller's order
+__global__ void k_combine(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ far,
+                          const double *__restrict__ near, double *__restrict__ phi,
+                          double *__restrict__ grad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t o = perm[i];
+  phi[o] = far[i] + near[i];
+  if (grad) {
+    grad[3 * o] = far[n + i] + near[n + i];
+    grad[3 * o + 1] = far[2 * n + i] + near[2 * n + i];
+    grad[3 * o + 2] = far[3 * n + i] + near[3 * n + i];
+  }
+}
+
+__global__ void k_adjoint_dx(int64_t n, const double *__restrict__ w, const double *__restrict__ q,
+                             const double *__restrict__ gq, const double *__restrict__ gw,
+                             double *__restrict__ dx) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n) return;
+  const int64_t k = i / 3;
+  dx[i] = w[k] * gq[i] + q[k] * gw[i];
+}
+
+int warps_for(size_t per_warp) {
+  int w = (int)std::min<size_t>(4, (96 * 1024) / std::max<size_t>(per_warp, 1));
+  return w < 1 ? 1 : w;
+}
+
+template <typename K>
+void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    FMM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+template <typename T>
+void launch_permute_charges(int64_t n, const int32_t *perm, const double *q,
+                            const typename V4<T>::type *pl, typename V4<T>::type *src, cudaStream_t s) {
+  if (n == 0) return;
+  k_permute_charges<T><<<ceil_div(n, 256), 256, 0, s>>>(n, perm, q, pl, src);
+  FMM_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_p2m(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                T *M, double *M64, int coarse, cudaStream_t s) {
+  if (nleaves == 0) return;
+  size_t per = (size_t)ncoef(p) * 33 * sizeof(T);
+  int w = warps_for(per);
+  allow_smem(k_p2m<T>, per * w);
+  k_p2m<T><<<ceil_div(nleaves, w), 32 * w, per * w, s>>>(p, nleaves, leaves, first, count, geo, src,
+                                                          D, M, M64, coarse);
+  FMM_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_p2l(int p, int64_t nx, const int32_t *xboxes, const int32_t *xoff, const int32_t *xidx,
+                const int32_t *first, const int32_t *count, const BoxGeo *geo,
+                const typename V4<T>::type *src, double D, T *L, cudaStream_t s) {
+  if (nx == 0) return;
+  size_t per = (size_t)ncoef(p) * 33 * sizeof(T);
+  int w = warps_for(per);
+  allow_smem(k_p2l<T>, per * w);
+  k_p2l<T><<<ceil_div(nx, w), 32 * w, per * w, s>>>(p, nx, xboxes, xoff, xidx, first, count, geo,
+                                                     src, D, L);
+  FMM_LAUNCH_CHECK();
+}
+
+template <typename Tin, typename Tout, typename Top, typename Tacc>
+void launch_m2m(int p, int32_t b0, int32_t nbl, const int32_t *child, const int32_t *nchild,
+                const BoxGeo *geo, const Tin *Mc, const Top *ops, Tout *Mp, float *Mp32,
+                cudaStream_t s) {
+  if (nbl == 0) return;
+  int64_t tot = (int64_t)nbl * ncoef(p);
+  k_m2m<Tin, Tout, Top, Tacc><<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, child, nchild, geo, Mc,
+                                                                 ops, Mp, Mp32);
+  FMM_LAUNCH_CHECK();
+}
+
+template <typename Tself, typename Tpar, typename Tout, typename Top, typename Tacc>
+void launch_l2l(int p, int32_t b0, int32_t nbl, const int32_t *parent, const BoxGeo *geo,
+                const Tself *Lself, const Tpar *Lpar, const Top *ops, Tout *Lout, float *Lout32,
+                cudaStream_t s) {
+  if (nbl == 0) return;
+  int64_t tot = (int64_t)nbl * ncoef(p);
+  k_l2l<Tself, Tpar, Tout, Top, Tacc><<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, parent, geo,
+                                                                         Lself, Lpar, ops, Lout,
+                                                                         Lout32);
+  FMM_LAUNCH_CHECK();
+}
+
+template <typename Tin>
+void launch_to_f64(int64_t count, const Tin *in, double *out, cudaStream_t s) {
+  if (count == 0) return;
+  k_to_f64<Tin><<<ceil_div(count, 256), 256, 0, s>>>(count, in, out);
+  FMM_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const T *L, int64_t n, double *far, cudaStream_t s) {
+  if (nleaves == 0) return;
+  size_t sm = (size_t)ncoef(p) * sizeof(T);
+  k_l2p<T><<<(unsigned)nleaves, 64, sm, s>>>(p, leaves, first, count, geo, src, D, L, n, far);
+  FMM_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, const int32_t *widx,
+                const int32_t *first, const int32_t *count, const BoxGeo *geo,
+                const typename V4<T>::type *src, double D, const T *M, int64_t n, double *far,
+                cudaStream_t s) {
+  if (nw == 0) return;
+  size_t sm = (size_t)ncoef(p) * sizeof(T);
+  k_m2p<T><<<(unsigned)nw, 64, sm, s>>>(p, wleaves, woff, widx, first, count, geo, src, D, M, n, far);
+  FMM_LAUNCH_CHECK();
+}
+
+void launch_combine(int64_t n, const int32_t *perm, const double *far, const double *near,
+                    double *phi, double *grad, cudaStream_t s) {
+  if (n == 0) return;
+  k_combine<<<ceil_div(n, 256), 256, 0, s>>>(n, perm, far, near, phi, grad);
+  FMM_LAUNCH_CHECK();
+}
+
+void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double *gq,
+                       const double *gw, double *dx, cudaStream_t s) {
+  if (n == 0) return;
+  k_adjoint_dx<<<ceil_div(3 * n, 256), 256, 0, s>>>(n, w, q, gq, gw, dx);
+  FMM_LAUNCH_CHECK();
+}
+
+// explicit instantiations
+#define FMM_INST_T(T)                                                                              \
+  template void launch_permute_charges<T>(int64_t, const int32_t *, const double *,                \
+                                          const V4<T>::type *, V4<T>::type *, cudaStream_t);       \
+  template void launch_p2m<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
+                              const BoxGeo *, const V4<T>::type *, double, T *, double *, int,     \
+                              cudaStream_t);                                                       \
+  template void launch_p2l<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
+                              const int32_t *, const int32_t *, const BoxGeo *,                    \
+                              const V4<T>::type *, double, T *, cudaStream_t);                     \
+  template void launch_l2p<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
+                              const BoxGeo *, const V4<T>::type *, double, const T *, int64_t,     \
+                              double *, cudaStream_t);                                             \
+  template void launch_m2p<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
+                              const int32_t *, const int32_t *, const BoxGeo *,                    \
+                              const V4<T>::type *, double, const T *, int64_t, double *,           \
+                              cudaStream_t);                                                       \
+  template void launch_to_f64<T>(int64_t, const T *, double *, cudaStream_t);
+FMM_INST_T(float)
+FMM_INST_T(double)
+#undef FMM_INST_T
+
+template void launch_m2m<double, double, double, double>(int, int32_t, int32_t, const int32_t *,
+                                                         const int32_t *, const BoxGeo *,
+                                                         const double *, const double *, double *,
+                                                         float *, cudaStream_t);
+template void launch_m2m<float, float, float, float>(int, int32_t, int32_t, const int32_t *,
+                                                     const int32_t *, const BoxGeo *, const float *,
+                                                     const float *, float *, float *, cudaStream_t);
+template void launch_m2m<float, double, double, double>(int, int32_t, int32_t, const int32_t *,
+                                                        const int32_t *, const BoxGeo *,
+                                                        const float *, const double *, double *,
+                                                        float *, cudaStream_t);
+template void launch_l2l<double, double, double, double, double>(int, int32_t, int32_t,
+                                                                  const int32_t *, const BoxGeo *,
+                                                                  const double *, const double *,
+                                                                  const double *, double *, float *,
+                                                                  cudaStream_t);
+template void launch_l2l<float, float, float, float, float>(int, int32_t, int32_t, const int32_t *,
+                                                            const BoxGeo *, const float *,
+                                                            const float *, const float *, float *,
+                                                            float *, cudaStream_t);
+template void launch_l2l<float, double, double, double, double>(int, int32_t, int32_t,
+                                                                const int32_t *, const BoxGeo *,
+                                                                const float *, const double *,
+                                                                const double *, double *, float *,
+                                                                cudaStream_t);
+
+}  // namespace fmm

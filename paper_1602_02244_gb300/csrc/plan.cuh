@@ -1,0 +1,153 @@
+// plan.cuh -- the plan object behind fmm_plan_t: tree, lists, operators and
+// evaluation workspace, all resident in HBM.
+#pragma once
+#include "common.cuh"
+
+namespace fmm {
+
+struct M2LTile {
+  int32_t start;   // first entry in m2l_order
+  int32_t count;   // targets in this tile (<= tile size)
+  int32_t parity;  // octant parity shared by the tile's targets (bit0 x, bit1 y, bit2 z)
+  int32_t pad;
+};
+
+struct Operators {
+  int order = -1;
+  // scale-free real-basis matrices, row-major [out][in], NC = (p+1)^2:
+  //   m2l[343][NC][NC] indexed by offset code (dx+3)*49+(dy+3)*7+(dz+3),
+  //   d = anchor(target) - anchor(source); m2m[8], l2l[8] by child octant.
+  DBuf<double> m2l64, m2m64, l2l64;
+  DBuf<float> m2l32, m2m32, l2l32;
+};
+
+// passes timed by the optional profiler (fmm_profile / fmm_profile_read)
+enum Pass { kPassSort = 0, kPassBoxes, kPassLists, kPassP2M, kPassM2M, kPassM2L, kPassP2L,
+            kPassL2L, kPassL2P, kPassM2P, kPassP2P, kPassReduce, kNumPasses };
+
+uint64_t launch_count();
+
+struct fmm_plan_impl {
+  // configuration
+  int order = 0, leaf_size = 1, precision = FMM_FP64, coarse_fp64_levels = 3, max_depth = kMaxDepth;
+  cudaStream_t stream = nullptr;
+
+  // points
+  int64_t n = 0;
+  double lo[3] = {0, 0, 0}, D = 1.0;
+  DBuf<double> geom;                // device: lo[3], D, nonfinite flag
+  DBuf<double> partial;             // bbox partials
+  DBuf<uint64_t> keys, keys_tmp;    // sorted Morton keys
+  DBuf<int32_t> perm, perm_tmp;     // sorted position -> input index
+  DBuf<double> xyz_sorted;          // n x 3 (sorted order)
+  DBuf<double4> pl64;               // per sorted point: position - leaf centre (w unused)
+  DBuf<float4> pl32;                // FP32 copy of pl64
+
+  // boxes, numbered by (level, key)
+  int nlevels = 0;
+  std::vector<int32_t> level_off;   // host, nlevels + 1
+  int64_t nboxes = 0;
+  DBuf<uint64_t> box_key;
+  DBuf<int32_t> box_level, box_first, box_count, box_parent, box_child, box_nchild;
+  DBuf<BoxGeo> box_geo;
+  DBuf<int32_t> colleagues;         // nboxes x 26, sorted, -1 padded
+  DBuf<int32_t> ncolleagues;
+
+  // lists (CSR over all boxes)
+  DBuf<int32_t> u_off, u_idx, v_off, v_idx, w_off, w_idx, x_off, x_idx;
+  int64_t nu = 0, nv = 0, nw = 0, nx = 0;
+
+  // work lists
+  DBuf<int32_t> leaves;             // leaf boxes
+  int64_t nleaves = 0;
+  DBuf<int32_t> xboxes;             // boxes with a non-empty X list
+  int64_t nxboxes = 0;
+  DBuf<int32_t> wleaves;            // leaves with a non-empty W list
+  int64_t nwleaves = 0;
+  DBuf<int32_t> m2l_order;          // boxes of level >= 2 ordered by (level, parity, index)
+  DBuf<M2LTile> m2l_tiles;
+  int64_t nm2l_tiles = 0;
+  int m2l_tile_size = 0;
+
+  // operators (rebuilt only when the order changes)
+  Operators ops;
+
+  // evaluation workspace
+  DBuf<double4> src64;              // per sorted point: (local x, y, z, q)
+  DBuf<float4> src32;
+  DBuf<double> M64, L64;            // nboxes x NC
+  DBuf<float> M32, L32;
+  DBuf<double> far_acc, near_acc;   // 4 x n each: phi, gx, gy, gz (sorted order)
+  DBuf<double> adj_grad_w, adj_grad_q;  // n x 3 (adjoint)
+  DBuf<double> adj_phi;
+  DBuf<double> host_io;             // device staging for fmm_solve_host
+
+  // profiler: CUDA events around each pass on the plan's stream
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct ProfRec {
+    int pass;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof_recs;
+  int64_t prof_launches[kNumPasses] = {};
+  cudaEvent_t next_event() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e;
+      FMM_CUDA(cudaEventCreate(&e));
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+
+  // scratch
+  DBuf<int32_t> s_i32a, s_i32b, s_i32c, s_hist, s_scan;
+  DBuf<uint64_t> s_u64a, s_u64b;
+  DBuf<int32_t> s_total;            // device scalars for scan totals
+  DBuf<int32_t> ca_off, ca_idx;     // coarser-or-equal adjacent leaves per box
+};
+
+// Records CUDA events around one pass when the plan's profiler is on.
+struct PassScope {
+  fmm_plan_impl &P;
+  int pass;
+  cudaEvent_t a = nullptr;
+  uint64_t l0 = 0;
+  PassScope(fmm_plan_impl &p, int ps) : P(p), pass(ps) {
+    if (!P.prof_on) return;
+    a = P.next_event();
+    FMM_CUDA(cudaEventRecord(a, P.stream));
+    l0 = launch_count();
+  }
+  ~PassScope() {
+    if (!a) return;
+    cudaEvent_t b = nullptr;
+    try {
+      b = P.next_event();
+    } catch (...) {
+      return;
+    }
+    if (cudaEventRecord(b, P.stream) != cudaSuccess) return;
+    P.prof_recs.push_back({pass, a, b});
+    P.prof_launches[pass] += (int64_t)(launch_count() - l0);
+  }
+};
+
+// tree.cu
+void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n);
+void set_points(fmm_plan_impl &P, const double *d_xyz);
+// operators.cu
+void build_operators(fmm_plan_impl &P);
+// eval.cu
+void eval_fmm(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad);
+void adjoint_fmm(fmm_plan_impl &P, const double *d_w, const double *d_q, const double *d_grad_q,
+                 double *d_dq, double *d_dx);
+void release_plan(fmm_plan_impl &P);
+
+// read a device int32 scalar (synchronous)
+int32_t read_scalar(const int32_t *d, cudaStream_t s);
+
+}  // namespace fmm
+
+struct fmm_plan_s : fmm::fmm_plan_impl {};

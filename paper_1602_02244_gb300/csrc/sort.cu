@@ -1,0 +1,221 @@
+// sort.cu -- exclusive scan and stable LSD radix sort for sm_103a.
+//
+// Radix sort: reduce-then-scan per 8-bit digit.  (1) every CTA counts the
+// digits of its 4096-key tile; (2) one device-wide exclusive scan over the
+// digit-major count table gives every (digit, tile) its output base; (3) every
+// CTA ranks its keys stably (warp match_any per 32-key round, warp-ordered
+// digit counters in shared memory) and scatters.  No inter-CTA waits.
+#include "sort.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *warp_sums,
+                                                        int32_t *total) {
+  // exclusive scan of one value per thread across a 256-thread block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = lane < (kScanThreads / 32) ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < (kScanThreads / 32)) warp_sums[lane] = w;  // inclusive
+  }
+  __syncthreads();
+  int32_t base = warp > 0 ? warp_sums[warp - 1] : 0;
+  if (total) *total = warp_sums[kScanThreads / 32 - 1];
+  return base + x - v;
+}
+
+__global__ void k_scan_reduce(const int32_t *__restrict__ in, int64_t n, int32_t *sums) {
+  __shared__ int32_t ws[32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int32_t s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  int32_t tot;
+  block_exclusive_scan(s, ws, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int32_t *sums, int nblocks, int32_t *d_total) {
+  // single CTA: exclusive scan of the block sums in chunks of 256
+  __shared__ int32_t ws[32];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int c = 0; c < nblocks; c += kScanThreads) {
+    int i = c + threadIdx.x;
+    int32_t v = i < nblocks ? sums[i] : 0;
+    int32_t tot;
+    int32_t ex = block_exclusive_scan(v, ws, &tot);
+    int32_t base = carry;
+    if (i < nblocks) sums[i] = base + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry = base + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
+__global__ void k_scan_apply(const int32_t *in, int32_t *out, int64_t n, const int32_t *sums) {
+  // each thread owns kScanItems consecutive elements of the tile
+  __shared__ int32_t ws[32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int32_t v[kScanItems];
+  int32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    v[k] = i < n ? in[i] : 0;
+    s += v[k];
+  }
+  int32_t ex = block_exclusive_scan(s, ws, nullptr) + sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    if (i < n) out[i] = ex;
+    ex += v[k];
+  }
+}
+
+// ------------------------------------------------------------ radix sort
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 16;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 4096 keys per CTA
+constexpr int kRsWarpSeg = 32 * kRsItems;       // 512 keys per warp
+
+__global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
+                             int32_t *__restrict__ hist, int nblocks) {
+  __shared__ int32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kRsTile;
+  for (int k = 0; k < kRsItems; ++k) {
+    int64_t i = base + (int64_t)k * kRsThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+template <bool kVals>
+__global__ void __launch_bounds__(kRsThreads)
+    k_radix_scatter(const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, int64_t n,
+                    int shift, const int32_t *__restrict__ offs, int nblocks,
+                    uint64_t *__restrict__ kout, int32_t *__restrict__ vout) {
+  __shared__ int32_t whist[kRsWarps][256];
+  __shared__ int32_t gbase[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = 0; w < kRsWarps; ++w) whist[w][threadIdx.x] = 0;
+  gbase[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  __syncthreads();
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t seg = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * kRsWarpSeg;
+  uint64_t key[kRsItems];
+  int32_t val[kRsItems];
+  int32_t rank[kRsItems];
+#pragma unroll
+  for (int r = 0; r < kRsItems; ++r) {
+    int64_t i = seg + r * 32 + lane;
+    bool valid = i < n;
+    key[r] = valid ? kin[i] : 0;
+    if (kVals) val[r] = valid ? vin[i] : 0;
+    unsigned d = valid ? (unsigned)((key[r] >> shift) & 255u) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int32_t prev = valid ? whist[warp][d] : 0;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) whist[warp][d] = prev + __popc(peers);
+    __syncwarp();
+    rank[r] = prev + __popc(peers & lt_mask);
+  }
+  __syncthreads();
+  {  // exclusive scan over warps, per digit
+    int32_t s = 0;
+    for (int w = 0; w < kRsWarps; ++w) {
+      int32_t c = whist[w][threadIdx.x];
+      whist[w][threadIdx.x] = s;
+      s += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRsItems; ++r) {
+    int64_t i = seg + r * 32 + lane;
+    if (i < n) {
+      unsigned d = (unsigned)((key[r] >> shift) & 255u);
+      int64_t pos = (int64_t)gbase[d] + whist[warp][d] + rank[r];
+      kout[pos] = key[r];
+      if (kVals) vout[pos] = val[r];
+    }
+  }
+}
+
+}  // namespace
+
+void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *d_total,
+                    DBuf<int32_t> &tmp, cudaStream_t s) {
+  if (n <= 0) {
+    if (d_total) FMM_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int32_t), s));
+    return;
+  }
+  int nb = ceil_div(n, kScanTile);
+  tmp.resize(nb, s);
+  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, n, tmp.p);
+  FMM_LAUNCH_CHECK();
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp.p, nb, d_total);
+  FMM_LAUNCH_CHECK();
+  k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, out, n, tmp.p);
+  FMM_LAUNCH_CHECK();
+}
+
+std::vector<int> digit_shifts(int lo, int hi) {
+  std::vector<int> v;
+  for (int b = lo; b < hi; b += 8) v.push_back(b);
+  return v;
+}
+
+void radix_sort(DBuf<uint64_t> &keys, DBuf<int32_t> &vals, DBuf<uint64_t> &tkeys,
+                DBuf<int32_t> &tvals, int64_t n, const std::vector<int> &shifts,
+                DBuf<int32_t> &hist, DBuf<int32_t> &tmp, cudaStream_t s) {
+  if (n <= 1 || shifts.empty()) return;
+  const bool has_vals = vals.p != nullptr;
+  int nb = ceil_div(n, kRsTile);
+  hist.resize((size_t)256 * nb, s);
+  tkeys.resize(n, s);
+  if (has_vals) tvals.resize(n, s);
+  for (int sh : shifts) {
+    k_radix_hist<<<nb, kRsThreads, 0, s>>>(keys.p, n, sh, hist.p, nb);
+    FMM_LAUNCH_CHECK();
+    scan_exclusive(hist.p, hist.p, (int64_t)256 * nb, nullptr, tmp, s);
+    if (has_vals)
+      k_radix_scatter<true><<<nb, kRsThreads, 0, s>>>(keys.p, vals.p, n, sh, hist.p, nb, tkeys.p,
+                                                      tvals.p);
+    else
+      k_radix_scatter<false><<<nb, kRsThreads, 0, s>>>(keys.p, nullptr, n, sh, hist.p, nb,
+                                                       tkeys.p, nullptr);
+    FMM_LAUNCH_CHECK();
+    std::swap(keys, tkeys);
+    if (has_vals) std::swap(vals, tvals);
+  }
+}
+
+}  // namespace fmm

@@ -1,0 +1,705 @@
+// tree.cu -- hierarchy of the FMM on the GPU: root cube, Morton keys (§3.1
+// 3D->1D locality mapping), stable radix sort, adaptive octree level by
+// level, colleagues, and the U/V/W/X interaction lists (§2.2: the
+// interaction list holds the children of the parent's neighbours that are
+// not neighbours, at most 189; U/W/X are the adaptive lists of the cited
+// kernel-independent FMM).
+//
+// All of it is integer work and bit-exact: the quantisation uses
+// round-to-nearest FP64 subtract then an exact power-of-two scale, boxes are
+// numbered by (level, key) and every list is sorted by box number.
+#include <algorithm>
+#include <memory>
+
+#include "m2l_config.cuh"
+#include "plan.cuh"
+#include "sort.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kT = 256;
+
+// ------------------------------------------------------------ root cube
+__global__ void k_bbox_partial(const double *__restrict__ xyz, int64_t n, double *partial) {
+  __shared__ double smin[3][kT], smax[3][kT];
+  __shared__ int sbad[kT];
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    for (int a = 0; a < 3; ++a) {
+      double v = xyz[3 * i + a];
+      if (!isfinite(v)) bad = 1;
+      mn[a] = fmin(mn[a], v);
+      mx[a] = fmax(mx[a], v);
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    smin[a][threadIdx.x] = mn[a];
+    smax[a][threadIdx.x] = mx[a];
+  }
+  sbad[threadIdx.x] = bad;
+  __syncthreads();
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      for (int a = 0; a < 3; ++a) {
+        smin[a][threadIdx.x] = fmin(smin[a][threadIdx.x], smin[a][threadIdx.x + o]);
+        smax[a][threadIdx.x] = fmax(smax[a][threadIdx.x], smax[a][threadIdx.x + o]);
+      }
+      sbad[threadIdx.x] |= sbad[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < 3; ++a) {
+      partial[7 * blockIdx.x + a] = smin[a][0];
+      partial[7 * blockIdx.x + 3 + a] = smax[a][0];
+    }
+    partial[7 * blockIdx.x + 6] = sbad[0];
+  }
+}
+
+__global__ void k_bbox_final(const double *partial, int nb, double *geom) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  double bad = 0;
+  for (int b = 0; b < nb; ++b) {
+    for (int a = 0; a < 3; ++a) {
+      mn[a] = fmin(mn[a], partial[7 * b + a]);
+      mx[a] = fmax(mx[a], partial[7 * b + 3 + a]);
+    }
+    bad = fmax(bad, partial[7 * b + 6]);
+  }
+  double ext = 0.0;
+  for (int a = 0; a < 3; ++a) ext = fmax(ext, mx[a] - mn[a]);
+  double D = 1.0;
+  if (ext > 0.0) {
+    int e;
+    frexp(ext, &e);  // ext = f 2^e with f in [0.5,1): 2^e is the smallest power of two > ext
+    D = ldexp(1.0, e);
+  }
+  for (int a = 0; a < 3; ++a) geom[a] = mn[a];
+  geom[3] = D;
+  geom[4] = bad;
+}
+
+__global__ void k_morton(const double *__restrict__ xyz, int64_t n, const double *__restrict__ geom,
+                         uint64_t *__restrict__ keys, int32_t *__restrict__ perm) {
+  int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i >= n) return;
+  const double D = geom[3];
+  const double s = ldexp(1.0, kMaxDepth) / D;  // power of two: the product below is exact
+  const double top = (double)((1u << kMaxDepth) - 1u);
+  uint32_t q[3];
+  for (int a = 0; a < 3; ++a) {
+    double t = floor(__dmul_rn(__dsub_rn(xyz[3 * i + a], geom[a]), s));
+    t = fmin(fmax(t, 0.0), top);
+    q[a] = (uint32_t)t;
+  }
+  keys[i] = morton3(q[0], q[1], q[2]);
+  perm[i] = (int32_t)i;
+}
+
+__global__ void k_gather_xyz(const double *__restrict__ xyz, const int32_t *__restrict__ perm,
+                             int64_t n, double *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i >= n) return;
+  int64_t j = perm[i];
+  out[3 * i] = xyz[3 * j];
+  out[3 * i + 1] = xyz[3 * j + 1];
+  out[3 * i + 2] = xyz[3 * j + 2];
+}
+
+// --------------------------------------------------------------- octree
+__device__ __forceinline__ int32_t lower_bound_digit(const uint64_t *keys, int32_t f, int32_t e,
+                                                     int shift, uint32_t o) {
+  // first i in [f, e) with digit(i) >= o; digits are non-decreasing in the range
+  while (f < e) {
+    int32_t m = f + ((e - f) >> 1);
+    if (((keys[m] >> shift) & 7u) < o) f = m + 1;
+    else e = m;
+  }
+  return f;
+}
+
+__global__ void k_split_count(int level, int32_t b0, int32_t nbl, const int32_t *__restrict__ first,
+                              const int32_t *__restrict__ count, const uint64_t *__restrict__ keys,
+                              int leaf_size, int max_depth, int32_t *__restrict__ nchild) {
+  int32_t t = blockIdx.x * kT + threadIdx.x;
+  if (t >= nbl) return;
+  int32_t b = b0 + t;
+  int32_t c = count[b];
+  if (c <= leaf_size || level >= max_depth) {
+    nchild[t] = 0;
+    return;
+  }
+  int shift = 3 * (kMaxDepth - (level + 1));
+  int32_t f = first[b], e = f + c, k = 0, s = f;
+  for (uint32_t o = 0; o < 8; ++o) {
+    int32_t s1 = lower_bound_digit(keys, s, e, shift, o + 1);
+    k += (s1 > s);
+    s = s1;
+  }
+  nchild[t] = k;
+}
+
+__global__ void k_split_make(int level, int32_t b0, int32_t nbl, int32_t child0,
+                             const int32_t *__restrict__ nchild, const int32_t *__restrict__ coff,
+                             const uint64_t *__restrict__ keys, int32_t *first, int32_t *count,
+                             uint64_t *bkey, int32_t *blevel, int32_t *parent, int32_t *child,
+                             int32_t *bnchild) {
+  int32_t t = blockIdx.x * kT + threadIdx.x;
+  if (t >= nbl) return;
+  int32_t b = b0 + t;
+  int32_t k = nchild[t];
+  bnchild[b] = k;
+  if (k == 0) {
+    child[b] = -1;
+    return;
+  }
+  int32_t c = child0 + coff[t];
+  child[b] = c;
+  int shift = 3 * (kMaxDepth - (level + 1));
+  int32_t f = first[b], e = f + count[b], s = f;
+  uint64_t pk = bkey[b];
+  for (uint32_t o = 0; o < 8; ++o) {
+    int32_t s1 = lower_bound_digit(keys, s, e, shift, o + 1);
+    if (s1 > s) {
+      first[c] = s;
+      count[c] = s1 - s;
+      bkey[c] = (pk << 3) | o;
+      blevel[c] = level + 1;
+      parent[c] = b;
+      ++c;
+    }
+    s = s1;
+  }
+}
+
+__global__ void k_box_geo(int64_t nb, const uint64_t *__restrict__ bkey,
+                          const int32_t *__restrict__ blevel, BoxGeo *__restrict__ geo) {
+  int64_t b = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (b >= nb) return;
+  uint64_t k = bkey[b];
+  BoxGeo g;
+  g.ix = (int32_t)compact3(k);
+  g.iy = (int32_t)compact3(k >> 1);
+  g.iz = (int32_t)compact3(k >> 2);
+  g.level = blevel[b];
+  geo[b] = g;
+}
+
+__global__ void k_flag(int64_t n, const int32_t *__restrict__ a, const int32_t *__restrict__ b,
+                       int mode, int32_t *__restrict__ flag) {
+  // mode 0: flag = (a[i] == 0)     (leaf: no children)
+  // mode 1: flag = (a[i+1] > a[i]) (non-empty CSR row)
+  // mode 2: flag = (b[i] == 0 && a[i+1] > a[i])
+  int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i >= n) return;
+  int32_t f;
+  if (mode == 0) f = a[i] == 0;
+  else if (mode == 1) f = a[i + 1] > a[i];
+  else f = (b[i] == 0) && (a[i + 1] > a[i]);
+  flag[i] = f;
+}
+
+__global__ void k_compact(int64_t n, const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
+                          int32_t *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i >= n) return;
+  if (flag[i]) out[pos[i]] = (int32_t)i;
+}
+
+__global__ void k_leaf_points(const int32_t *__restrict__ leaves, const BoxGeo *__restrict__ geo,
+                              const int32_t *__restrict__ first, const int32_t *__restrict__ count,
+                              const double *__restrict__ xyz, double lx, double ly, double lz,
+                              double D, double4 *__restrict__ pl64, float4 *__restrict__ pl32) {
+  int32_t b = leaves[blockIdx.x];
+  BoxGeo g = geo[b];
+  double a = box_side(D, g.level);
+  double cx = lx + ((double)g.ix + 0.5) * a, cy = ly + ((double)g.iy + 0.5) * a,
+         cz = lz + ((double)g.iz + 0.5) * a;
+  int32_t f = first[b], c = count[b];
+  for (int32_t i = f + threadIdx.x; i < f + c; i += blockDim.x) {
+    double x = xyz[3 * (int64_t)i] - cx, y = xyz[3 * (int64_t)i + 1] - cy,
+           z = xyz[3 * (int64_t)i + 2] - cz;
+    pl64[i] = make_double4(x, y, z, 0.0);
+    pl32[i] = make_float4((float)x, (float)y, (float)z, 0.f);
+  }
+}
+
+// ------------------------------------------------------------ adjacency
+__device__ __forceinline__ bool adjacent(const BoxGeo &A, const BoxGeo &B) {
+  int sa = kMaxDepth - A.level, sb = kMaxDepth - B.level;
+  int64_t alo, ahi, blo, bhi;
+  alo = (int64_t)A.ix << sa; ahi = ((int64_t)A.ix + 1) << sa;
+  blo = (int64_t)B.ix << sb; bhi = ((int64_t)B.ix + 1) << sb;
+  if (alo > bhi || blo > ahi) return false;
+  alo = (int64_t)A.iy << sa; ahi = ((int64_t)A.iy + 1) << sa;
+  blo = (int64_t)B.iy << sb; bhi = ((int64_t)B.iy + 1) << sb;
+  if (alo > bhi || blo > ahi) return false;
+  alo = (int64_t)A.iz << sa; ahi = ((int64_t)A.iz + 1) << sa;
+  blo = (int64_t)B.iz << sb; bhi = ((int64_t)B.iz + 1) << sb;
+  if (alo > bhi || blo > ahi) return false;
+  return true;
+}
+
+// colleagues: same-level boxes adjacent to B (excluding B), ascending
+__global__ void k_colleagues(int64_t nb, const BoxGeo *__restrict__ geo,
+                             const uint64_t *__restrict__ bkey, const int32_t *__restrict__ loff,
+                             int32_t *__restrict__ col, int32_t *__restrict__ ncol) {
+  int64_t b = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (b >= nb) return;
+  BoxGeo g = geo[b];
+  int32_t found[26];
+  int k = 0;
+  if (g.level > 0) {
+    const int32_t lo = loff[g.level], hi = loff[g.level + 1];
+    const int32_t lim = 1 << g.level;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (!dx && !dy && !dz) continue;
+          int32_t x = g.ix + dx, y = g.iy + dy, z = g.iz + dz;
+          if (x < 0 || y < 0 || z < 0 || x >= lim || y >= lim || z >= lim) continue;
+          uint64_t key = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+          int32_t f = lo, e = hi;
+          while (f < e) {
+            int32_t m = f + ((e - f) >> 1);
+            if (bkey[m] < key) f = m + 1;
+            else e = m;
+          }
+          if (f < hi && bkey[f] == key) {
+            int j = k++;  // insertion sort
+            while (j > 0 && found[j - 1] > f) {
+              found[j] = found[j - 1];
+              --j;
+            }
+            found[j] = f;
+          }
+        }
+  }
+  for (int j = 0; j < 26; ++j) col[26 * b + j] = j < k ? found[j] : -1;
+  ncol[b] = k;
+}
+
+// V(B), level >= 2: children of colleagues of parent(B) not adjacent to B
+template <bool kFill>
+__global__ void k_vlist(int64_t nb, const BoxGeo *__restrict__ geo, const int32_t *__restrict__ parent,
+                        const int32_t *__restrict__ child, const int32_t *__restrict__ nchild,
+                        const int32_t *__restrict__ col, const int32_t *__restrict__ ncol,
+                        int32_t *__restrict__ cnt, const int32_t *__restrict__ off,
+                        int32_t *__restrict__ idx) {
+  int64_t b = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (b >= nb) return;
+  BoxGeo g = geo[b];
+  int32_t k = 0;
+  int32_t o = kFill ? off[b] : 0;
+  if (g.level >= 2) {
+    int32_t P = parent[b];
+    for (int j = 0; j < ncol[P]; ++j) {
+      int32_t C = col[26 * (int64_t)P + j];
+      int32_t c0 = child[C], c1 = c0 + nchild[C];
+      for (int32_t A = c0; A < c1; ++A) {
+        if (!adjacent(geo[A], g)) {
+          if (kFill) idx[o + k] = A;
+          ++k;
+        }
+      }
+    }
+  }
+  if (!kFill) cnt[b] = k;
+}
+
+// CA(B): leaves with level <= level(B), adjacent to B, other than B.  They are
+// the leaf colleagues of B's ancestors (and of B) that touch B; ascending.
+template <bool kFill>
+__global__ void k_calist(int64_t nb, const BoxGeo *__restrict__ geo, const int32_t *__restrict__ parent,
+                         const int32_t *__restrict__ nchild, const int32_t *__restrict__ col,
+                         const int32_t *__restrict__ ncol, int32_t *__restrict__ cnt,
+                         const int32_t *__restrict__ off, int32_t *__restrict__ idx) {
+  int64_t b = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (b >= nb) return;
+  BoxGeo g = geo[b];
+  int32_t chain[kMaxDepth + 1];
+  int32_t Q = (int32_t)b;
+  for (int l = g.level; l >= 0; --l) {
+    chain[l] = Q;
+    Q = parent[Q];
+  }
+  int32_t k = 0;
+  int32_t o = kFill ? off[b] : 0;
+  for (int l = 1; l <= g.level; ++l) {
+    int32_t A = chain[l];
+    for (int j = 0; j < ncol[A]; ++j) {
+      int32_t C = col[26 * (int64_t)A + j];
+      if (nchild[C] == 0 && adjacent(geo[C], g)) {
+        if (kFill) idx[o + k] = C;
+        ++k;
+      }
+    }
+  }
+  if (!kFill) cnt[b] = k;
+}
+
+// U pairs of leaf B: (B,B), (B,A) for A in CA(B), and (A,B) for the coarser
+// A in CA(B) (finer adjacent leaves find B in their own CA lists).
+template <bool kFill>
+__global__ void k_upairs(int64_t nleaves, const int32_t *__restrict__ leaves,
+                         const BoxGeo *__restrict__ geo, const int32_t *__restrict__ caoff,
+                         const int32_t *__restrict__ caidx, int32_t *__restrict__ cnt,
+                         const int32_t *__restrict__ off, uint64_t *__restrict__ pairs) {
+  int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (t >= nleaves) return;
+  int32_t B = leaves[t];
+  int lb = geo[B].level;
+  int32_t k = 0;
+  int64_t o = kFill ? off[t] : 0;
+  if (kFill) pairs[o] = ((uint64_t)B << 32) | (uint32_t)B;
+  ++k;
+  for (int32_t e = caoff[B]; e < caoff[B + 1]; ++e) {
+    int32_t A = caidx[e];
+    if (kFill) pairs[o + k] = ((uint64_t)B << 32) | (uint32_t)A;
+    ++k;
+    if (geo[A].level < lb) {
+      if (kFill) pairs[o + k] = ((uint64_t)A << 32) | (uint32_t)B;
+      ++k;
+    }
+  }
+  if (!kFill) cnt[t] = k;
+}
+
+// X(C) = { A in CA(parent(C)) : A not adjacent to C }
+template <bool kFill>
+__global__ void k_xlist(int64_t nb, const BoxGeo *__restrict__ geo, const int32_t *__restrict__ parent,
+                        const int32_t *__restrict__ caoff, const int32_t *__restrict__ caidx,
+                        int32_t *__restrict__ cnt, const int32_t *__restrict__ off,
+                        int32_t *__restrict__ idx) {
+  int64_t C = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (C >= nb) return;
+  BoxGeo g = geo[C];
+  int32_t k = 0;
+  int32_t o = kFill ? off[C] : 0;
+  if (g.level >= 2) {
+    int32_t P = parent[C];
+    for (int32_t e = caoff[P]; e < caoff[P + 1]; ++e) {
+      int32_t A = caidx[e];
+      if (!adjacent(geo[A], g)) {
+        if (kFill) idx[o + k] = A;
+        ++k;
+      }
+    }
+  }
+  if (!kFill) cnt[C] = k;
+}
+
+// W pairs from X: (A, C) for every A in X(C)
+__global__ void k_wpairs(int64_t nb, const int32_t *__restrict__ xoff, const int32_t *__restrict__ xidx,
+                         uint64_t *__restrict__ pairs) {
+  int64_t C = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (C >= nb) return;
+  for (int32_t e = xoff[C]; e < xoff[C + 1]; ++e)
+    pairs[e] = ((uint64_t)(uint32_t)xidx[e] << 32) | (uint32_t)C;
+}
+
+// CSR rows from (row << 32 | col) keys sorted ascending
+__global__ void k_pairs_csr(int64_t np, int64_t nb, const uint64_t *__restrict__ keys,
+                            int32_t *__restrict__ off, int32_t *__restrict__ idx) {
+  int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i > np) return;
+  int64_t prev = i > 0 ? (int64_t)(keys[i - 1] >> 32) : -1;
+  int64_t cur = i < np ? (int64_t)(keys[i] >> 32) : nb;
+  for (int64_t r = prev + 1; r <= cur; ++r) off[r] = (int32_t)i;
+  if (i < np) idx[i] = (int32_t)(keys[i] & 0xffffffffu);
+}
+
+// M2L ordering key: (level, parity) class of every box of level >= 2
+__global__ void k_m2l_class(int64_t b0, int64_t nb, const BoxGeo *__restrict__ geo,
+                            uint64_t *__restrict__ key, int32_t *__restrict__ val,
+                            int32_t *__restrict__ hist) {
+  int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (t >= nb - b0) return;
+  int64_t b = b0 + t;
+  BoxGeo g = geo[b];
+  int cls = g.level * 8 + (g.ix & 1) + 2 * (g.iy & 1) + 4 * (g.iz & 1);
+  key[t] = (uint64_t)cls;
+  val[t] = (int32_t)b;
+  atomicAdd(&hist[cls], 1);
+}
+
+inline int grid(int64_t n) { return n > 0 ? ceil_div(n, kT) : 1; }
+
+int bits_for(int64_t v) {
+  int b = 1;
+  while ((int64_t(1) << b) <= v) ++b;
+  return b;
+}
+
+// CSR row offsets (nb+1) from per-row counts (nb); returns the total
+int64_t counts_to_offsets(fmm_plan_impl &P, const int32_t *cnt, DBuf<int32_t> &off, int64_t nrows) {
+  off.resize(nrows + 1, P.stream);
+  scan_exclusive(cnt, off.p, nrows, off.p + nrows, P.s_scan, P.stream);
+  return read_scalar(off.p + nrows, P.stream);
+}
+
+// sort (row<<32|col) pairs and convert to CSR over nb rows
+void pairs_to_csr(fmm_plan_impl &P, DBuf<uint64_t> &pairs, int64_t np, int64_t nb,
+                  DBuf<int32_t> &off, DBuf<int32_t> &idx) {
+  cudaStream_t s = P.stream;
+  int b = bits_for(nb);
+  std::vector<int> sh = digit_shifts(0, b);
+  for (int x : digit_shifts(32, 32 + b)) sh.push_back(x);
+  DBuf<int32_t> novals;
+  radix_sort(pairs, novals, P.s_u64b, novals, np, sh, P.s_hist, P.s_scan, s);
+  off.resize(nb + 1, s);
+  idx.resize(np > 0 ? np : 1, s);
+  k_pairs_csr<<<grid(np + 1), kT, 0, s>>>(np, nb, pairs.p, off.p, idx.p);
+  FMM_LAUNCH_CHECK();
+}
+
+int64_t compact(fmm_plan_impl &P, int64_t n, const int32_t *flag, DBuf<int32_t> &out) {
+  cudaStream_t s = P.stream;
+  P.s_i32c.resize(n + 1, s);
+  scan_exclusive(flag, P.s_i32c.p, n, P.s_i32c.p + n, P.s_scan, s);
+  int64_t m = read_scalar(P.s_i32c.p + n, s);
+  out.resize(m > 0 ? m : 1, s);
+  k_compact<<<grid(n), kT, 0, s>>>(n, flag, P.s_i32c.p, out.p);
+  FMM_LAUNCH_CHECK();
+  return m;
+}
+
+}  // namespace
+
+int32_t read_scalar(const int32_t *d, cudaStream_t s) {
+  int32_t h = 0;
+  FMM_CUDA(cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+void set_points(fmm_plan_impl &P, const double *d_xyz) {
+  cudaStream_t s = P.stream;
+  int64_t n = P.n;
+  if (n == 0) return;
+  k_gather_xyz<<<grid(n), kT, 0, s>>>(d_xyz, P.perm.p, n, P.xyz_sorted.p);
+  FMM_LAUNCH_CHECK();
+  k_leaf_points<<<(int)P.nleaves, 128, 0, s>>>(P.leaves.p, P.box_geo.p, P.box_first.p,
+                                                P.box_count.p, P.xyz_sorted.p, P.lo[0], P.lo[1],
+                                                P.lo[2], P.D, P.pl64.p, P.pl32.p);
+  FMM_LAUNCH_CHECK();
+}
+
+void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
+  cudaStream_t s = P.stream;
+  P.n = n;
+  P.nboxes = 0;
+  P.nlevels = 0;
+  P.level_off.assign(1, 0);
+  P.nu = P.nv = P.nw = P.nx = 0;
+  P.nleaves = P.nxboxes = P.nwleaves = P.nm2l_tiles = 0;
+  if (n == 0) return;
+  std::unique_ptr<PassScope> scope(new PassScope(P, kPassSort));
+
+  // ---- root cube
+  int nbb = std::min(ceil_div(n, kT * 8), 1024);
+  P.partial.resize((size_t)7 * nbb, s);
+  P.geom.resize(8, s);
+  k_bbox_partial<<<nbb, kT, 0, s>>>(d_xyz, n, P.partial.p);
+  FMM_LAUNCH_CHECK();
+  k_bbox_final<<<1, 32, 0, s>>>(P.partial.p, nbb, P.geom.p);
+  FMM_LAUNCH_CHECK();
+  double hg[5];
+  FMM_CUDA(cudaMemcpyAsync(hg, P.geom.p, sizeof(hg), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(cudaStreamSynchronize(s));
+  if (hg[4] != 0.0) throw Error(FMM_ERR_NONFINITE_INPUT, "a coordinate is NaN or infinite");
+  P.lo[0] = hg[0];
+  P.lo[1] = hg[1];
+  P.lo[2] = hg[2];
+  P.D = hg[3];
+
+  // ---- keys and stable sort
+  P.keys.resize(n, s);
+  P.perm.resize(n, s);
+  k_morton<<<grid(n), kT, 0, s>>>(d_xyz, n, P.geom.p, P.keys.p, P.perm.p);
+  FMM_LAUNCH_CHECK();
+  radix_sort(P.keys, P.perm, P.keys_tmp, P.perm_tmp, n, digit_shifts(0, 3 * kMaxDepth), P.s_hist,
+             P.s_scan, s);
+  P.xyz_sorted.resize(3 * n, s);
+  k_gather_xyz<<<grid(n), kT, 0, s>>>(d_xyz, P.perm.p, n, P.xyz_sorted.p);
+  FMM_LAUNCH_CHECK();
+
+  // ---- boxes, level by level
+  scope.reset(new PassScope(P, kPassBoxes));
+  size_t cap0 = std::max<size_t>(1024, 2 * (size_t)n / (size_t)P.leaf_size + 64);
+  auto grow_boxes = [&](size_t need, size_t keep) {
+    P.box_key.grow(std::max(need, cap0), keep, s);
+    P.box_level.grow(std::max(need, cap0), keep, s);
+    P.box_first.grow(std::max(need, cap0), keep, s);
+    P.box_count.grow(std::max(need, cap0), keep, s);
+    P.box_parent.grow(std::max(need, cap0), keep, s);
+    P.box_child.grow(std::max(need, cap0), keep, s);
+    P.box_nchild.grow(std::max(need, cap0), keep, s);
+  };
+  grow_boxes(1, 0);
+  {
+    uint64_t k0 = 0;
+    int32_t z = 0, m1 = -1, cnt = (int32_t)n;
+    FMM_CUDA(cudaMemcpyAsync(P.box_key.p, &k0, sizeof k0, cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaMemcpyAsync(P.box_level.p, &z, sizeof z, cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaMemcpyAsync(P.box_first.p, &z, sizeof z, cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaMemcpyAsync(P.box_count.p, &cnt, sizeof cnt, cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaMemcpyAsync(P.box_parent.p, &m1, sizeof m1, cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaStreamSynchronize(s));  // the host values above are stack variables
+  }
+  P.level_off = {0, 1};
+  int64_t nb = 1;
+  for (int l = 0;; ++l) {
+    int32_t b0 = P.level_off[l], nbl = P.level_off[l + 1] - b0;
+    P.s_i32a.resize(nbl + 1, s);
+    P.s_i32b.resize(nbl + 1, s);
+    k_split_count<<<grid(nbl), kT, 0, s>>>(l, b0, nbl, P.box_first.p, P.box_count.p, P.keys.p,
+                                            P.leaf_size, P.max_depth, P.s_i32a.p);
+    FMM_LAUNCH_CHECK();
+    scan_exclusive(P.s_i32a.p, P.s_i32b.p, nbl, P.s_i32b.p + nbl, P.s_scan, s);
+    int32_t nnew = read_scalar(P.s_i32b.p + nbl, s);
+    if (nnew > 0) grow_boxes(nb + nnew, nb);
+    k_split_make<<<grid(nbl), kT, 0, s>>>(l, b0, nbl, (int32_t)nb, P.s_i32a.p, P.s_i32b.p, P.keys.p,
+                                           P.box_first.p, P.box_count.p, P.box_key.p, P.box_level.p,
+                                           P.box_parent.p, P.box_child.p, P.box_nchild.p);
+    FMM_LAUNCH_CHECK();
+    if (nnew == 0) break;
+    nb += nnew;
+    P.level_off.push_back((int32_t)nb);
+  }
+  P.nboxes = nb;
+  P.nlevels = (int)P.level_off.size() - 1;
+
+  P.box_geo.resize(nb, s);
+  k_box_geo<<<grid(nb), kT, 0, s>>>(nb, P.box_key.p, P.box_level.p, P.box_geo.p);
+  FMM_LAUNCH_CHECK();
+
+  // ---- leaves and leaf-local coordinates
+  P.s_i32a.resize(nb, s);
+  k_flag<<<grid(nb), kT, 0, s>>>(nb, P.box_nchild.p, nullptr, 0, P.s_i32a.p);
+  FMM_LAUNCH_CHECK();
+  P.nleaves = compact(P, nb, P.s_i32a.p, P.leaves);
+  P.pl64.resize(n, s);
+  P.pl32.resize(n, s);
+  k_leaf_points<<<(int)P.nleaves, 128, 0, s>>>(P.leaves.p, P.box_geo.p, P.box_first.p,
+                                                P.box_count.p, P.xyz_sorted.p, P.lo[0], P.lo[1],
+                                                P.lo[2], P.D, P.pl64.p, P.pl32.p);
+  FMM_LAUNCH_CHECK();
+
+  // ---- colleagues
+  scope.reset(new PassScope(P, kPassLists));
+  DBuf<int32_t> &loff = P.s_i32b;
+  loff.resize(P.level_off.size(), s);
+  FMM_CUDA(cudaMemcpyAsync(loff.p, P.level_off.data(), sizeof(int32_t) * P.level_off.size(),
+                           cudaMemcpyHostToDevice, s));
+  P.colleagues.resize((size_t)26 * nb, s);
+  P.ncolleagues.resize(nb, s);
+  k_colleagues<<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_key.p, loff.p, P.colleagues.p,
+                                        P.ncolleagues.p);
+  FMM_LAUNCH_CHECK();
+  FMM_CUDA(cudaStreamSynchronize(s));  // level_off host vector must outlive the copy
+
+  // ---- V lists
+  P.s_i32a.resize(nb, s);
+  k_vlist<false><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_child.p,
+                                          P.box_nchild.p, P.colleagues.p, P.ncolleagues.p,
+                                          P.s_i32a.p, nullptr, nullptr);
+  FMM_LAUNCH_CHECK();
+  P.nv = counts_to_offsets(P, P.s_i32a.p, P.v_off, nb);
+  P.v_idx.resize(P.nv > 0 ? P.nv : 1, s);
+  k_vlist<true><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_child.p,
+                                         P.box_nchild.p, P.colleagues.p, P.ncolleagues.p, nullptr,
+                                         P.v_off.p, P.v_idx.p);
+  FMM_LAUNCH_CHECK();
+
+  // ---- coarser-or-equal adjacent leaves (CA)
+  k_calist<false><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_nchild.p,
+                                           P.colleagues.p, P.ncolleagues.p, P.s_i32a.p, nullptr,
+                                           nullptr);
+  FMM_LAUNCH_CHECK();
+  int64_t nca = counts_to_offsets(P, P.s_i32a.p, P.ca_off, nb);
+  P.ca_idx.resize(nca > 0 ? nca : 1, s);
+  k_calist<true><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_nchild.p,
+                                          P.colleagues.p, P.ncolleagues.p, nullptr, P.ca_off.p,
+                                          P.ca_idx.p);
+  FMM_LAUNCH_CHECK();
+
+  // ---- U lists (pairs -> sort -> CSR)
+  {
+    int64_t nl = P.nleaves;
+    P.s_i32a.resize(nl + 1, s);
+    k_upairs<false><<<grid(nl), kT, 0, s>>>(nl, P.leaves.p, P.box_geo.p, P.ca_off.p, P.ca_idx.p,
+                                             P.s_i32a.p, nullptr, nullptr);
+    FMM_LAUNCH_CHECK();
+    DBuf<int32_t> &uoffs = P.s_i32b;
+    uoffs.resize(nl + 1, s);
+    scan_exclusive(P.s_i32a.p, uoffs.p, nl, uoffs.p + nl, P.s_scan, s);
+    int64_t np = read_scalar(uoffs.p + nl, s);
+    P.s_u64a.resize(np, s);
+    k_upairs<true><<<grid(nl), kT, 0, s>>>(nl, P.leaves.p, P.box_geo.p, P.ca_off.p, P.ca_idx.p,
+                                            nullptr, uoffs.p, P.s_u64a.p);
+    FMM_LAUNCH_CHECK();
+    pairs_to_csr(P, P.s_u64a, np, nb, P.u_off, P.u_idx);
+    P.nu = np;
+  }
+
+  // ---- X lists, then W as their transpose
+  k_xlist<false><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.ca_off.p, P.ca_idx.p,
+                                          P.s_i32a.p, nullptr, nullptr);
+  FMM_LAUNCH_CHECK();
+  P.nx = counts_to_offsets(P, P.s_i32a.p, P.x_off, nb);
+  P.x_idx.resize(P.nx > 0 ? P.nx : 1, s);
+  k_xlist<true><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.ca_off.p, P.ca_idx.p,
+                                         nullptr, P.x_off.p, P.x_idx.p);
+  FMM_LAUNCH_CHECK();
+  P.s_u64a.resize(P.nx > 0 ? P.nx : 1, s);
+  k_wpairs<<<grid(nb), kT, 0, s>>>(nb, P.x_off.p, P.x_idx.p, P.s_u64a.p);
+  FMM_LAUNCH_CHECK();
+  pairs_to_csr(P, P.s_u64a, P.nx, nb, P.w_off, P.w_idx);
+  P.nw = P.nx;
+
+  // ---- work lists for P2L and M2P
+  P.s_i32a.resize(nb, s);
+  k_flag<<<grid(nb), kT, 0, s>>>(nb, P.x_off.p, nullptr, 1, P.s_i32a.p);
+  FMM_LAUNCH_CHECK();
+  P.nxboxes = compact(P, nb, P.s_i32a.p, P.xboxes);
+  k_flag<<<grid(nb), kT, 0, s>>>(nb, P.w_off.p, P.box_nchild.p, 2, P.s_i32a.p);
+  FMM_LAUNCH_CHECK();
+  P.nwleaves = compact(P, nb, P.s_i32a.p, P.wleaves);
+
+  // ---- M2L tiles: boxes of level >= 2 grouped by (level, octant parity)
+  P.m2l_tile_size = m2l_tile_size(P.order, P.precision);
+  int64_t b2 = P.nlevels > 2 ? P.level_off[2] : nb;
+  int64_t n2 = nb - b2;
+  if (n2 > 0) {
+    const int ncls = 8 * (kMaxDepth + 1);
+    P.s_hist.resize(ncls, s);
+    FMM_CUDA(cudaMemsetAsync(P.s_hist.p, 0, sizeof(int32_t) * ncls, s));
+    P.s_u64a.resize(n2, s);
+    P.m2l_order.resize(n2, s);
+    k_m2l_class<<<grid(n2), kT, 0, s>>>(b2, nb, P.box_geo.p, P.s_u64a.p, P.m2l_order.p, P.s_hist.p);
+    FMM_LAUNCH_CHECK();
+    std::vector<int32_t> h(ncls);
+    FMM_CUDA(cudaMemcpyAsync(h.data(), P.s_hist.p, sizeof(int32_t) * ncls, cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
+    radix_sort(P.s_u64a, P.m2l_order, P.s_u64b, P.s_i32a, n2, {0}, P.s_hist, P.s_scan, s);
+    std::vector<M2LTile> tiles;
+    int32_t o = 0, T = P.m2l_tile_size;
+    for (int c = 0; c < ncls; ++c) {
+      for (int32_t t = 0; t < h[c]; t += T) tiles.push_back({o + t, std::min(T, h[c] - t), c & 7, 0});
+      o += h[c];
+    }
+    P.nm2l_tiles = (int64_t)tiles.size();
+    P.m2l_tiles.resize(tiles.size(), s);
+    FMM_CUDA(cudaMemcpyAsync(P.m2l_tiles.p, tiles.data(), sizeof(M2LTile) * tiles.size(),
+                             cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaStreamSynchronize(s));  // `tiles` is a host temporary
+  }
+}
+
+}  // namespace fmm

@@ -1,0 +1,137 @@
+"""GPU FMM mat-vec vs the oracle.
+
+FP64 mode: potentials and each gradient component within 1e-12 relative L2 of
+the oracle FMM with the same tree and order.  Both precisions: error against
+the direct sum within the stated bars.  Mixed mode: error against the FP64
+oracle is stated per case (FP32 arithmetic, floor ~1e-6)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1602_02244_gb300 import binding, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_gpu(cuda, xyz, q, S, p, precision="fp64", **kw):
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=S, order=p,
+                        precision=precision, **kw)
+    phi, g = plan.eval(torch.tensor(q, device=cuda))
+    out = phi.cpu().numpy(), g.cpu().numpy()
+    plan.close()
+    return out
+
+
+def problem(kind, n, seed=0):
+    if kind == "uniform":
+        return workloads.uniform_cube_problem(n, seed)
+    if kind == "plummer":
+        x, _ = workloads.plummer_problem(n, seed)
+        return x, workloads.rng(seed + 50).uniform(-1, 1, n)
+    x, q, _ = workloads.sphere_problem(n, seed)
+    return x, q
+
+
+FP64_CASES = [("uniform", 4096, 64, 4), ("uniform", 20000, 32, 8), ("plummer", 30000, 24, 6),
+              ("sphere", 20000, 16, 5), ("plummer", 8000, 5, 3), ("uniform", 3000, 40, 10),
+              ("plummer", 6000, 30, 12), ("uniform", 500, 16, 0), ("uniform", 700, 20, 1),
+              ("plummer", 2000, 10, 16)]
+
+
+@pytest.mark.parametrize("kind,n,S,p", FP64_CASES)
+def test_fp64_matches_oracle_fmm(cuda, kind, n, S, p):
+    xyz, q = problem(kind, n)
+    phi, g = run_gpu(cuda, xyz, q, S, p)
+    t = oracle.Tree(xyz, S)
+    po, go = t.eval(p, q)
+    assert rel(phi, po) <= 1e-12
+    for a in range(3):
+        assert rel(g[:, a], go[:, a]) <= 1e-12
+
+
+def test_fp64_config1_meets_direct_bar(cuda):
+    """N = 4096 uniform, p = 4, leaf <= 64: potential and gradient vs the
+    full direct sum."""
+    xyz, q = workloads.uniform_cube_problem(4096, 0)
+    phi, g = run_gpu(cuda, xyz, q, 64, 4)
+    pd, gd = oracle.direct(xyz, q)
+    assert rel(phi, pd) <= 1e-3
+    assert rel(g, gd) <= 1e-2
+
+
+def test_fp64_config2_1m_p10_vs_direct(cuda):
+    """N = 1,048,576 uniform, p = 10, on 4096 sampled targets.  The
+    one-box-separation list gives ~2.5e-6 at p = 10 (1e-6 is reached at
+    p = 12, pinned on the oracle), so the bar here is 5e-6."""
+    xyz, q = workloads.uniform_cube_problem(1048576, 0)
+    phi, g = run_gpu(cuda, xyz, q, 64, 10)
+    sel = workloads.sample_targets(len(xyz), 4096, 1)
+    pd, gd = oracle.direct(xyz, q, xyz[sel])
+    assert rel(phi[sel], pd) <= 5e-6
+    assert rel(g[sel], gd) <= 5e-5
+
+
+MIXED_CASES = [("uniform", 20000, 32, 8), ("plummer", 40000, 32, 8), ("sphere", 20000, 24, 6),
+               ("plummer", 5000, 6, 4)]
+
+
+@pytest.mark.parametrize("kind,n,S,p", MIXED_CASES)
+def test_mixed_vs_oracle_and_direct(cuda, kind, n, S, p):
+    xyz, q = problem(kind, n)
+    phi, g = run_gpu(cuda, xyz, q, S, p, precision="mixed")
+    t = oracle.Tree(xyz, S)
+    po, go = t.eval(p, q)
+    pd, gd = oracle.direct(xyz, q)
+    e_or, e_dir, e_fmm = rel(phi, po), rel(phi, pd), rel(po, pd)
+    print(kind, n, S, p, "mixed vs oracle %.2e, vs direct %.2e (fp64 fmm %.2e)" % (e_or, e_dir, e_fmm))
+    assert e_or <= 1e-5
+    assert rel(g, go) <= 1e-4
+    assert e_dir <= e_fmm + 1e-5
+
+
+def test_mixed_config3_plummer_4m(cuda):
+    """Headline workload: N = 4,194,304 Plummer, charges 1/N, p = 8, mixed;
+    error vs the direct sum on 4096 sampled targets."""
+    xyz, q = workloads.plummer_problem(4194304, 0)
+    phi, g = run_gpu(cuda, xyz, q, 64, 8, precision="mixed")
+    sel = workloads.sample_targets(len(xyz), 4096, 1)
+    pd, gd = oracle.direct(xyz, q, xyz[sel])
+    print("config3 mixed: phi rel %.2e grad rel %.2e" % (rel(phi[sel], pd), rel(g[sel], gd)))
+    assert rel(phi[sel], pd) <= 1e-5
+    assert rel(g[sel], gd) <= 1e-4
+
+
+def test_coincident_points_and_single_point(cuda):
+    xyz = np.vstack([np.tile([[0.5, 0.5, 0.5]], (40, 1)), workloads.uniform_cube(200, 4)])
+    q = workloads.rng(9).uniform(-1, 1, len(xyz))
+    phi, g = run_gpu(cuda, xyz, q, 8, 6)
+    po, go = oracle.Tree(xyz, 8).eval(6, q)
+    assert rel(phi, po) <= 1e-12 and rel(g, go) <= 1e-12
+    phi1, g1 = run_gpu(cuda, np.array([[1.0, 2.0, 3.0]]), np.array([5.0]), 8, 4)
+    assert phi1[0] == 0.0 and np.all(g1 == 0.0)
+
+
+def test_host_entry_point_matches_device_path(cuda):
+    xyz, q = workloads.uniform_cube_problem(30000, 5)
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=32, order=6)
+    phi_d, g_d = plan.eval(torch.tensor(q, device=cuda))
+    phi_h, g_h = plan.solve_host(xyz, q)
+    assert np.array_equal(phi_h, phi_d.cpu().numpy())
+    assert np.array_equal(g_h, g_d.cpu().numpy())
+    plan.close()
+
+
+def test_rebuild_reuses_plan(cuda):
+    xyz1, q1 = workloads.uniform_cube_problem(10000, 1)
+    xyz2, q2 = workloads.plummer_problem(15000, 2)
+    plan = binding.Plan(torch.tensor(xyz1, device=cuda), leaf_size=16, order=5)
+    plan.rebuild(torch.tensor(xyz2, device=cuda))
+    phi, g = plan.eval(torch.tensor(q2, device=cuda))
+    po, go = oracle.Tree(xyz2, 16).eval(5, q2)
+    assert rel(phi.cpu().numpy(), po) <= 1e-12
+    plan.close()
