@@ -149,6 +149,32 @@ fmm_status fmm_profile_read(fmm_plan_t plan, double ms[FMM_NPASS], int64_t launc
 /* Number of kernels this library has launched in this process so far. */
 uint64_t fmm_kernel_launches(void);
 
+/* Morton keys and their stable sort, allocating no device memory.
+ * The paper has no counterpart: this serves callers that cannot let a
+ * library call cudaMalloc -- e.g. a host application whose memory manager
+ * already holds all free device memory in its own pool, or a
+ * latency-critical loop that forbids cudaMalloc/cudaFree because they can
+ * synchronise the device and take unbounded time.
+ *   d_xyz  : device, n x 3 FP64 (input)
+ *   d_keys : device, uint64[n] (output) sorted Morton keys, the same as
+ *            fmm_plan_export array 0 of a plan built on d_xyz
+ *   d_perm : device, int32[n] (output) input index of each sorted key
+ *            (stable), the same as export array 1
+ *   h_root : host double[4] (output, may be NULL): lo_x, lo_y, lo_z, D
+ * Scratch comes from one fixed device array of this library (12,906,752
+ * bytes: room for FMM_NOALLOC_MAX_POINTS points) that every GPU loading the
+ * library holds until the process exits.  n above FMM_NOALLOC_MAX_POINTS is
+ * rejected with FMM_ERR_INVALID_ARG.  The first call on a device looks up
+ * the array's device address (once per device), so make that first call
+ * before any stream capture.  All calls share the array: calls that can
+ * overlap on the GPU (different streams, or different host threads on one
+ * device) race and must be serialised by the caller.  Synchronises `stream`
+ * (the root cube and the finiteness check are read back).
+ * Errors: INVALID_ARG, NONFINITE_INPUT, CUDA. */
+#define FMM_NOALLOC_MAX_POINTS 1048576
+fmm_status fmm_morton_sort_noalloc(const double *d_xyz, int64_t n, uint64_t *d_keys,
+                                   int32_t *d_perm, double *h_root, void *stream);
+
 /* Release the plan and all its device memory (synchronises its stream). */
 fmm_status fmm_plan_destroy(fmm_plan_t plan);
 

@@ -70,6 +70,8 @@ void check_opts(const fmm_opts *o) {
 
 }  // namespace
 
+fmm_status record_error(fmm_status s, const std::string &msg) { return fail(s, msg); }
+
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 

@@ -38,6 +38,9 @@ void note_launch();
     FMM_CUDA(cudaGetLastError());      \
   } while (0)
 
+// sets the message returned by fmm_last_error_message() and returns s
+fmm_status record_error(fmm_status s, const std::string &msg);
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------- device buffers

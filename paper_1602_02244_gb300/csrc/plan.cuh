@@ -136,6 +136,10 @@ struct PassScope {
 
 // tree.cu
 void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n);
+// root cube + Morton keys into caller memory: partial holds 7 x 1024 doubles,
+// geom 8 doubles (lo[3], D, non-finite flag); perm gets the identity
+void morton_keys_raw(const double *d_xyz, int64_t n, double *partial, double *geom, uint64_t *keys,
+                     int32_t *perm, cudaStream_t s);
 void set_points(fmm_plan_impl &P, const double *d_xyz);
 // operators.cu
 void build_operators(fmm_plan_impl &P);

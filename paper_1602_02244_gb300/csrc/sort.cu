@@ -187,6 +187,46 @@ void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *d_total
   FMM_LAUNCH_CHECK();
 }
 
+size_t scan_raw_tmp_elems(int64_t n) { return n > 0 ? (size_t)ceil_div(n, kScanTile) : 1; }
+
+size_t radix_raw_hist_elems(int64_t n) { return (size_t)256 * (n > 0 ? ceil_div(n, kRsTile) : 1); }
+
+void scan_exclusive_raw(const int32_t *in, int32_t *out, int64_t n, int32_t *d_total,
+                        int32_t *block_sums, cudaStream_t s) {
+  if (n <= 0) {
+    if (d_total) FMM_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int32_t), s));
+    return;
+  }
+  int nb = ceil_div(n, kScanTile);
+  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, n, block_sums);
+  FMM_LAUNCH_CHECK();
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(block_sums, nb, d_total);
+  FMM_LAUNCH_CHECK();
+  k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, out, n, block_sums);
+  FMM_LAUNCH_CHECK();
+}
+
+void radix_sort_raw(uint64_t *keys, int32_t *vals, uint64_t *tkeys, int32_t *tvals, int64_t n,
+                    const int *shifts, int nshifts, int32_t *hist, int32_t *scan_tmp,
+                    cudaStream_t s) {
+  if (n <= 1 || nshifts <= 0) return;
+  if (nshifts % 2 != 0) throw Error(FMM_ERR_INVALID_ARG, "radix_sort_raw needs an even pass count");
+  int nb = ceil_div(n, kRsTile);
+  for (int ip = 0; ip < nshifts; ++ip) {
+    const int sh = shifts[ip];
+    k_radix_hist<<<nb, kRsThreads, 0, s>>>(keys, n, sh, hist, nb);
+    FMM_LAUNCH_CHECK();
+    scan_exclusive_raw(hist, hist, (int64_t)256 * nb, nullptr, scan_tmp, s);
+    if (vals)
+      k_radix_scatter<true><<<nb, kRsThreads, 0, s>>>(keys, vals, n, sh, hist, nb, tkeys, tvals);
+    else
+      k_radix_scatter<false><<<nb, kRsThreads, 0, s>>>(keys, nullptr, n, sh, hist, nb, tkeys, nullptr);
+    FMM_LAUNCH_CHECK();
+    std::swap(keys, tkeys);
+    std::swap(vals, tvals);
+  }
+}
+
 std::vector<int> digit_shifts(int lo, int hi) {
   std::vector<int> v;
   for (int b = lo; b < hi; b += 8) v.push_back(b);

@@ -478,6 +478,18 @@ int32_t read_scalar(const int32_t *d, cudaStream_t s) {
   return h;
 }
 
+void morton_keys_raw(const double *d_xyz, int64_t n, double *partial, double *geom, uint64_t *keys,
+                     int32_t *perm, cudaStream_t s) {
+  if (n <= 0) return;
+  int nbb = std::min(ceil_div(n, kT * 8), 1024);
+  k_bbox_partial<<<nbb, kT, 0, s>>>(d_xyz, n, partial);
+  FMM_LAUNCH_CHECK();
+  k_bbox_final<<<1, 32, 0, s>>>(partial, nbb, geom);
+  FMM_LAUNCH_CHECK();
+  k_morton<<<grid(n), kT, 0, s>>>(d_xyz, n, geom, keys, perm);
+  FMM_LAUNCH_CHECK();
+}
+
 void set_points(fmm_plan_impl &P, const double *d_xyz) {
   cudaStream_t s = P.stream;
   int64_t n = P.n;
