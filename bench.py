@@ -49,10 +49,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4194304)
     ap.add_argument("--order", type=int, default=8)
-    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--leaf", type=int, default=0, help="leaf size; 0 = autotune (default)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--cpu-sample", type=int, default=131072,
-                    help="points in the oracle's CPU sample")
+    ap.add_argument("--cpu-sample", type=int, default=1048576,
+                    help="points in the oracle's CPU-baseline sample")
+    ap.add_argument("--ref-sample", type=int, default=262144,
+                    help="points per step of the reference arm (the CPU oracle)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true")
@@ -150,14 +152,15 @@ def run_reference(args):
         return
     import oracle
     from paper_1602_02244_gb300 import workloads
-    n = args.cpu_sample
+    n = args.ref_sample
+    leaf = args.leaf or 64
     xyz, q = workloads.plummer_problem(n, 0)
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle.Tree(xyz, args.leaf).eval(args.order, q)
+    for _ in range(min(args.warmup, 1)):
+        oracle.Tree(xyz, leaf).eval(args.order, q)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.Tree(xyz, args.leaf).eval(args.order, q)
+        oracle.Tree(xyz, leaf).eval(args.order, q)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     val = n / (ms / 1e3)
@@ -165,7 +168,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "Plummer N=%d (bounded CPU sample of the N=4,194,304 problem), "
-                                   "p=%d, leaf %d, FP64" % (n, args.order, args.leaf)},
+                                   "p=%d, leaf %d, FP64" % (n, args.order, leaf)},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle",
                              "sample": "Plummer N=%d per step: plan + FP64 FMM eval" % n},
@@ -174,6 +177,17 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------------- ours
+def max_over_ranks(value, world, device=None):
+    """Largest `value` over all ranks (the slowest replica sets the step time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def algorithmic_work(plan):
     """Per-step algorithmic work from the plan layout: P2P pairs (targets x
     U-list sources) and M2L matvecs (|V| pairs)."""
@@ -214,7 +228,8 @@ def run_ours(args):
     xyz_np, q_np = workloads.plummer_problem(n, rank)
     X = torch.tensor(xyz_np, device=dev)
     Q = torch.tensor(q_np, device=dev)
-    plan = binding.Plan(X, leaf_size=S, order=p, precision=args.precision)
+    plan = binding.Plan(X, leaf_size=S, order=p, precision=args.precision)  # S = 0: autotune
+    S = plan.sizes()["leaf_size"]
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     grad = torch.empty(n, 3, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -255,11 +270,7 @@ def run_ours(args):
     L.fmm_profile(plan._h, 0)
     pass_ms = {PASSES[i]: ms_arr[i] / args.steps for i in range(12)}
     pass_launch = {PASSES[i]: la_arr[i] / args.steps for i in range(12)}
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(step_ms)), world, dev)
     value = n * world / (ms / 1e3)
 
     # error statement: GPU result vs the direct sum on sampled targets
@@ -294,9 +305,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": "Plummer N=%d, charges 1/N, p=%d, leaf %d, %s precision; step = "
-                                   "plan (keys, sort, octree, U/V/W/X lists) + eval (phi and grad)"
-                                   % (n, p, S, args.precision),
+            "config": {"workload": "Plummer N=%d, charges 1/N, p=%d, leaf %d (%s), %s precision; "
+                                   "step = plan (keys, sort, octree, U/V/W/X lists) + eval (phi and "
+                                   "grad)" % (n, p, S, "autotuned" if args.leaf == 0 else "fixed",
+                                              args.precision),
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MB flush between steps; working set >> L2",
                        "boxes": sizes["nboxes"], "levels": sizes["nlevels"], "U": sizes["nu"],
@@ -344,11 +356,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             plan.solve_host_ptr(hx.data_ptr(), hq.data_ptr(), n, hphi.data_ptr(), hg.data_ptr())
-        t_e2e = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
         line["e2e"] = {"value": n * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                        "d2h_bytes_per_step": 32 * n, "ms": 1e3 * t_e2e}
 

@@ -71,13 +71,17 @@ typedef struct {
 
 /* Build a plan for n points (d_xyz: device, n x 3 FP64).
  *   leaf_size : a box holding more than leaf_size points splits (>= 1);
- *               a leaf exceeds it only at max_depth.
+ *               a leaf exceeds it only at max_depth.  0 = autotune: time
+ *               plan + mat-vec on these points for leaf sizes 16..512 and
+ *               keep the fastest (cached per size bucket, order and
+ *               precision for the life of the process; fmm_plan_rebuild of
+ *               an autotuned plan reuses the cache).
  *   order     : expansion order p = largest harmonic degree, 0..20;
  *               (p+1)^2 real coefficients per box.
  * The plan copies what it needs from d_xyz; d_xyz may be freed afterwards.
  * n == 0 gives a valid empty plan.  Synchronises `stream` (box counts per
  * level are read back to size the lists).
- * Errors: INVALID_ARG (n < 0, n >= 2^31, leaf_size < 1, order outside 0..20,
+ * Errors: INVALID_ARG (n < 0, n >= 2^31, leaf_size < 0, order outside 0..20,
  * bad opts, NULL out/d_xyz with n > 0), NONFINITE_INPUT, OOM, CUDA. */
 fmm_status fmm_plan_create(const double *d_xyz, int64_t n, int leaf_size, int order,
                            const fmm_opts *opts, void *stream, fmm_plan_t *out);

@@ -107,7 +107,9 @@ void release_plan(fmm_plan_impl &P) {
   P.adj_grad_w.release(); P.adj_grad_q.release(); P.adj_phi.release(); P.host_io.release();
   P.s_i32a.release(); P.s_i32b.release(); P.s_i32c.release(); P.s_hist.release();
   P.s_scan.release(); P.s_u64a.release(); P.s_u64b.release(); P.s_total.release();
-  P.ca_off.release(); P.ca_idx.release();
+  P.ca_off.release(); P.ca_idx.release(); P.m2l_src.release(); P.m2l_slots.release();
+  P.m2l_nslots.release(); P.ops.m2l32p.release();
+  P.xslot.release(); P.K64.release(); P.K32.release();
 }
 
 }  // namespace fmm
@@ -121,7 +123,7 @@ fmm_status fmm_plan_create(const double *d_xyz, int64_t n, int leaf_size, int or
   if (!out) return fail(FMM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n < 0 || n >= (int64_t(1) << 31)) return fail(FMM_ERR_INVALID_ARG, "n must be in [0, 2^31)");
-  if (leaf_size < 1) return fail(FMM_ERR_INVALID_ARG, "leaf_size must be >= 1");
+  if (leaf_size < 0) return fail(FMM_ERR_INVALID_ARG, "leaf_size must be >= 1 (or 0: autotune)");
   if (order < 0 || order > kMaxOrder) return fail(FMM_ERR_INVALID_ARG, "order must be in 0..20");
   if (n > 0 && !d_xyz) return fail(FMM_ERR_INVALID_ARG, "d_xyz is NULL");
   fmm_plan_s *P = nullptr;
@@ -129,13 +131,15 @@ fmm_status fmm_plan_create(const double *d_xyz, int64_t n, int leaf_size, int or
     check_opts(opts);
     P = new fmm_plan_s();
     P->order = order;
-    P->leaf_size = leaf_size;
+    P->leaf_size = leaf_size > 0 ? leaf_size : 64;
+    P->autotune = leaf_size == 0;
     P->stream = (cudaStream_t)stream;
     if (opts) {
       P->precision = opts->precision;
       P->coarse_fp64_levels = opts->coarse_fp64_levels == 0 ? 3 : opts->coarse_fp64_levels;
       P->max_depth = opts->max_depth == 0 ? kMaxDepth : opts->max_depth;
     }
+    if (P->autotune && n > 0) P->leaf_size = tuned_leaf_size(*P, d_xyz, n);
     build_tree(*P, d_xyz, n);
   });
   if (st != FMM_OK) {
@@ -156,6 +160,7 @@ fmm_status fmm_plan_rebuild(fmm_plan_t plan, const double *d_xyz, int64_t n, voi
   if (n > 0 && !d_xyz) return fail(FMM_ERR_INVALID_ARG, "d_xyz is NULL");
   return guarded([&] {
     plan->stream = (cudaStream_t)stream;
+    if (plan->autotune && n > 0) plan->leaf_size = tuned_leaf_size(*plan, d_xyz, n);
     build_tree(*plan, d_xyz, n);
   });
 }

@@ -116,6 +116,12 @@ __host__ __device__ inline uint64_t morton3(uint32_t ix, uint32_t iy, uint32_t i
 // --------------------------------------------------------- coefficients
 __host__ __device__ constexpr int ncoef(int p) { return (p + 1) * (p + 1); }
 __host__ __device__ constexpr int cidx(int n, int m) { return n * n + n + m; }
+// row pitch (in elements) of coefficient arrays and padded operators: a
+// multiple of 4 (16-byte rows for FP32) whose quarter is odd, so rows read as
+// float4 by consecutive threads fall in distinct shared-memory bank groups
+__host__ __device__ constexpr int coef_pitch(int p) {
+  return ((ncoef(p) + 3) / 4 % 2 == 1) ? (ncoef(p) + 3) / 4 * 4 : (ncoef(p) + 3) / 4 * 4 + 4;
+}
 
 // Box geometry record: integer anchor at its level and the level.
 struct __align__(16) BoxGeo {

@@ -7,13 +7,16 @@
 // in FP32 and keeps FP64 only for M2M/L2L into the coarsest levels
 // (<= coarse_fp64_levels) and for the per-target totals.
 #include "eval_kernels.cuh"
+#include <algorithm>
+
+#include "m2l_config.cuh"
 
 namespace fmm {
 
 namespace {
 
 void ensure_workspace(fmm_plan_impl &P, bool need64, bool need32) {
-  const size_t nc = (size_t)ncoef(P.order);
+  const size_t nc = (size_t)coef_pitch(P.order);  // row pitch of the coefficient arrays
   const size_t nb = (size_t)P.nboxes;
   cudaStream_t s = P.stream;
   P.far_acc.resize(4 * (size_t)P.n, s);
@@ -69,8 +72,10 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   }
   {
     PassScope ps_(P, kPassM2P);
-    launch_m2p<double>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.box_first.p, P.box_count.p,
-                       P.box_geo.p, P.src64.p, P.D, P.M64.p, n, P.far_acc.p, s);
+    P.K64.resize(std::max<size_t>(1, (size_t)P.nxboxes * 4 * coef_pitch(p + 1)), s);
+    launch_m2p<double>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.nxboxes, P.xboxes.p,
+                       P.xslot.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src64.p, P.D, P.M64.p,
+                       P.K64.p, n, P.far_acc.p, s);
   }
   {
     PassScope ps_(P, kPassP2P);
@@ -116,15 +121,19 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   }
   {
     PassScope ps_(P, kPassM2L);
-    launch_m2l<float>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_order.p, P.v_off.p,
-                      P.v_idx.p, P.box_geo.p, P.M32.p, P.ops.m2l32.p, P.L32.p, s);
+    if (p <= kM2LStagedMaxOrder)
+      launch_m2l_staged(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_src.p, P.m2l_slots.p, P.m2l_nslots.p,
+                        P.m2l_order.p, P.M32.p, P.ops.m2l32p.p, P.L32.p, s);
+    else
+      launch_m2l<float>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_order.p, P.v_off.p,
+                        P.v_idx.p, P.box_geo.p, P.M32.p, P.ops.m2l32.p, P.L32.p, s);
   }
   {
     PassScope ps_(P, kPassP2L);
     launch_p2l<float>(p, P.nxboxes, P.xboxes.p, P.x_off.p, P.x_idx.p, P.box_first.p, P.box_count.p,
                       P.box_geo.p, P.src32.p, P.D, P.L32.p, s);
   }
-  const size_t nc = (size_t)ncoef(p);
+  const size_t nc = (size_t)coef_pitch(p);
   if (coarse && P.nlevels > 2) {
     const size_t b0 = (size_t)P.level_off[2], b1 = (size_t)P.level_off[3];
     PassScope ps_(P, kPassL2L);
@@ -148,8 +157,10 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   }
   {
     PassScope ps_(P, kPassM2P);
-    launch_m2p<float>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.box_first.p, P.box_count.p,
-                      P.box_geo.p, P.src32.p, P.D, P.M32.p, n, P.far_acc.p, s);
+    P.K32.resize(std::max<size_t>(1, (size_t)P.nxboxes * 4 * coef_pitch(p + 1)), s);
+    launch_m2p<float>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.nxboxes, P.xboxes.p,
+                      P.xslot.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p, P.D, P.M32.p,
+                      P.K32.p, n, P.far_acc.p, s);
   }
   {
     PassScope ps_(P, kPassP2P);

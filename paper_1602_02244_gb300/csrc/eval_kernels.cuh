@@ -40,11 +40,12 @@ template <typename T>
 void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
                 const T *L, int64_t n, double *far, cudaStream_t s);
+// M2P over W lists; K is scratch of 4 * coef_pitch(p+1) per X box (the W sources)
 template <typename T>
 void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, const int32_t *widx,
-                const int32_t *first, const int32_t *count, const BoxGeo *geo,
-                const typename V4<T>::type *src, double D, const T *M, int64_t n, double *far,
-                cudaStream_t s);
+                int64_t nx, const int32_t *xboxes, const int32_t *xslot, const int32_t *first,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const T *M, T *K, int64_t n, double *far, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *perm, const double *far, const double *near,
                     double *phi, double *grad, cudaStream_t s);
 void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double *gq,
@@ -55,6 +56,10 @@ template <typename T>
 void launch_m2l(int p, int64_t ntiles, const M2LTile *tiles, int tile, const int32_t *order,
                 const int32_t *voff, const int32_t *vidx, const BoxGeo *geo, const T *M,
                 const T *ops, T *L, cudaStream_t s);
+
+void launch_m2l_staged(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *table,
+                       const int16_t *slots, const int32_t *nslots, const int32_t *order,
+                       const float *M, const float *opsp, float *L, cudaStream_t s);
 
 // p2p.cu
 template <typename T>

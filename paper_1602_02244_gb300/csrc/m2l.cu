@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kM2LThreads)
   int32_t *used = src + 216 * TILE;                           // [216]
   int32_t *tgt = used + 216;                                  // [TILE]
 
-  const int nc = ncoef(p);
+  const int nc = ncoef(p), ld = coef_pitch(p);
   const M2LTile tile = tiles[blockIdx.x];
   const int tid = threadIdx.x;
   for (int i = tid; i < 216 * TILE; i += kM2LThreads) src[i] = -1;
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kM2LThreads)
       for (int i = tid; i < KC * TILE; i += kM2LThreads) {
         const int t = i / KC, k = i - t * KC;
         const int32_t A = src[slot * TILE + t];
-        Ms[k * MP + t] = (A >= 0 && kc + k < nc) ? M[(size_t)A * nc + kc + k] : T(0);
+        Ms[k * MP + t] = (A >= 0 && kc + k < nc) ? M[(size_t)A * ld + kc + k] : T(0);
       }
       __syncthreads();
 #pragma unroll 4
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kM2LThreads)
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
         const int r = rg + RG * i;
-        if (r < nc) L[(size_t)B * nc + r] = acc[j][i];
+        if (r < nc) L[(size_t)B * ld + r] = acc[j][i];
       }
     }
   }
@@ -119,6 +119,165 @@ void run(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *order, cons
   auto kern = k_m2l<T, TILE, TPT, RPT>;
   FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<(unsigned)ntiles, kM2LThreads, smem, s>>>(p, tiles, order, voff, vidx, geo, M, ops, L);
+  FMM_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------ plan-time tables
+// One CTA per tile: src[tile][slot][t] = source box of target t in that slot
+// (-1 if none) and the ascending list of occupied slots.
+__global__ void k_m2l_table(int tile_size, const M2LTile *__restrict__ tiles,
+                            const int32_t *__restrict__ order, const int32_t *__restrict__ voff,
+                            const int32_t *__restrict__ vidx, const BoxGeo *__restrict__ geo,
+                            int32_t *__restrict__ table, int16_t *__restrict__ slots,
+                            int32_t *__restrict__ nslots) {
+  __shared__ int32_t used[216];
+  const M2LTile tile = tiles[blockIdx.x];
+  int32_t *tab = table + (size_t)blockIdx.x * 216 * tile_size;
+  for (int i = threadIdx.x; i < 216 * tile_size; i += blockDim.x) tab[i] = -1;
+  for (int i = threadIdx.x; i < 216; i += blockDim.x) used[i] = 0;
+  __syncthreads();
+  const int px = tile.parity & 1, py = (tile.parity >> 1) & 1, pz = (tile.parity >> 2) & 1;
+  for (int t = threadIdx.x >> 5; t < tile.count; t += blockDim.x >> 5) {
+    const int32_t B = order[tile.start + t];
+    const BoxGeo gb = geo[B];
+    for (int32_t e = voff[B] + (threadIdx.x & 31); e < voff[B + 1]; e += 32) {
+      const int32_t A = vidx[e];
+      const BoxGeo ga = geo[A];
+      const int sx = ga.ix - gb.ix + 2 + px, sy = ga.iy - gb.iy + 2 + py, sz = ga.iz - gb.iz + 2 + pz;
+      if ((unsigned)sx < 6u && (unsigned)sy < 6u && (unsigned)sz < 6u) {  // always, by construction
+        const int slot = (sx * 6 + sy) * 6 + sz;
+        tab[slot * tile_size + t] = A;
+        used[slot] = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // compact the occupied slots in order
+    int base = 0;
+    for (int s0 = 0; s0 < 216; s0 += 32) {
+      const int sl = s0 + threadIdx.x;
+      const bool u = sl < 216 && used[sl];
+      const unsigned mask = __ballot_sync(0xffffffffu, u);
+      if (u) slots[(size_t)blockIdx.x * 216 + base + __popc(mask & ((1u << threadIdx.x) - 1u))] = (int16_t)sl;
+      base += __popc(mask);
+    }
+    if (threadIdx.x == 0) nslots[blockIdx.x] = base;
+  }
+}
+
+// ------------------------------------------------- staged FP32 M2L kernel
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+constexpr int kStagedTile = 64, kStagedTPT = 4, kStagedRG = 16;
+
+// Per occupied slot: the slot's padded operator rows [NCP][ld] and the 64
+// targets' source multipoles [64][ld] are copied into one of two shared
+// stages with cp.async while the other stage is contracted; each thread owns
+// 4 targets x RPT rows and reads both operands as float4 along k.
+template <int RPT>
+__global__ void __launch_bounds__(kM2LThreads)
+    k_m2l_staged(int p, const M2LTile *__restrict__ tiles, const int32_t *__restrict__ table,
+                 const int16_t *__restrict__ slots, const int32_t *__restrict__ nslots,
+                 const int32_t *__restrict__ order, const float *__restrict__ M,
+                 const float *__restrict__ opsp, float *__restrict__ L) {
+  constexpr int NCP = kStagedRG * RPT;
+  constexpr int TILE = kStagedTile, TPT = kStagedTPT;
+  extern __shared__ float4 smem4[];
+  float *sm = reinterpret_cast<float *>(smem4);
+  const int nc = ncoef(p), ld = coef_pitch(p), cpr = ld / 4;
+  const int stage = (NCP + TILE) * ld;
+  const int tid = threadIdx.x, rg = tid % kStagedRG, tg = tid / kStagedRG;
+  const M2LTile tile = tiles[blockIdx.x];
+  const int ns = nslots[blockIdx.x];
+  const int px = tile.parity & 1, py = (tile.parity >> 1) & 1, pz = (tile.parity >> 2) & 1;
+  const int32_t *tab = table + (size_t)blockIdx.x * 216 * TILE;
+  const int16_t *sl = slots + (size_t)blockIdx.x * 216;
+
+  auto issue = [&](int j, int buf) {
+    const int slot = sl[j];
+    const int sx = slot / 36, sy = (slot / 6) % 6, sz = slot % 6;
+    const int code = (2 + px - sx + 3) * 49 + (2 + py - sy + 3) * 7 + (2 + pz - sz + 3);
+    const float *op = opsp + (size_t)code * NCP * ld;
+    float *Ts = sm + buf * stage;
+    float *Ms = Ts + NCP * ld;
+    for (int c = tid; c < NCP * cpr; c += kM2LThreads) cp_async16(Ts + 4 * c, op + 4 * c, 16);
+    for (int c = tid; c < TILE * cpr; c += kM2LThreads) {
+      const int t = c / cpr, kk = c - t * cpr;
+      const int32_t A = tab[slot * TILE + t];
+      cp_async16(Ms + t * ld + 4 * kk, A >= 0 ? M + (size_t)A * ld + 4 * kk : M, A >= 0 ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+
+  float acc[TPT][RPT];
+#pragma unroll
+  for (int j = 0; j < TPT; ++j)
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) acc[j][i] = 0.f;
+
+  if (ns > 0) issue(0, 0);
+  for (int j = 0; j < ns; ++j) {
+    if (j + 1 < ns) {
+      issue(j + 1, (j + 1) & 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float *Ts = sm + (j & 1) * stage;
+    const float *Ms = Ts + NCP * ld;
+#pragma unroll 3
+    for (int k4 = 0; k4 < cpr; ++k4) {
+      float4 mv[TPT], tv[RPT];
+#pragma unroll
+      for (int q = 0; q < TPT; ++q)
+        mv[q] = *reinterpret_cast<const float4 *>(Ms + (tg * TPT + q) * ld + 4 * k4);
+#pragma unroll
+      for (int i = 0; i < RPT; ++i)
+        tv[i] = *reinterpret_cast<const float4 *>(Ts + (rg + kStagedRG * i) * ld + 4 * k4);
+#pragma unroll
+      for (int q = 0; q < TPT; ++q)
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          float a = acc[q][i];
+          a = fmaf(tv[i].x, mv[q].x, a);
+          a = fmaf(tv[i].y, mv[q].y, a);
+          a = fmaf(tv[i].z, mv[q].z, a);
+          a = fmaf(tv[i].w, mv[q].w, a);
+          acc[q][i] = a;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const int t = tg * TPT + q;
+    if (t < tile.count) {
+      const int32_t B = order[tile.start + t];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int r = rg + kStagedRG * i;
+        if (r < nc) L[(size_t)B * ld + r] = acc[q][i];
+      }
+    }
+  }
+}
+
+template <int RPT>
+void run_staged(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *table,
+                const int16_t *slots, const int32_t *nslots, const int32_t *order, const float *M,
+                const float *opsp, float *L, cudaStream_t s) {
+  constexpr int NCP = kStagedRG * RPT;
+  const size_t smem = 2 * sizeof(float) * (size_t)(NCP + kStagedTile) * coef_pitch(p);
+  auto kern = k_m2l_staged<RPT>;
+  FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)ntiles, kM2LThreads, smem, s>>>(p, tiles, table, slots, nslots, order, M, opsp, L);
   FMM_LAUNCH_CHECK();
 }
 
@@ -144,6 +303,36 @@ void launch_m2l(int p, int64_t ntiles, const M2LTile *tiles, int tile, const int
   FMM_M2L_CASE(16, 1, 28)
 #undef FMM_M2L_CASE
   throw Error(FMM_ERR_UNSUPPORTED, "no M2L tile shape for this order");
+}
+
+void launch_m2l_staged(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *table,
+                       const int16_t *slots, const int32_t *nslots, const int32_t *order,
+                       const float *M, const float *opsp, float *L, cudaStream_t s) {
+  if (ntiles == 0) return;
+  switch (m2l_rows(p) / kStagedRG) {
+    case 1: return run_staged<1>(p, ntiles, tiles, table, slots, nslots, order, M, opsp, L, s);
+    case 2: return run_staged<2>(p, ntiles, tiles, table, slots, nslots, order, M, opsp, L, s);
+    case 3: return run_staged<3>(p, ntiles, tiles, table, slots, nslots, order, M, opsp, L, s);
+    case 4: return run_staged<4>(p, ntiles, tiles, table, slots, nslots, order, M, opsp, L, s);
+    case 5: return run_staged<5>(p, ntiles, tiles, table, slots, nslots, order, M, opsp, L, s);
+    case 6: return run_staged<6>(p, ntiles, tiles, table, slots, nslots, order, M, opsp, L, s);
+    case 7: return run_staged<7>(p, ntiles, tiles, table, slots, nslots, order, M, opsp, L, s);
+    case 8: return run_staged<8>(p, ntiles, tiles, table, slots, nslots, order, M, opsp, L, s);
+  }
+  throw Error(FMM_ERR_UNSUPPORTED, "staged M2L supports orders up to 10");
+}
+
+void build_m2l_tables(fmm_plan_impl &P) {
+  cudaStream_t s = P.stream;
+  const int64_t nt = P.nm2l_tiles;
+  if (nt == 0) return;
+  P.m2l_src.resize((size_t)nt * 216 * P.m2l_tile_size, s);
+  P.m2l_slots.resize((size_t)nt * 216, s);
+  P.m2l_nslots.resize((size_t)nt, s);
+  k_m2l_table<<<(unsigned)nt, 256, 0, s>>>(P.m2l_tile_size, P.m2l_tiles.p, P.m2l_order.p, P.v_off.p,
+                                            P.v_idx.p, P.box_geo.p, P.m2l_src.p, P.m2l_slots.p,
+                                            P.m2l_nslots.p);
+  FMM_LAUNCH_CHECK();
 }
 
 template void launch_m2l<float>(int, int64_t, const M2LTile *, int, const int32_t *, const int32_t *,

@@ -32,4 +32,9 @@ inline M2LShape m2l_shape(int order) {
 
 inline int m2l_tile_size(int order, int /*precision*/) { return m2l_shape(order).tile; }
 
+// Staged FP32 kernel (orders up to 10): 64 targets x 16*RPT rows per CTA,
+// one whole slot (operator + gathered multipoles) per pipeline stage.
+constexpr int kM2LStagedMaxOrder = 10;
+__host__ __device__ constexpr int m2l_rows(int order) { return (ncoef(order) + 15) / 16 * 16; }
+
 }  // namespace fmm

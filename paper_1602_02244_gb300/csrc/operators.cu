@@ -19,6 +19,7 @@
 #include <complex>
 #include <vector>
 
+#include "m2l_config.cuh"
 #include "plan.cuh"
 
 namespace fmm {
@@ -158,6 +159,19 @@ void build_operators(fmm_plan_impl &P) {
     FMM_CUDA(cudaStreamSynchronize(s));  // host vectors are reused
   };
   up(m2l, P.ops.m2l64, P.ops.m2l32);
+  if (p <= kM2LStagedMaxOrder) {  // padded output-major FP32 copy for the staged kernel
+    const int rows = m2l_rows(p), ld = coef_pitch(p);
+    const size_t slab = (size_t)rows * ld;
+    std::vector<float> padded(343 * slab, 0.f);
+    for (int code = 0; code < 343; ++code)
+      for (int r = 0; r < nc; ++r)
+        for (int k = 0; k < nc; ++k)
+          padded[code * slab + (size_t)r * ld + k] = (float)m2l[code * nn + (size_t)k * nc + r];
+    P.ops.m2l32p.resize(padded.size(), s);
+    FMM_CUDA(cudaMemcpyAsync(P.ops.m2l32p.p, padded.data(), padded.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
+  }
   up(m2m, P.ops.m2m64, P.ops.m2m32);
   up(l2l, P.ops.l2l64, P.ops.l2l32);
   P.ops.order = p;

@@ -40,7 +40,7 @@ __global__ void k_p2m(int p, int64_t nleaves, const int32_t *__restrict__ leaves
                       const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
                       double D, T *__restrict__ M, double *__restrict__ M64, int coarse) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nc = ncoef(p), pitch = 33, lane = threadIdx.x & 31;
+  const int nc = ncoef(p), ld = coef_pitch(p), pitch = 33, lane = threadIdx.x & 31;
   T *buf = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * nc * pitch;
   int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= nleaves) return;
@@ -76,11 +76,11 @@ __global__ void k_p2m(int p, int64_t nleaves, const int32_t *__restrict__ leaves
     __syncwarp();
   }
 #pragma unroll
-  for (int t = 0; t < kAccSlots; ++t) {
+  for (int t = 0; t < kAccSlots; ++t) {  // the row padding is written as zero
     const int k = lane + 32 * t;
-    if (k < nc) {
-      M[(int64_t)b * nc + k] = acc[t];
-      if (M64 && g.level <= coarse) M64[(int64_t)b * nc + k] = (double)acc[t];
+    if (k < ld) {
+      M[(int64_t)b * ld + k] = acc[t];
+      if (M64 && g.level <= coarse) M64[(int64_t)b * ld + k] = (double)acc[t];
     }
   }
 }
@@ -93,7 +93,7 @@ __global__ void k_p2l(int p, int64_t nboxes_x, const int32_t *__restrict__ xboxe
                       const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
                       double D, T *__restrict__ L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nc = ncoef(p), pitch = 33, lane = threadIdx.x & 31;
+  const int nc = ncoef(p), ld = coef_pitch(p), pitch = 33, lane = threadIdx.x & 31;
   T *buf = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * nc * pitch;
   int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= nboxes_x) return;
@@ -140,7 +140,7 @@ __global__ void k_p2l(int p, int64_t nboxes_x, const int32_t *__restrict__ xboxe
 #pragma unroll
   for (int t = 0; t < kAccSlots; ++t) {
     const int k = lane + 32 * t;
-    if (k < nc) L[(int64_t)C * nc + k] += acc[t];
+    if (k < nc) L[(int64_t)C * ld + k] += acc[t];
   }
 }
 
@@ -162,23 +162,25 @@ __global__ void k_m2m(int p, int32_t b0, int32_t nbl, const int32_t *__restrict_
                       const int32_t *__restrict__ nchild, const BoxGeo *__restrict__ geo,
                       const Tin *__restrict__ Mc, const Top *__restrict__ ops, Tout *__restrict__ Mp,
                       float *__restrict__ Mp32) {
-  const int nc = ncoef(p);
+  const int nc = ncoef(p), ld = coef_pitch(p);
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nbl * nc) return;
-  const int32_t b = b0 + (int32_t)(t / nc);
-  const int r = (int)(t % nc);
+  if (t >= (int64_t)nbl * ld) return;
+  const int32_t b = b0 + (int32_t)(t / ld);
+  const int r = (int)(t % ld);
   const int nch = nchild[b];
   if (nch == 0) return;
-  const int kmax = ncoef(degree_of(r));
   Tacc acc = Tacc(0);
-  const int32_t c0 = child[b];
-  for (int32_t cc = c0; cc < c0 + nch; ++cc) {
-    const Top *row = ops + ((size_t)octant(geo[cc]) * nc + r) * nc;
-    const Tin *m = Mc + (int64_t)cc * nc;
-    for (int k = 0; k < kmax; ++k) acc += (Tacc)row[k] * (Tacc)m[k];
+  if (r < nc) {  // the row padding is written as zero
+    const int kmax = ncoef(degree_of(r));
+    const int32_t c0 = child[b];
+    for (int32_t cc = c0; cc < c0 + nch; ++cc) {
+      const Top *row = ops + ((size_t)octant(geo[cc]) * nc + r) * nc;
+      const Tin *m = Mc + (int64_t)cc * ld;
+      for (int k = 0; k < kmax; ++k) acc += (Tacc)row[k] * (Tacc)m[k];
+    }
   }
-  Mp[(int64_t)b * nc + r] = (Tout)acc;
-  if (Mp32) Mp32[(int64_t)b * nc + r] = (float)acc;
+  Mp[(int64_t)b * ld + r] = (Tout)acc;
+  if (Mp32) Mp32[(int64_t)b * ld + r] = (float)acc;
 }
 
 // L2L into the boxes of one level: L(child) = L_self(child) + T(octant) L(parent);
@@ -187,7 +189,7 @@ template <typename Tself, typename Tpar, typename Tout, typename Top, typename T
 __global__ void k_l2l(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ parent,
                       const BoxGeo *__restrict__ geo, const Tself *Lself, const Tpar *Lpar,
                       const Top *__restrict__ ops, Tout *Lout, float *Lout32) {
-  const int nc = ncoef(p);
+  const int nc = ncoef(p), ld = coef_pitch(p);
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)nbl * nc) return;
   const int32_t b = b0 + (int32_t)(t / nc);
@@ -195,11 +197,11 @@ __global__ void k_l2l(int p, int32_t b0, int32_t nbl, const int32_t *__restrict_
   const int32_t P = parent[b];
   const int n = degree_of(r);
   const Top *row = ops + ((size_t)octant(geo[b]) * nc + r) * nc;
-  const Tpar *lp = Lpar + (int64_t)P * nc;
-  Tacc acc = (Tacc)Lself[(int64_t)b * nc + r];
+  const Tpar *lp = Lpar + (int64_t)P * ld;
+  Tacc acc = (Tacc)Lself[(int64_t)b * ld + r];
   for (int k = n * n; k < nc; ++k) acc += (Tacc)row[k] * (Tacc)lp[k];
-  Lout[(int64_t)b * nc + r] = (Tout)acc;
-  if (Lout32) Lout32[(int64_t)b * nc + r] = (float)acc;
+  Lout[(int64_t)b * ld + r] = (Tout)acc;
+  if (Lout32) Lout32[(int64_t)b * ld + r] = (float)acc;
 }
 
 template <typename Tin>
@@ -228,7 +230,7 @@ __global__ void k_l2p(int p, const int32_t *__restrict__ leaves, const int32_t *
       for (int a = 0; a < 4; ++a) far[a * n + i] = 0.0;
     return;
   }
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) Ls[k] = L[(int64_t)b * nc + k];
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) Ls[k] = L[(int64_t)b * coef_pitch(p) + k];
   __syncthreads();
   const double a = box_side(D, g.level);
   const T inva = (T)(1.0 / a);
@@ -260,71 +262,125 @@ __global__ void k_l2p(int p, const int32_t *__restrict__ leaves, const int32_t *
   }
 }
 
-// M2P over W lists: phi += (1/a_A) sum M^ I(u), u = (x - c_A)/a_A, gradient from
-// d/dz I_n^m = -I_{n+1}^m, d/dx I_n^m = (I_{n+1}^{m+1} - I_{n+1}^{m-1})/2,
-// d/dy I_n^m = -i (I_{n+1}^{m+1} + I_{n+1}^{m-1})/2, regrouped per I_n^m.
+// M2P over W lists: phi += (1/a_A) sum M^ I(u), u = (x - c_A)/a_A.  The
+// gradient uses d/dz I_n^m = -I_{n+1}^m, d/dx I_n^m = (I_{n+1}^{m+1} - I_{n+1}^{m-1})/2,
+// d/dy I_n^m = -i (I_{n+1}^{m+1} + I_{n+1}^{m-1})/2; regrouped per I_n^m they are
+// expansions of degree p+1 with coefficients
+//   Kz_n^m = -M_{n-1}^m,  Kx_n^m = (M_{n-1}^{m-1} - M_{n-1}^{m+1})/2,
+//   Ky_n^m = -i (M_{n-1}^{m-1} + M_{n-1}^{m+1})/2,
+// which obey the same X_n^{-m} = (-1)^m conj(X_n^m) symmetry.  A prepass writes
+// (M, Kx, Ky, Kz) of every W source box in the real layout (pitch
+// coef_pitch(p+1)); the evaluation is then four branch-free dot products.
 template <typename T>
-__global__ void k_m2p(int p, const int32_t *__restrict__ wleaves, const int32_t *__restrict__ woff,
-                      const int32_t *__restrict__ widx, const int32_t *__restrict__ first,
-                      const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
-                      const typename V4<T>::type *__restrict__ src, double D,
-                      const T *__restrict__ M, int64_t n, double *__restrict__ far) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *Ms = reinterpret_cast<T *>(smem_raw);
-  const int nc = ncoef(p);
+__global__ void k_m2p_prep(int p, int64_t nx, const int32_t *__restrict__ xboxes,
+                           const T *__restrict__ M, T *__restrict__ K) {
+  const int ld = coef_pitch(p), ld1 = coef_pitch(p + 1), nc1 = ncoef(p + 1);
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nx * nc1) return;
+  const int64_t j = t / nc1;
+  const int r = (int)(t % nc1);
+  const T *Ma = M + (int64_t)xboxes[j] * ld;
+  int n = (int)sqrtf((float)r);
+  while (n * n > r) --n;
+  while ((n + 1) * (n + 1) <= r) ++n;
+  const int mm = r - n * n - n;       // signed index of this slot
+  const int m = mm < 0 ? -mm : mm;    // the slot holds Re (mm >= 0) or Im (mm < 0) of X_n^m
+  const bool im_part = mm < 0;
+  T k0 = 0, kx = 0, ky = 0, kz = 0;
+  T ar, ai, br, bi, cr, ci;
+  if (n <= p) {
+    cget(Ma, p, n, m, ar, ai);
+    k0 = im_part ? ai : ar;
+  }
+  cget(Ma, p, n - 1, m, ar, ai);
+  cget(Ma, p, n - 1, m - 1, br, bi);
+  cget(Ma, p, n - 1, m + 1, cr, ci);
+  kz = -(im_part ? ai : ar);
+  kx = T(0.5) * (im_part ? (bi - ci) : (br - cr));
+  ky = im_part ? T(-0.5) * (br + cr) : T(0.5) * (bi + ci);
+  T *Kj = K + j * 4 * ld1;
+  Kj[r] = k0;
+  Kj[ld1 + r] = kx;
+  Kj[2 * ld1 + r] = ky;
+  Kj[3 * ld1 + r] = kz;
+}
+
+// One CTA per target leaf; k = floor(128 / targets) threads share a target and
+// split its W list; partial sums are combined in FP64.
+constexpr int kM2PThreads = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kM2PThreads)
+    k_m2p(int p, const int32_t *__restrict__ wleaves, const int32_t *__restrict__ woff,
+          const int32_t *__restrict__ widx, const int32_t *__restrict__ xslot,
+          const int32_t *__restrict__ first, const int32_t *__restrict__ count,
+          const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src, double D,
+          const T *__restrict__ K, int64_t n, double *__restrict__ far) {
+  __shared__ double red[4][kM2PThreads];
+  const int tid = threadIdx.x, ld1 = coef_pitch(p + 1);
   const int32_t B = wleaves[blockIdx.x];
   const BoxGeo gb = geo[B];
-  const int32_t f = first[B], c = count[B];
-  for (int32_t i0 = 0; i0 < c; i0 += blockDim.x) {
-    const int32_t i = f + i0 + threadIdx.x;
-    const bool act = i0 + (int32_t)threadIdx.x < c;
-    typename V4<T>::type s;
-    if (act) s = src[i];
+  const int32_t f = first[B], c = count[B], e0 = woff[B], e1 = woff[B + 1];
+  for (int32_t tc = 0; tc < c; tc += kM2PThreads) {
+    const int tcount = min(kM2PThreads, c - tc);
+    const int k = max(1, min(min(32, kM2PThreads / tcount), e1 - e0));
+    const int ti = tid / k, sl = tid - ti * k;
     double phi = 0, gx = 0, gy = 0, gz = 0;
-    for (int32_t e = woff[B]; e < woff[B + 1]; ++e) {
-      const int32_t A = widx[e];
-      __syncthreads();
-      for (int k = threadIdx.x; k < nc; k += blockDim.x) Ms[k] = M[(int64_t)A * nc + k];
-      __syncthreads();
-      if (!act) continue;
-      const BoxGeo ga = geo[A];
-      const double aa = box_side(D, ga.level);
-      const T inva = (T)(1.0 / aa);
-      const T sx = (T)center_delta(gb.ix, gb.level, ga.ix, ga.level, D);
-      const T sy = (T)center_delta(gb.iy, gb.level, ga.iy, ga.level, D);
-      const T sz = (T)center_delta(gb.iz, gb.level, ga.iz, ga.level, D);
-      T fp = 0, fx = 0, fy = 0, fz = 0;
-      irregular_stream<T>(p + 1, (s.x + sx) * inva, (s.y + sy) * inva, (s.z + sz) * inva,
-                          [&](int nn, int m, T re, T im) {
-                            const T w = m ? T(2) : T(1);
-                            T ar, ai, br, bi, cr, ci;
-                            if (nn <= p) {
-                              cget(Ms, p, nn, m, ar, ai);
-                              fp += w * (ar * re - ai * im);
-                            }
-                            if (nn >= 1) {
-                              cget(Ms, p, nn - 1, m, ar, ai);
-                              fz -= w * (ar * re - ai * im);
-                              cget(Ms, p, nn - 1, m - 1, br, bi);
-                              cget(Ms, p, nn - 1, m + 1, cr, ci);
-                              const T gr = T(0.5) * (br - cr), gi = T(0.5) * (bi - ci);
-                              fx += w * (gr * re - gi * im);
-                              const T hr = T(0.5) * (bi + ci), hi = T(-0.5) * (br + cr);
-                              fy += w * (hr * re - hi * im);
-                            }
-                          });
-      const double ia = 1.0 / aa;
-      phi += (double)fp * ia;
-      gx += (double)fx * ia * ia;
-      gy += (double)fy * ia * ia;
-      gz += (double)fz * ia * ia;
+    if (ti < tcount) {
+      const typename V4<T>::type s = src[f + tc + ti];
+      for (int32_t e = e0 + sl; e < e1; e += k) {
+        const int32_t A = widx[e];
+        const BoxGeo ga = geo[A];
+        const double aa = box_side(D, ga.level);
+        const T inva = (T)(1.0 / aa);
+        const T sx = (T)center_delta(gb.ix, gb.level, ga.ix, ga.level, D);
+        const T sy = (T)center_delta(gb.iy, gb.level, ga.iy, ga.level, D);
+        const T sz = (T)center_delta(gb.iz, gb.level, ga.iz, ga.level, D);
+        const T *K0 = K + (int64_t)xslot[A] * 4 * ld1;
+        const T *Kx = K0 + ld1, *Ky = K0 + 2 * ld1, *Kz = K0 + 3 * ld1;
+        T fp = 0, fx = 0, fy = 0, fz = 0;
+        irregular_stream<T>(p + 1, (s.x + sx) * inva, (s.y + sy) * inva, (s.z + sz) * inva,
+                            [&](int nn, int m, T re, T im) {
+                              const int rp = cidx(nn, m), rn = cidx(nn, -m);
+                              if (m == 0) {
+                                fp += K0[rp] * re;
+                                fx += Kx[rp] * re;
+                                fy += Ky[rp] * re;
+                                fz += Kz[rp] * re;
+                              } else {
+                                fp += T(2) * (K0[rp] * re - K0[rn] * im);
+                                fx += T(2) * (Kx[rp] * re - Kx[rn] * im);
+                                fy += T(2) * (Ky[rp] * re - Ky[rn] * im);
+                                fz += T(2) * (Kz[rp] * re - Kz[rn] * im);
+                              }
+                            });
+        const double ia = 1.0 / aa;
+        phi += (double)fp * ia;
+        gx += (double)fx * ia * ia;
+        gy += (double)fy * ia * ia;
+        gz += (double)fz * ia * ia;
+      }
     }
-    if (act) {
-      far[i] += phi;
-      far[n + i] += gx;
-      far[2 * n + i] += gy;
-      far[3 * n + i] += gz;
+    red[0][tid] = phi;
+    red[1][tid] = gx;
+    red[2][tid] = gy;
+    red[3][tid] = gz;
+    __syncthreads();
+    if (tid < tcount) {
+      double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      for (int s2 = 0; s2 < k; ++s2) {
+        a0 += red[0][tid * k + s2];
+        a1 += red[1][tid * k + s2];
+        a2 += red[2][tid * k + s2];
+        a3 += red[3][tid * k + s2];
+      }
+      const int64_t i = f + tc + tid;
+      far[i] += a0;
+      far[n + i] += a1;
+      far[2 * n + i] += a2;
+      far[3 * n + i] += a3;
     }
+    __syncthreads();
   }
 }
 
@@ -405,7 +461,7 @@ void launch_m2m(int p, int32_t b0, int32_t nbl, const int32_t *child, const int3
                 const BoxGeo *geo, const Tin *Mc, const Top *ops, Tout *Mp, float *Mp32,
                 cudaStream_t s) {
   if (nbl == 0) return;
-  int64_t tot = (int64_t)nbl * ncoef(p);
+  int64_t tot = (int64_t)nbl * coef_pitch(p);
   k_m2m<Tin, Tout, Top, Tacc><<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, child, nchild, geo, Mc,
                                                                  ops, Mp, Mp32);
   FMM_LAUNCH_CHECK();
@@ -442,12 +498,15 @@ void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *fi
 
 template <typename T>
 void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, const int32_t *widx,
-                const int32_t *first, const int32_t *count, const BoxGeo *geo,
-                const typename V4<T>::type *src, double D, const T *M, int64_t n, double *far,
-                cudaStream_t s) {
+                int64_t nx, const int32_t *xboxes, const int32_t *xslot, const int32_t *first,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const T *M, T *K, int64_t n, double *far, cudaStream_t s) {
   if (nw == 0) return;
-  size_t sm = (size_t)ncoef(p) * sizeof(T);
-  k_m2p<T><<<(unsigned)nw, 64, sm, s>>>(p, wleaves, woff, widx, first, count, geo, src, D, M, n, far);
+  const int64_t tot = nx * ncoef(p + 1);
+  k_m2p_prep<T><<<ceil_div(tot, 256), 256, 0, s>>>(p, nx, xboxes, M, K);
+  FMM_LAUNCH_CHECK();
+  k_m2p<T><<<(unsigned)nw, kM2PThreads, 0, s>>>(p, wleaves, woff, widx, xslot, first, count, geo, src,
+                                                D, K, n, far);
   FMM_LAUNCH_CHECK();
 }
 
@@ -479,9 +538,9 @@ void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double
                               const BoxGeo *, const V4<T>::type *, double, const T *, int64_t,     \
                               double *, cudaStream_t);                                             \
   template void launch_m2p<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
-                              const int32_t *, const int32_t *, const BoxGeo *,                    \
-                              const V4<T>::type *, double, const T *, int64_t, double *,           \
-                              cudaStream_t);                                                       \
+                              int64_t, const int32_t *, const int32_t *, const int32_t *,          \
+                              const int32_t *, const BoxGeo *, const V4<T>::type *, double,        \
+                              const T *, T *, int64_t, double *, cudaStream_t);                    \
   template void launch_to_f64<T>(int64_t, const T *, double *, cudaStream_t);
 FMM_INST_T(float)
 FMM_INST_T(double)

@@ -19,6 +19,8 @@ struct Operators {
   //   d = anchor(target) - anchor(source); m2m[8], l2l[8] by child octant.
   DBuf<double> m2l64, m2m64, l2l64;
   DBuf<float> m2l32, m2m32, l2l32;
+  // FP32 M2L, output-major and zero padded: m2l32p[343][m2l_rows(p)][coef_pitch(p)]
+  DBuf<float> m2l32p;
 };
 
 // passes timed by the optional profiler (fmm_profile / fmm_profile_read)
@@ -29,7 +31,7 @@ uint64_t launch_count();
 
 struct fmm_plan_impl {
   // configuration
-  int order = 0, leaf_size = 1, precision = FMM_FP64, coarse_fp64_levels = 3, max_depth = kMaxDepth;
+  int order = 0, leaf_size = 1, autotune = 0, precision = FMM_FP64, coarse_fp64_levels = 3, max_depth = kMaxDepth;
   cudaStream_t stream = nullptr;
 
   // points
@@ -60,14 +62,20 @@ struct fmm_plan_impl {
   // work lists
   DBuf<int32_t> leaves;             // leaf boxes
   int64_t nleaves = 0;
-  DBuf<int32_t> xboxes;             // boxes with a non-empty X list
+  DBuf<int32_t> xboxes;             // boxes with a non-empty X list (= the W sources)
   int64_t nxboxes = 0;
+  DBuf<int32_t> xslot;              // per box: its index in xboxes, or -1
   DBuf<int32_t> wleaves;            // leaves with a non-empty W list
   int64_t nwleaves = 0;
   DBuf<int32_t> m2l_order;          // boxes of level >= 2 ordered by (level, parity, index)
   DBuf<M2LTile> m2l_tiles;
   int64_t nm2l_tiles = 0;
   int m2l_tile_size = 0;
+  // per tile: source box of every (slot, target) (-1 = none), and the
+  // occupied slots in ascending order
+  DBuf<int32_t> m2l_src;            // ntiles x 216 x tile
+  DBuf<int16_t> m2l_slots;          // ntiles x 216
+  DBuf<int32_t> m2l_nslots;         // ntiles
 
   // operators (rebuilt only when the order changes)
   Operators ops;
@@ -77,6 +85,8 @@ struct fmm_plan_impl {
   DBuf<float4> src32;
   DBuf<double> M64, L64;            // nboxes x NC
   DBuf<float> M32, L32;
+  DBuf<double> K64;                 // M2P coefficient sets of the W sources
+  DBuf<float> K32;
   DBuf<double> far_acc, near_acc;   // 4 x n each: phi, gx, gy, gz (sorted order)
   DBuf<double> adj_grad_w, adj_grad_q;  // n x 3 (adjoint)
   DBuf<double> adj_phi;
@@ -143,6 +153,10 @@ void morton_keys_raw(const double *d_xyz, int64_t n, double *partial, double *ge
 void set_points(fmm_plan_impl &P, const double *d_xyz);
 // operators.cu
 void build_operators(fmm_plan_impl &P);
+// m2l.cu
+void build_m2l_tables(fmm_plan_impl &P);
+// tune.cu: fastest leaf size for these points (cached per size bucket, order, precision)
+int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n);
 // eval.cu
 void eval_fmm(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad);
 void adjoint_fmm(fmm_plan_impl &P, const double *d_w, const double *d_q, const double *d_grad_q,

@@ -61,27 +61,45 @@ __global__ void k_bbox_partial(const double *__restrict__ xyz, int64_t n, double
 }
 
 __global__ void k_bbox_final(const double *partial, int nb, double *geom) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // one CTA of kT threads reduces the per-CTA partials
+  __shared__ double smin[3][kT], smax[3][kT], sbad[kT];
   double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
   double bad = 0;
-  for (int b = 0; b < nb; ++b) {
+  for (int b = threadIdx.x; b < nb; b += kT) {
     for (int a = 0; a < 3; ++a) {
       mn[a] = fmin(mn[a], partial[7 * b + a]);
       mx[a] = fmax(mx[a], partial[7 * b + 3 + a]);
     }
     bad = fmax(bad, partial[7 * b + 6]);
   }
+  for (int a = 0; a < 3; ++a) {
+    smin[a][threadIdx.x] = mn[a];
+    smax[a][threadIdx.x] = mx[a];
+  }
+  sbad[threadIdx.x] = bad;
+  __syncthreads();
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      for (int a = 0; a < 3; ++a) {
+        smin[a][threadIdx.x] = fmin(smin[a][threadIdx.x], smin[a][threadIdx.x + o]);
+        smax[a][threadIdx.x] = fmax(smax[a][threadIdx.x], smax[a][threadIdx.x + o]);
+      }
+      sbad[threadIdx.x] = fmax(sbad[threadIdx.x], sbad[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
   double ext = 0.0;
-  for (int a = 0; a < 3; ++a) ext = fmax(ext, mx[a] - mn[a]);
+  for (int a = 0; a < 3; ++a) ext = fmax(ext, smax[a][0] - smin[a][0]);
   double D = 1.0;
   if (ext > 0.0) {
     int e;
     frexp(ext, &e);  // ext = f 2^e with f in [0.5,1): 2^e is the smallest power of two > ext
     D = ldexp(1.0, e);
   }
-  for (int a = 0; a < 3; ++a) geom[a] = mn[a];
+  for (int a = 0; a < 3; ++a) geom[a] = smin[a][0];
   geom[3] = D;
-  geom[4] = bad;
+  geom[4] = sbad[0];
 }
 
 __global__ void k_morton(const double *__restrict__ xyz, int64_t n, const double *__restrict__ geom,
@@ -202,6 +220,11 @@ __global__ void k_flag(int64_t n, const int32_t *__restrict__ a, const int32_t *
   else if (mode == 1) f = a[i + 1] > a[i];
   else f = (b[i] == 0) && (a[i + 1] > a[i]);
   flag[i] = f;
+}
+
+__global__ void k_slot_of(int64_t nsel, const int32_t *__restrict__ sel, int32_t *__restrict__ slot) {
+  int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (j < nsel) slot[sel[j]] = (int32_t)j;
 }
 
 __global__ void k_compact(int64_t n, const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
@@ -484,7 +507,7 @@ void morton_keys_raw(const double *d_xyz, int64_t n, double *partial, double *ge
   int nbb = std::min(ceil_div(n, kT * 8), 1024);
   k_bbox_partial<<<nbb, kT, 0, s>>>(d_xyz, n, partial);
   FMM_LAUNCH_CHECK();
-  k_bbox_final<<<1, 32, 0, s>>>(partial, nbb, geom);
+  k_bbox_final<<<1, kT, 0, s>>>(partial, nbb, geom);
   FMM_LAUNCH_CHECK();
   k_morton<<<grid(n), kT, 0, s>>>(d_xyz, n, geom, keys, perm);
   FMM_LAUNCH_CHECK();
@@ -519,7 +542,7 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   P.geom.resize(8, s);
   k_bbox_partial<<<nbb, kT, 0, s>>>(d_xyz, n, P.partial.p);
   FMM_LAUNCH_CHECK();
-  k_bbox_final<<<1, 32, 0, s>>>(P.partial.p, nbb, P.geom.p);
+  k_bbox_final<<<1, kT, 0, s>>>(P.partial.p, nbb, P.geom.p);
   FMM_LAUNCH_CHECK();
   double hg[5];
   FMM_CUDA(cudaMemcpyAsync(hg, P.geom.p, sizeof(hg), cudaMemcpyDeviceToHost, s));
@@ -680,6 +703,12 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   k_flag<<<grid(nb), kT, 0, s>>>(nb, P.x_off.p, nullptr, 1, P.s_i32a.p);
   FMM_LAUNCH_CHECK();
   P.nxboxes = compact(P, nb, P.s_i32a.p, P.xboxes);
+  P.xslot.resize(nb, s);
+  FMM_CUDA(cudaMemsetAsync(P.xslot.p, 0xff, sizeof(int32_t) * nb, s));
+  if (P.nxboxes > 0) {
+    k_slot_of<<<grid(P.nxboxes), kT, 0, s>>>(P.nxboxes, P.xboxes.p, P.xslot.p);
+    FMM_LAUNCH_CHECK();
+  }
   k_flag<<<grid(nb), kT, 0, s>>>(nb, P.w_off.p, P.box_nchild.p, 2, P.s_i32a.p);
   FMM_LAUNCH_CHECK();
   P.nwleaves = compact(P, nb, P.s_i32a.p, P.wleaves);
@@ -711,6 +740,7 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
     FMM_CUDA(cudaMemcpyAsync(P.m2l_tiles.p, tiles.data(), sizeof(M2LTile) * tiles.size(),
                              cudaMemcpyHostToDevice, s));
     FMM_CUDA(cudaStreamSynchronize(s));  // `tiles` is a host temporary
+    if (P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder) build_m2l_tables(P);
   }
 }
 

@@ -1,0 +1,89 @@
+// tune.cu -- leaf-size autotuner.  fmm_plan_create/rebuild with leaf_size 0
+// times plan + mat-vec on the caller's own points for a ladder of leaf sizes
+// and keeps the fastest.  The balance it settles is the paper's compute-memory
+// trade-off inside the FMM (§1): larger leaves move work from the
+// translations (M2L) to the dense near field (P2P).  Results are cached per
+// (size bucket, order, precision) for the life of the process.
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "plan.cuh"
+
+namespace fmm {
+
+namespace {
+
+__global__ void k_fill(int64_t n, double v, double *out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = v;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune_cache;
+
+}  // namespace
+
+int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
+  const int bucket = n > 0 ? (int)std::floor(std::log2((double)n)) : 0;
+  const auto key = std::make_tuple(bucket, P.order, P.precision);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return it->second;
+  }
+  static const int ladder[] = {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+  cudaStream_t s = P.stream;
+  DBuf<double> q, phi;
+  q.resize(n, s);
+  phi.resize(n, s);
+  k_fill<<<ceil_div(n, 256), 256, 0, s>>>(n, 1.0 / (double)n, q.p);
+  FMM_LAUNCH_CHECK();
+  cudaEvent_t a, b;
+  FMM_CUDA(cudaEventCreate(&a));
+  FMM_CUDA(cudaEventCreate(&b));
+  int best = 64;
+  float best_ms = 1e30f;
+  const bool prof = P.prof_on;
+  P.prof_on = false;
+  try {
+    build_operators(P);
+    for (int S : ladder) {
+      if (S > 2 * n && S != ladder[0]) break;
+      P.leaf_size = S;
+      float t_min = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        FMM_CUDA(cudaEventRecord(a, s));
+        build_tree(P, d_xyz, n);
+        eval_fmm(P, q.p, phi.p, nullptr);
+        FMM_CUDA(cudaEventRecord(b, s));
+        FMM_CUDA(cudaEventSynchronize(b));
+        float t = 0.f;
+        FMM_CUDA(cudaEventElapsedTime(&t, a, b));
+        t_min = std::min(t_min, t);
+      }
+      if (t_min < best_ms) {
+        best_ms = t_min;
+        best = S;
+      }
+    }
+  } catch (...) {
+    P.prof_on = prof;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    q.release();
+    phi.release();
+    throw;
+  }
+  P.prof_on = prof;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  q.release();
+  phi.release();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+  return best;
+}
+
+}  // namespace fmm
