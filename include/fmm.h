@@ -86,8 +86,22 @@ typedef struct {
 fmm_status fmm_plan_create(const double *d_xyz, int64_t n, int leaf_size, int order,
                            const fmm_opts *opts, void *stream, fmm_plan_t *out);
 
+/* A batch of independent problems in one plan: problem b owns points
+ * [h_offsets[b], h_offsets[b+1]) of d_xyz (host offsets, nproblems + 1
+ * entries, h_offsets[0] = 0, non-decreasing).  Each problem gets its own root
+ * cube and octree (a forest); problems never interact.  fmm_eval /
+ * fmm_adjoint then run every pass once over all problems' boxes, and each
+ * problem's results equal those of its own single plan bit for bit (same
+ * leaf size, order and options).  Charges and outputs are concatenated in the
+ * same order as the points.  Errors as fmm_plan_create, plus INVALID_ARG for
+ * bad offsets. */
+fmm_status fmm_plan_create_batch(const double *d_xyz, const int64_t *h_offsets, int nproblems,
+                                 int leaf_size, int order, const fmm_opts *opts, void *stream,
+                                 fmm_plan_t *out);
+
 /* Rebuild an existing plan for new points (n may change), keeping its leaf
  * size, order and options and reusing its device memory where it fits.
+ * A batch plan rebuilds only for the same total size (same offsets).
  * Same errors and synchronisation as fmm_plan_create. */
 fmm_status fmm_plan_rebuild(fmm_plan_t plan, const double *d_xyz, int64_t n, void *stream);
 
@@ -109,6 +123,16 @@ fmm_status fmm_eval(fmm_plan_t plan, const double *d_q, double *d_phi, double *d
  * only d_dq is produced).  Asynchronous. */
 fmm_status fmm_adjoint(fmm_plan_t plan, const double *d_w, const double *d_q,
                        const double *d_grad_q, double *d_dq, double *d_dx, void *stream);
+
+/* fmm_eval, and fmm_adjoint when d_w is not NULL (d_dq, d_dx as in
+ * fmm_adjoint, with d_grad as the stored forward gradient), replayed as one
+ * CUDA graph.  The first call with a given set of pointers runs the work once
+ * eagerly (sizing buffers, building operators), captures it on `stream`, and
+ * launches the graph; later calls with the same pointers only launch the
+ * graph.  `stream` must not be the legacy default stream.  A rebuild of the
+ * plan drops the graph.  Asynchronous. */
+fmm_status fmm_eval_graph(fmm_plan_t plan, const double *d_q, double *d_phi, double *d_grad,
+                          const double *d_w, double *d_dq, double *d_dx, void *stream);
 
 /* End-to-end call on HOST buffers: copies h_xyz (n x 3) and h_q (n) to the
  * device, rebuilds `plan` for them, evaluates, and copies phi (n) and, if
@@ -135,7 +159,8 @@ fmm_status fmm_plan_sizes(fmm_plan_t plan, int64_t sizes[10]);
  *   9 box_nchild(int32, nboxes)
  *  10/11 U offsets (int32, nboxes+1) / sources (int32, |U|)
  *  12/13 V, 14/15 W, 16/17 X likewise.
- *  18 root cube (double, 4): lo_x, lo_y, lo_z, D.
+ *  18 root cubes (double, 4 per problem): lo_x, lo_y, lo_z, D.
+ *  19 problem offsets (int64, nproblems + 1).
  * Boxes are numbered by (level, key); list sources ascend by box number.
  * `bytes` must equal the array's size in bytes (INVALID_ARG otherwise). */
 fmm_status fmm_plan_export(fmm_plan_t plan, int which, void *h_dst, size_t bytes);

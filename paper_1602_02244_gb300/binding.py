@@ -18,13 +18,13 @@ FMM_FP64, FMM_MIXED = 0, 1
 _STATUS = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_CUDA", 3: "FMM_ERR_OOM",
            4: "FMM_ERR_TIMEOUT", 5: "FMM_ERR_NONFINITE_INPUT", 6: "FMM_ERR_UNSUPPORTED"}
 
-EXPORTS = ("fmm_plan_create", "fmm_plan_rebuild", "fmm_plan_set_points", "fmm_eval", "fmm_adjoint",
-           "fmm_solve_host", "fmm_plan_sizes", "fmm_plan_export", "fmm_plan_destroy",
+EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_plan_set_points",
+           "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_plan_sizes", "fmm_plan_export", "fmm_plan_destroy",
            "fmm_status_string", "fmm_last_error_message")
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
                  "box_parent", "box_child", "box_nchild", "u_off", "u_idx", "v_off", "v_idx",
-                 "w_off", "w_idx", "x_off", "x_idx", "root")
+                 "w_off", "w_idx", "x_off", "x_idx", "root", "offsets")
 
 
 class FMMError(RuntimeError):
@@ -54,10 +54,13 @@ def library():
         L = ctypes.CDLL(LIB_PATH)
         L.fmm_plan_create.argtypes = [_vp, _i64, _int, _int, ctypes.POINTER(Options), _vp,
                                       ctypes.POINTER(_vp)]
+        L.fmm_plan_create_batch.argtypes = [_vp, ctypes.POINTER(_i64), _int, _int, _int,
+                                            ctypes.POINTER(Options), _vp, ctypes.POINTER(_vp)]
         L.fmm_plan_rebuild.argtypes = [_vp, _vp, _i64, _vp]
         L.fmm_plan_set_points.argtypes = [_vp, _vp, _vp]
         L.fmm_eval.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.fmm_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.fmm_eval_graph.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.fmm_solve_host.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _vp]
         L.fmm_plan_sizes.argtypes = [_vp, ctypes.POINTER(_i64)]
         L.fmm_plan_export.argtypes = [_vp, _int, _vp, ctypes.c_size_t]
@@ -99,11 +102,13 @@ class Plan:
     """Tree, interaction lists and workspace of one FMM problem (fmm_plan_t).
 
     ``points``: (N, 3) float64 CUDA tensor.  ``order`` is the largest harmonic
-    degree p; ``precision`` is "fp64" or "mixed".
+    degree p; ``precision`` is "fp64" or "mixed"; ``leaf_size`` 0 autotunes.
+    ``offsets`` (sequence of B+1 ints) makes a batch of B independent problems
+    over the concatenated points (fmm_plan_create_batch).
     """
 
     def __init__(self, points, leaf_size=64, order=8, precision="fp64", coarse_fp64_levels=0,
-                 max_depth=0, stream=None):
+                 max_depth=0, stream=None, offsets=None):
         L = library()
         self.device = points.device
         self.n = int(points.shape[0])
@@ -114,9 +119,18 @@ class Plan:
         opts.max_depth = max_depth
         self.precision, self.order, self.leaf_size = precision, order, leaf_size
         h = _vp()
+        self.nproblems = 1 if offsets is None else len(offsets) - 1
         with torch.cuda.device(self.device):
-            _check(L.fmm_plan_create(_ptr(pts), self.n, leaf_size, order, ctypes.byref(opts),
-                                     _stream(stream), ctypes.byref(h)))
+            if offsets is None:
+                _check(L.fmm_plan_create(_ptr(pts), self.n, leaf_size, order, ctypes.byref(opts),
+                                         _stream(stream), ctypes.byref(h)))
+            else:
+                off = (_i64 * len(offsets))(*[int(v) for v in offsets])
+                if off[len(offsets) - 1] != self.n:
+                    raise ValueError("offsets[-1] must equal the number of points")
+                _check(L.fmm_plan_create_batch(_ptr(pts), off, self.nproblems, leaf_size, order,
+                                               ctypes.byref(opts), _stream(stream),
+                                               ctypes.byref(h)))
         self._h = h
 
     # -------------------------------------------------------------- life
@@ -170,6 +184,14 @@ class Plan:
                                          _ptr(dx), _stream(stream)))
         return dq, dx
 
+    def eval_graph(self, q, phi, grad, w=None, dq=None, dx=None, stream=None):
+        """fmm_eval (+ fmm_adjoint when w is given) replayed as one CUDA graph
+        on a non-default stream; outputs are written into the given tensors."""
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.device(self.device):
+            _check(library().fmm_eval_graph(self._h, _ptr(q), _ptr(phi), _ptr(grad), _ptr(w),
+                                            _ptr(dq), _ptr(dx), _vp(s.cuda_stream)))
+
     def solve_host(self, xyz, q, grad=True, stream=None):
         """End to end on host arrays: H2D, rebuild, eval, D2H (fmm_solve_host)."""
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
@@ -208,7 +230,7 @@ class Plan:
                [(np.int32, nb)] * 6 + \
                [(np.int32, nb1), (np.int32, sz["nu"]), (np.int32, nb1), (np.int32, sz["nv"]),
                 (np.int32, nb1), (np.int32, sz["nw"]), (np.int32, nb1), (np.int32, sz["nx"]),
-                (np.float64, 4)]
+                (np.float64, 4 * self.nproblems), (np.int64, self.nproblems + 1)]
         out = {}
         for i, (name, (dt, cnt)) in enumerate(zip(EXPORT_FIELDS, spec)):
             a = np.zeros(cnt, dtype=dt)

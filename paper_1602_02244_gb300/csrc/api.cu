@@ -7,6 +7,7 @@
 #include <new>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "plan.cuh"
 
@@ -92,7 +93,14 @@ void device_free(void *p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
+void drop_graph(fmm_plan_impl &P) {
+  if (P.graph_exec) cudaGraphExecDestroy(P.graph_exec);
+  P.graph_exec = nullptr;
+  for (auto &k : P.graph_key) k = nullptr;
+}
+
 void release_plan(fmm_plan_impl &P) {
+  drop_graph(P);
   P.geom.release(); P.partial.release(); P.keys.release(); P.keys_tmp.release();
   P.perm.release(); P.perm_tmp.release(); P.xyz_sorted.release(); P.pl64.release();
   P.pl32.release(); P.box_key.release(); P.box_level.release(); P.box_first.release();
@@ -109,7 +117,8 @@ void release_plan(fmm_plan_impl &P) {
   P.s_scan.release(); P.s_u64a.release(); P.s_u64b.release(); P.s_total.release();
   P.ca_off.release(); P.ca_idx.release(); P.m2l_src.release(); P.m2l_slots.release();
   P.m2l_nslots.release(); P.ops.m2l32p.release();
-  P.xslot.release(); P.K64.release(); P.K32.release();
+  P.xslot.release(); P.K64.release(); P.K32.release(); P.box_prob.release();
+  P.box_side.release(); P.prob_off.release(); P.prob_geom.release();
 }
 
 }  // namespace fmm
@@ -154,10 +163,56 @@ fmm_status fmm_plan_create(const double *d_xyz, int64_t n, int leaf_size, int or
   return FMM_OK;
 }
 
+fmm_status fmm_plan_create_batch(const double *d_xyz, const int64_t *h_offsets, int nproblems,
+                                 int leaf_size, int order, const fmm_opts *opts, void *stream,
+                                 fmm_plan_t *out) {
+  if (!out) return fail(FMM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nproblems < 1 || !h_offsets) return fail(FMM_ERR_INVALID_ARG, "need nproblems >= 1 and offsets");
+  if (h_offsets[0] != 0) return fail(FMM_ERR_INVALID_ARG, "offsets[0] must be 0");
+  for (int b = 0; b < nproblems; ++b)
+    if (h_offsets[b + 1] < h_offsets[b]) return fail(FMM_ERR_INVALID_ARG, "offsets must not decrease");
+  const int64_t n = h_offsets[nproblems];
+  if (n >= (int64_t(1) << 31)) return fail(FMM_ERR_INVALID_ARG, "total points must be < 2^31");
+  if (leaf_size < 0) return fail(FMM_ERR_INVALID_ARG, "leaf_size must be >= 1 (or 0: autotune)");
+  if (order < 0 || order > kMaxOrder) return fail(FMM_ERR_INVALID_ARG, "order must be in 0..20");
+  if (n > 0 && !d_xyz) return fail(FMM_ERR_INVALID_ARG, "d_xyz is NULL");
+  fmm_plan_s *P = nullptr;
+  fmm_status st = guarded([&] {
+    check_opts(opts);
+    P = new fmm_plan_s();
+    P->order = order;
+    P->leaf_size = leaf_size > 0 ? leaf_size : 64;
+    P->autotune = leaf_size == 0;
+    P->stream = (cudaStream_t)stream;
+    P->nproblems = nproblems;
+    P->prob_off_h.assign(h_offsets, h_offsets + nproblems + 1);
+    if (opts) {
+      P->precision = opts->precision;
+      P->coarse_fp64_levels = opts->coarse_fp64_levels == 0 ? 3 : opts->coarse_fp64_levels;
+      P->max_depth = opts->max_depth == 0 ? kMaxDepth : opts->max_depth;
+    }
+    if (P->autotune && n > 0) P->leaf_size = tuned_leaf_size(*P, d_xyz, n);
+    build_tree(*P, d_xyz, n);
+  });
+  if (st != FMM_OK) {
+    if (P) {
+      release_plan(*P);
+      cudaStreamSynchronize(P->stream);
+      delete P;
+    }
+    return st;
+  }
+  *out = P;
+  return FMM_OK;
+}
+
 fmm_status fmm_plan_rebuild(fmm_plan_t plan, const double *d_xyz, int64_t n, void *stream) {
   if (!plan) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
   if (n < 0 || n >= (int64_t(1) << 31)) return fail(FMM_ERR_INVALID_ARG, "n must be in [0, 2^31)");
   if (n > 0 && !d_xyz) return fail(FMM_ERR_INVALID_ARG, "d_xyz is NULL");
+  if (plan->nproblems > 1 && n != plan->prob_off_h.back())
+    return fail(FMM_ERR_INVALID_ARG, "a batch plan rebuilds only for the same problem sizes");
   return guarded([&] {
     plan->stream = (cudaStream_t)stream;
     if (plan->autotune && n > 0) plan->leaf_size = tuned_leaf_size(*plan, d_xyz, n);
@@ -195,11 +250,61 @@ fmm_status fmm_adjoint(fmm_plan_t plan, const double *d_w, const double *d_q,
   });
 }
 
+fmm_status fmm_eval_graph(fmm_plan_t plan, const double *d_q, double *d_phi, double *d_grad,
+                          const double *d_w, double *d_dq, double *d_dx, void *stream) {
+  if (!plan) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
+  if (!stream) return fail(FMM_ERR_INVALID_ARG, "fmm_eval_graph needs a non-default stream");
+  if (plan->n > 0 && (!d_q || !d_phi)) return fail(FMM_ERR_INVALID_ARG, "d_q or d_phi is NULL");
+  if (plan->n > 0 && d_w && !d_dq) return fail(FMM_ERR_INVALID_ARG, "d_dq is NULL");
+  return guarded([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->stream = s;
+    if (plan->n == 0) return;
+    const void *key[8] = {d_q, d_phi, d_grad, d_w, d_dq, d_dx, nullptr, nullptr};
+    bool same = plan->graph_exec != nullptr;
+    for (int i = 0; i < 8 && same; ++i) same = key[i] == plan->graph_key[i];
+    if (!same) {
+      drop_graph(*plan);
+      // one eager pass sizes every buffer and builds the operators, so the
+      // captured work allocates nothing and never synchronises
+      auto work = [&] {
+        eval_fmm(*plan, d_q, d_phi, d_grad);
+        if (d_w) adjoint_fmm(*plan, d_w, d_q, d_grad, d_dq, d_dx);
+      };
+      work();
+      const bool prof = plan->prof_on;
+      plan->prof_on = false;
+      cudaGraph_t g = nullptr;
+      FMM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      try {
+        work();
+      } catch (...) {
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        plan->prof_on = prof;
+        throw;
+      }
+      plan->prof_on = prof;
+      FMM_CUDA(cudaStreamEndCapture(s, &g));
+      cudaError_t e = cudaGraphInstantiate(&plan->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        plan->graph_exec = nullptr;
+        throw Error(FMM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+      for (int i = 0; i < 8; ++i) plan->graph_key[i] = key[i];
+    }
+    FMM_CUDA(cudaGraphLaunch(plan->graph_exec, s));
+  });
+}
+
 fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_q, int64_t n,
                           double *h_phi, double *h_grad, void *stream) {
   if (!plan) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
   if (n < 0 || n >= (int64_t(1) << 31)) return fail(FMM_ERR_INVALID_ARG, "n must be in [0, 2^31)");
   if (n > 0 && (!h_xyz || !h_q || !h_phi)) return fail(FMM_ERR_INVALID_ARG, "a host pointer is NULL");
+  if (plan->nproblems > 1 && n != plan->prob_off_h.back())
+    return fail(FMM_ERR_INVALID_ARG, "a batch plan solves only for the same problem sizes");
   return guarded([&] {
     cudaStream_t s = (cudaStream_t)stream;
     plan->stream = s;
@@ -242,7 +347,11 @@ fmm_status fmm_plan_export(fmm_plan_t plan, int which, void *h_dst, size_t bytes
   size_t want = 0;
   const size_t n = (size_t)P.n, nb = (size_t)P.nboxes, nb1 = nb + 1;
   bool lists = nb > 0;
-  double geo4[4] = {P.lo[0], P.lo[1], P.lo[2], P.D};
+  std::vector<double> geo4;
+  for (int b = 0; b < P.nproblems; ++b)
+    for (int a = 0; a < 4; ++a)
+      geo4.push_back(P.prob_geom_h.size() >= (size_t)8 * (b + 1) ? P.prob_geom_h[8 * b + a]
+                                                                  : (a == 3 ? 1.0 : 0.0));
   switch (which) {
     case 0: src = P.keys.p; want = n * 8; break;
     case 1: src = P.perm.p; want = n * 4; break;
@@ -262,7 +371,8 @@ fmm_status fmm_plan_export(fmm_plan_t plan, int which, void *h_dst, size_t bytes
     case 15: src = P.w_idx.p; want = (size_t)P.nw * 4; break;
     case 16: src = P.x_off.p; want = lists ? nb1 * 4 : 0; break;
     case 17: src = P.x_idx.p; want = (size_t)P.nx * 4; break;
-    case 18: src = nullptr; want = sizeof geo4; break;
+    case 18: src = nullptr; want = geo4.size() * sizeof(double); break;
+    case 19: src = nullptr; want = (P.prob_off_h.empty() ? 2 : P.prob_off_h.size()) * sizeof(int64_t); break;
     default: return fail(FMM_ERR_INVALID_ARG, "unknown export array");
   }
   if (bytes != want)
@@ -274,7 +384,12 @@ fmm_status fmm_plan_export(fmm_plan_t plan, int which, void *h_dst, size_t bytes
     return FMM_OK;
   }
   if (which == 18) {
-    std::memcpy(h_dst, geo4, want);
+    std::memcpy(h_dst, geo4.data(), want);
+    return FMM_OK;
+  }
+  if (which == 19) {
+    std::vector<int64_t> off = P.prob_off_h.empty() ? std::vector<int64_t>{0, P.n} : P.prob_off_h;
+    std::memcpy(h_dst, off.data(), want);
     return FMM_OK;
   }
   return guarded([&] {

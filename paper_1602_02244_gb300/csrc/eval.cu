@@ -41,7 +41,7 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
     PassScope ps_(P, kPassP2M);
     launch_permute_charges<double>(n, P.perm.p, d_q, P.pl64.p, P.src64.p, s);
     launch_p2m<double>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p,
-                       P.src64.p, P.D, P.M64.p, nullptr, -1, s);
+                       P.src64.p, P.box_side.p, P.M64.p, nullptr, -1, s);
   }
   for (int l = P.nlevels - 2; l >= 2; --l) {
     PassScope ps_(P, kPassM2M);
@@ -57,7 +57,7 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   {
     PassScope ps_(P, kPassP2L);
     launch_p2l<double>(p, P.nxboxes, P.xboxes.p, P.x_off.p, P.x_idx.p, P.box_first.p, P.box_count.p,
-                       P.box_geo.p, P.src64.p, P.D, P.L64.p, s);
+                       P.box_geo.p, P.src64.p, P.box_side.p, P.L64.p, s);
   }
   for (int l = 3; l < P.nlevels; ++l) {
     PassScope ps_(P, kPassL2L);
@@ -68,19 +68,19 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   {
     PassScope ps_(P, kPassL2P);
     launch_l2p<double>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src64.p,
-                       P.D, P.L64.p, n, P.far_acc.p, s);
+                       P.box_side.p, P.L64.p, n, P.far_acc.p, s);
   }
   {
     PassScope ps_(P, kPassM2P);
     P.K64.resize(std::max<size_t>(1, (size_t)P.nxboxes * 4 * coef_pitch(p + 1)), s);
     launch_m2p<double>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.nxboxes, P.xboxes.p,
-                       P.xslot.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src64.p, P.D, P.M64.p,
+                       P.xslot.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src64.p, P.box_side.p, P.M64.p,
                        P.K64.p, n, P.far_acc.p, s);
   }
   {
     PassScope ps_(P, kPassP2P);
     launch_p2p<double>(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
-                       P.box_geo.p, P.src64.p, P.D, n, P.near_acc.p, s);
+                       P.box_geo.p, P.src64.p, P.box_side.p, n, P.near_acc.p, s);
   }
   {
     PassScope ps_(P, kPassReduce);
@@ -100,7 +100,7 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
     PassScope ps_(P, kPassP2M);
     launch_permute_charges<float>(n, P.perm.p, d_q, P.pl32.p, P.src32.p, s);
     launch_p2m<float>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p,
-                      P.D, P.M32.p, coarse ? P.M64.p : nullptr, lc, s);
+                      P.box_side.p, P.M32.p, coarse ? P.M64.p : nullptr, lc, s);
   }
   for (int l = P.nlevels - 2; l >= 2; --l) {
     const int32_t b0 = P.level_off[l], nbl = P.level_off[l + 1] - b0;
@@ -131,7 +131,7 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   {
     PassScope ps_(P, kPassP2L);
     launch_p2l<float>(p, P.nxboxes, P.xboxes.p, P.x_off.p, P.x_idx.p, P.box_first.p, P.box_count.p,
-                      P.box_geo.p, P.src32.p, P.D, P.L32.p, s);
+                      P.box_geo.p, P.src32.p, P.box_side.p, P.L32.p, s);
   }
   const size_t nc = (size_t)coef_pitch(p);
   if (coarse && P.nlevels > 2) {
@@ -153,19 +153,19 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   {
     PassScope ps_(P, kPassL2P);
     launch_l2p<float>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p,
-                      P.D, P.L32.p, n, P.far_acc.p, s);
+                      P.box_side.p, P.L32.p, n, P.far_acc.p, s);
   }
   {
     PassScope ps_(P, kPassM2P);
     P.K32.resize(std::max<size_t>(1, (size_t)P.nxboxes * 4 * coef_pitch(p + 1)), s);
     launch_m2p<float>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.nxboxes, P.xboxes.p,
-                      P.xslot.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p, P.D, P.M32.p,
+                      P.xslot.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p, P.box_side.p, P.M32.p,
                       P.K32.p, n, P.far_acc.p, s);
   }
   {
     PassScope ps_(P, kPassP2P);
     launch_p2p<float>(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
-                      P.box_geo.p, P.src32.p, P.D, n, P.near_acc.p, s);
+                      P.box_geo.p, P.src32.p, P.box_side.p, n, P.near_acc.p, s);
   }
   {
     PassScope ps_(P, kPassReduce);

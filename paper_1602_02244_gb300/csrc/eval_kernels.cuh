@@ -20,12 +20,12 @@ void launch_permute_charges(int64_t n, const int32_t *perm, const double *q,
                             const typename V4<T>::type *pl, typename V4<T>::type *src, cudaStream_t s);
 template <typename T>
 void launch_p2m(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
-                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 T *M, double *M64, int coarse, cudaStream_t s);
 template <typename T>
 void launch_p2l(int p, int64_t nx, const int32_t *xboxes, const int32_t *xoff, const int32_t *xidx,
                 const int32_t *first, const int32_t *count, const BoxGeo *geo,
-                const typename V4<T>::type *src, double D, T *L, cudaStream_t s);
+                const typename V4<T>::type *src, const double *side, T *L, cudaStream_t s);
 template <typename Tin, typename Tout, typename Top, typename Tacc>
 void launch_m2m(int p, int32_t b0, int32_t nbl, const int32_t *child, const int32_t *nchild,
                 const BoxGeo *geo, const Tin *Mc, const Top *ops, Tout *Mp, float *Mp32,
@@ -38,13 +38,13 @@ template <typename Tin>
 void launch_to_f64(int64_t count, const Tin *in, double *out, cudaStream_t s);
 template <typename T>
 void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
-                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 const T *L, int64_t n, double *far, cudaStream_t s);
 // M2P over W lists; K is scratch of 4 * coef_pitch(p+1) per X box (the W sources)
 template <typename T>
 void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, const int32_t *widx,
                 int64_t nx, const int32_t *xboxes, const int32_t *xslot, const int32_t *first,
-                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 const T *M, T *K, int64_t n, double *far, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *perm, const double *far, const double *near,
                     double *phi, double *grad, cudaStream_t s);
@@ -65,6 +65,6 @@ void launch_m2l_staged(int p, int64_t ntiles, const M2LTile *tiles, const int32_
 template <typename T>
 void launch_p2p(int64_t nleaves, const int32_t *leaves, const int32_t *uoff, const int32_t *uidx,
                 const int32_t *first, const int32_t *count, const BoxGeo *geo,
-                const typename V4<T>::type *src, double D, int64_t n, double *near, cudaStream_t s);
+                const typename V4<T>::type *src, const double *side, int64_t n, double *near, cudaStream_t s);
 
 }  // namespace fmm

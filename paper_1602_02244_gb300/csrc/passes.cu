@@ -13,9 +13,10 @@ namespace fmm {
 
 namespace {
 
-__device__ __forceinline__ double center_delta(int32_t ia, int la, int32_t ib, int lb, double D) {
-  // (c_A - c_B) along one axis, exact: both centres are dyadic multiples of D
-  return ((double)ia + 0.5) * box_side(D, la) - ((double)ib + 0.5) * box_side(D, lb);
+__device__ __forceinline__ double center_delta(int32_t ia, double sa, int32_t ib, double sb) {
+  // (c_A - c_B) along one axis from anchors and box sides, exact: both centres
+  // are dyadic multiples of the root side
+  return ((double)ia + 0.5) * sa - ((double)ib + 0.5) * sb;
 }
 
 constexpr int kAccSlots = 14;  // ceil(441 / 32): coefficients per lane for p <= 20
@@ -38,7 +39,8 @@ template <typename T>
 __global__ void k_p2m(int p, int64_t nleaves, const int32_t *__restrict__ leaves,
                       const int32_t *__restrict__ first, const int32_t *__restrict__ count,
                       const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
-                      double D, T *__restrict__ M, double *__restrict__ M64, int coarse) {
+                      const double *__restrict__ side, T *__restrict__ M, double *__restrict__ M64,
+                      int coarse) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = ncoef(p), ld = coef_pitch(p), pitch = 33, lane = threadIdx.x & 31;
   T *buf = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * nc * pitch;
@@ -46,7 +48,7 @@ __global__ void k_p2m(int p, int64_t nleaves, const int32_t *__restrict__ leaves
   if (w >= nleaves) return;
   const int32_t b = leaves[w];
   const BoxGeo g = geo[b];
-  const T inva = (T)(1.0 / box_side(D, g.level));
+  const T inva = (T)(1.0 / side[b]);
   T acc[kAccSlots];
 #pragma unroll
   for (int t = 0; t < kAccSlots; ++t) acc[t] = T(0);
@@ -91,7 +93,7 @@ __global__ void k_p2l(int p, int64_t nboxes_x, const int32_t *__restrict__ xboxe
                       const int32_t *__restrict__ xoff, const int32_t *__restrict__ xidx,
                       const int32_t *__restrict__ first, const int32_t *__restrict__ count,
                       const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
-                      double D, T *__restrict__ L) {
+                      const double *__restrict__ side, T *__restrict__ L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = ncoef(p), ld = coef_pitch(p), pitch = 33, lane = threadIdx.x & 31;
   T *buf = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * nc * pitch;
@@ -99,7 +101,7 @@ __global__ void k_p2l(int p, int64_t nboxes_x, const int32_t *__restrict__ xboxe
   if (w >= nboxes_x) return;
   const int32_t C = xboxes[w];
   const BoxGeo gc = geo[C];
-  const double ac = box_side(D, gc.level);
+  const double ac = side[C];
   const T inva = (T)(1.0 / ac);
   T acc[kAccSlots];
 #pragma unroll
@@ -107,9 +109,9 @@ __global__ void k_p2l(int p, int64_t nboxes_x, const int32_t *__restrict__ xboxe
   for (int32_t e = xoff[C]; e < xoff[C + 1]; ++e) {
     const int32_t A = xidx[e];
     const BoxGeo ga = geo[A];
-    const T sx = (T)center_delta(ga.ix, ga.level, gc.ix, gc.level, D);
-    const T sy = (T)center_delta(ga.iy, ga.level, gc.iy, gc.level, D);
-    const T sz = (T)center_delta(ga.iz, ga.level, gc.iz, gc.level, D);
+    const T sx = (T)center_delta(ga.ix, side[A], gc.ix, ac);
+    const T sy = (T)center_delta(ga.iy, side[A], gc.iy, ac);
+    const T sz = (T)center_delta(ga.iz, side[A], gc.iz, ac);
     const int32_t f = first[A], c = count[A];
     for (int32_t j0 = 0; j0 < c; j0 += 32) {
       const int32_t j = j0 + lane;
@@ -217,8 +219,9 @@ __global__ void k_to_f64(int64_t count, const Tin *__restrict__ in, double *__re
 template <typename T>
 __global__ void k_l2p(int p, const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
                       const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
-                      const typename V4<T>::type *__restrict__ src, double D,
-                      const T *__restrict__ L, int64_t n, double *__restrict__ far) {
+                      const typename V4<T>::type *__restrict__ src,
+                      const double *__restrict__ side, const T *__restrict__ L, int64_t n,
+                      double *__restrict__ far) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Ls = reinterpret_cast<T *>(smem_raw);
   const int nc = ncoef(p);
@@ -232,7 +235,7 @@ __global__ void k_l2p(int p, const int32_t *__restrict__ leaves, const int32_t *
   }
   for (int k = threadIdx.x; k < nc; k += blockDim.x) Ls[k] = L[(int64_t)b * coef_pitch(p) + k];
   __syncthreads();
-  const double a = box_side(D, g.level);
+  const double a = side[b];
   const T inva = (T)(1.0 / a);
   for (int32_t i = f + threadIdx.x; i < f + c; i += blockDim.x) {
     const typename V4<T>::type s = src[i];
@@ -314,8 +317,9 @@ __global__ void __launch_bounds__(kM2PThreads)
     k_m2p(int p, const int32_t *__restrict__ wleaves, const int32_t *__restrict__ woff,
           const int32_t *__restrict__ widx, const int32_t *__restrict__ xslot,
           const int32_t *__restrict__ first, const int32_t *__restrict__ count,
-          const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src, double D,
-          const T *__restrict__ K, int64_t n, double *__restrict__ far) {
+          const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
+          const double *__restrict__ side, const T *__restrict__ K, int64_t n,
+          double *__restrict__ far) {
   __shared__ double red[4][kM2PThreads];
   const int tid = threadIdx.x, ld1 = coef_pitch(p + 1);
   const int32_t B = wleaves[blockIdx.x];
@@ -331,11 +335,11 @@ __global__ void __launch_bounds__(kM2PThreads)
       for (int32_t e = e0 + sl; e < e1; e += k) {
         const int32_t A = widx[e];
         const BoxGeo ga = geo[A];
-        const double aa = box_side(D, ga.level);
+        const double aa = side[A];
         const T inva = (T)(1.0 / aa);
-        const T sx = (T)center_delta(gb.ix, gb.level, ga.ix, ga.level, D);
-        const T sy = (T)center_delta(gb.iy, gb.level, ga.iy, ga.level, D);
-        const T sz = (T)center_delta(gb.iz, gb.level, ga.iz, ga.level, D);
+        const T sx = (T)center_delta(gb.ix, side[B], ga.ix, aa);
+        const T sy = (T)center_delta(gb.iy, side[B], ga.iy, aa);
+        const T sz = (T)center_delta(gb.iz, side[B], ga.iz, aa);
         const T *K0 = K + (int64_t)xslot[A] * 4 * ld1;
         const T *Kx = K0 + ld1, *Ky = K0 + 2 * ld1, *Kz = K0 + 3 * ld1;
         T fp = 0, fx = 0, fy = 0, fz = 0;
@@ -432,27 +436,27 @@ void launch_permute_charges(int64_t n, const int32_t *perm, const double *q,
 
 template <typename T>
 void launch_p2m(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
-                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 T *M, double *M64, int coarse, cudaStream_t s) {
   if (nleaves == 0) return;
   size_t per = (size_t)ncoef(p) * 33 * sizeof(T);
   int w = warps_for(per);
   allow_smem(k_p2m<T>, per * w);
   k_p2m<T><<<ceil_div(nleaves, w), 32 * w, per * w, s>>>(p, nleaves, leaves, first, count, geo, src,
-                                                          D, M, M64, coarse);
+                                                          side, M, M64, coarse);
   FMM_LAUNCH_CHECK();
 }
 
 template <typename T>
 void launch_p2l(int p, int64_t nx, const int32_t *xboxes, const int32_t *xoff, const int32_t *xidx,
                 const int32_t *first, const int32_t *count, const BoxGeo *geo,
-                const typename V4<T>::type *src, double D, T *L, cudaStream_t s) {
+                const typename V4<T>::type *src, const double *side, T *L, cudaStream_t s) {
   if (nx == 0) return;
   size_t per = (size_t)ncoef(p) * 33 * sizeof(T);
   int w = warps_for(per);
   allow_smem(k_p2l<T>, per * w);
   k_p2l<T><<<ceil_div(nx, w), 32 * w, per * w, s>>>(p, nx, xboxes, xoff, xidx, first, count, geo,
-                                                     src, D, L);
+                                                     src, side, L);
   FMM_LAUNCH_CHECK();
 }
 
@@ -488,25 +492,25 @@ void launch_to_f64(int64_t count, const Tin *in, double *out, cudaStream_t s) {
 
 template <typename T>
 void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
-                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 const T *L, int64_t n, double *far, cudaStream_t s) {
   if (nleaves == 0) return;
   size_t sm = (size_t)ncoef(p) * sizeof(T);
-  k_l2p<T><<<(unsigned)nleaves, 64, sm, s>>>(p, leaves, first, count, geo, src, D, L, n, far);
+  k_l2p<T><<<(unsigned)nleaves, 64, sm, s>>>(p, leaves, first, count, geo, src, side, L, n, far);
   FMM_LAUNCH_CHECK();
 }
 
 template <typename T>
 void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, const int32_t *widx,
                 int64_t nx, const int32_t *xboxes, const int32_t *xslot, const int32_t *first,
-                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, double D,
+                const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 const T *M, T *K, int64_t n, double *far, cudaStream_t s) {
   if (nw == 0) return;
   const int64_t tot = nx * ncoef(p + 1);
   k_m2p_prep<T><<<ceil_div(tot, 256), 256, 0, s>>>(p, nx, xboxes, M, K);
   FMM_LAUNCH_CHECK();
   k_m2p<T><<<(unsigned)nw, kM2PThreads, 0, s>>>(p, wleaves, woff, widx, xslot, first, count, geo, src,
-                                                D, K, n, far);
+                                                side, K, n, far);
   FMM_LAUNCH_CHECK();
 }
 
@@ -529,17 +533,17 @@ void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double
   template void launch_permute_charges<T>(int64_t, const int32_t *, const double *,                \
                                           const V4<T>::type *, V4<T>::type *, cudaStream_t);       \
   template void launch_p2m<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
-                              const BoxGeo *, const V4<T>::type *, double, T *, double *, int,     \
+                              const BoxGeo *, const V4<T>::type *, const double *, T *, double *, int,     \
                               cudaStream_t);                                                       \
   template void launch_p2l<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
                               const int32_t *, const int32_t *, const BoxGeo *,                    \
-                              const V4<T>::type *, double, T *, cudaStream_t);                     \
+                              const V4<T>::type *, const double *, T *, cudaStream_t);                     \
   template void launch_l2p<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
-                              const BoxGeo *, const V4<T>::type *, double, const T *, int64_t,     \
+                              const BoxGeo *, const V4<T>::type *, const double *, const T *, int64_t,     \
                               double *, cudaStream_t);                                             \
   template void launch_m2p<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
                               int64_t, const int32_t *, const int32_t *, const int32_t *,          \
-                              const int32_t *, const BoxGeo *, const V4<T>::type *, double,        \
+                              const int32_t *, const BoxGeo *, const V4<T>::type *, const double *, \
                               const T *, T *, int64_t, double *, cudaStream_t);                    \
   template void launch_to_f64<T>(int64_t, const T *, double *, cudaStream_t);
 FMM_INST_T(float)

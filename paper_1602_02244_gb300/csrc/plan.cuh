@@ -34,6 +34,15 @@ struct fmm_plan_impl {
   int order = 0, leaf_size = 1, autotune = 0, precision = FMM_FP64, coarse_fp64_levels = 3, max_depth = kMaxDepth;
   cudaStream_t stream = nullptr;
 
+  // problems: a plan holds one problem, or a batch of independent problems
+  // (a forest: each problem has its own root cube and tree; they never
+  // interact).  Problem b owns input points [prob_off_h[b], prob_off_h[b+1]).
+  int nproblems = 1;
+  std::vector<int64_t> prob_off_h;
+  DBuf<int64_t> prob_off;
+  DBuf<double> prob_geom;           // per problem: lo[3], D, non-finite flag, pad
+  std::vector<double> prob_geom_h;
+
   // points
   int64_t n = 0;
   double lo[3] = {0, 0, 0}, D = 1.0;
@@ -52,6 +61,8 @@ struct fmm_plan_impl {
   DBuf<uint64_t> box_key;
   DBuf<int32_t> box_level, box_first, box_count, box_parent, box_child, box_nchild;
   DBuf<BoxGeo> box_geo;
+  DBuf<int32_t> box_prob;           // problem of each box
+  DBuf<double> box_side;            // side length of each box
   DBuf<int32_t> colleagues;         // nboxes x 26, sorted, -1 padded
   DBuf<int32_t> ncolleagues;
 
@@ -111,6 +122,10 @@ struct fmm_plan_impl {
     return ev_pool[ev_used++];
   }
 
+  // CUDA graph of one eval (+ adjoint) for fixed buffers; dropped on rebuild
+  cudaGraphExec_t graph_exec = nullptr;
+  const void *graph_key[8] = {};
+
   // scratch
   DBuf<int32_t> s_i32a, s_i32b, s_i32c, s_hist, s_scan;
   DBuf<uint64_t> s_u64a, s_u64b;
@@ -162,6 +177,7 @@ void eval_fmm(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad
 void adjoint_fmm(fmm_plan_impl &P, const double *d_w, const double *d_q, const double *d_grad_q,
                  double *d_dq, double *d_dx);
 void release_plan(fmm_plan_impl &P);
+void drop_graph(fmm_plan_impl &P);
 
 // read a device int32 scalar (synchronous)
 int32_t read_scalar(const int32_t *d, cudaStream_t s);

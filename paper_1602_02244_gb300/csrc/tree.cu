@@ -102,21 +102,105 @@ __global__ void k_bbox_final(const double *partial, int nb, double *geom) {
   geom[4] = sbad[0];
 }
 
+// one CTA per problem of a batch: root cube of its points (same rule as above)
+__global__ void k_bbox_problems(const double *__restrict__ xyz, const int64_t *__restrict__ off,
+                                double *__restrict__ geom) {
+  __shared__ double smin[3][kT], smax[3][kT];
+  __shared__ int sbad[kT];
+  const int b = blockIdx.x;
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int bad = 0;
+  for (int64_t i = off[b] + threadIdx.x; i < off[b + 1]; i += kT)
+    for (int a = 0; a < 3; ++a) {
+      double v = xyz[3 * i + a];
+      if (!isfinite(v)) bad = 1;
+      mn[a] = fmin(mn[a], v);
+      mx[a] = fmax(mx[a], v);
+    }
+  for (int a = 0; a < 3; ++a) {
+    smin[a][threadIdx.x] = mn[a];
+    smax[a][threadIdx.x] = mx[a];
+  }
+  sbad[threadIdx.x] = bad;
+  __syncthreads();
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      for (int a = 0; a < 3; ++a) {
+        smin[a][threadIdx.x] = fmin(smin[a][threadIdx.x], smin[a][threadIdx.x + o]);
+        smax[a][threadIdx.x] = fmax(smax[a][threadIdx.x], smax[a][threadIdx.x + o]);
+      }
+      sbad[threadIdx.x] |= sbad[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  double *g = geom + 8 * b;
+  if (off[b + 1] == off[b]) {  // empty problem
+    g[0] = g[1] = g[2] = 0.0;
+    g[3] = 1.0;
+    g[4] = 0.0;
+    return;
+  }
+  double ext = 0.0;
+  for (int a = 0; a < 3; ++a) ext = fmax(ext, smax[a][0] - smin[a][0]);
+  double D = 1.0;
+  if (ext > 0.0) {
+    int e;
+    frexp(ext, &e);
+    D = ldexp(1.0, e);
+  }
+  for (int a = 0; a < 3; ++a) g[a] = smin[a][0];
+  g[3] = D;
+  g[4] = sbad[0];
+}
+
+__device__ __forceinline__ int problem_of(int64_t i, const int64_t *__restrict__ off, int nprob) {
+  int lo = 0, hi = nprob - 1;  // last b with off[b] <= i
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Morton key of every point in its own problem's root cube (geom: 8 doubles
+// per problem; one problem when off == nullptr)
 __global__ void k_morton(const double *__restrict__ xyz, int64_t n, const double *__restrict__ geom,
-                         uint64_t *__restrict__ keys, int32_t *__restrict__ perm) {
+                         const int64_t *__restrict__ off, int nprob, uint64_t *__restrict__ keys,
+                         int32_t *__restrict__ perm) {
   int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
   if (i >= n) return;
-  const double D = geom[3];
+  const double *g = geom + (off ? 8 * problem_of(i, off, nprob) : 0);
+  const double D = g[3];
   const double s = ldexp(1.0, kMaxDepth) / D;  // power of two: the product below is exact
   const double top = (double)((1u << kMaxDepth) - 1u);
   uint32_t q[3];
   for (int a = 0; a < 3; ++a) {
-    double t = floor(__dmul_rn(__dsub_rn(xyz[3 * i + a], geom[a]), s));
+    double t = floor(__dmul_rn(__dsub_rn(xyz[3 * i + a], g[a]), s));
     t = fmin(fmax(t, 0.0), top);
     q[a] = (uint32_t)t;
   }
   keys[i] = morton3(q[0], q[1], q[2]);
   perm[i] = (int32_t)i;
+}
+
+__global__ void k_problem_keys(int64_t n, const int32_t *__restrict__ perm,
+                               const int64_t *__restrict__ off, int nprob,
+                               uint64_t *__restrict__ pk, int32_t *__restrict__ idx) {
+  int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i >= n) return;
+  pk[i] = (uint64_t)problem_of(perm[i], off, nprob);
+  idx[i] = (int32_t)i;
+}
+
+__global__ void k_apply_perm(int64_t n, const int32_t *__restrict__ sigma,
+                             const uint64_t *__restrict__ kin, const int32_t *__restrict__ pin,
+                             uint64_t *__restrict__ kout, int32_t *__restrict__ pout) {
+  int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i >= n) return;
+  kout[i] = kin[sigma[i]];
+  pout[i] = pin[sigma[i]];
 }
 
 __global__ void k_gather_xyz(const double *__restrict__ xyz, const int32_t *__restrict__ perm,
@@ -166,7 +250,7 @@ __global__ void k_split_make(int level, int32_t b0, int32_t nbl, int32_t child0,
                              const int32_t *__restrict__ nchild, const int32_t *__restrict__ coff,
                              const uint64_t *__restrict__ keys, int32_t *first, int32_t *count,
                              uint64_t *bkey, int32_t *blevel, int32_t *parent, int32_t *child,
-                             int32_t *bnchild) {
+                             int32_t *bnchild, int32_t *bprob) {
   int32_t t = blockIdx.x * kT + threadIdx.x;
   if (t >= nbl) return;
   int32_t b = b0 + t;
@@ -189,6 +273,7 @@ __global__ void k_split_make(int level, int32_t b0, int32_t nbl, int32_t child0,
       bkey[c] = (pk << 3) | o;
       blevel[c] = level + 1;
       parent[c] = b;
+      bprob[c] = bprob[b];
       ++c;
     }
     s = s1;
@@ -206,6 +291,14 @@ __global__ void k_box_geo(int64_t nb, const uint64_t *__restrict__ bkey,
   g.iz = (int32_t)compact3(k >> 2);
   g.level = blevel[b];
   geo[b] = g;
+}
+
+__global__ void k_box_side(int64_t nb, const int32_t *__restrict__ blevel,
+                           const int32_t *__restrict__ bprob, const double *__restrict__ geom,
+                           double *__restrict__ side) {
+  int64_t b = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (b >= nb) return;
+  side[b] = box_side(geom[8 * bprob[b] + 3], blevel[b]);
 }
 
 __global__ void k_flag(int64_t n, const int32_t *__restrict__ a, const int32_t *__restrict__ b,
@@ -236,13 +329,15 @@ __global__ void k_compact(int64_t n, const int32_t *__restrict__ flag, const int
 
 __global__ void k_leaf_points(const int32_t *__restrict__ leaves, const BoxGeo *__restrict__ geo,
                               const int32_t *__restrict__ first, const int32_t *__restrict__ count,
-                              const double *__restrict__ xyz, double lx, double ly, double lz,
-                              double D, double4 *__restrict__ pl64, float4 *__restrict__ pl32) {
+                              const double *__restrict__ xyz, const int32_t *__restrict__ bprob,
+                              const double *__restrict__ pgeom, const double *__restrict__ side,
+                              double4 *__restrict__ pl64, float4 *__restrict__ pl32) {
   int32_t b = leaves[blockIdx.x];
   BoxGeo g = geo[b];
-  double a = box_side(D, g.level);
-  double cx = lx + ((double)g.ix + 0.5) * a, cy = ly + ((double)g.iy + 0.5) * a,
-         cz = lz + ((double)g.iz + 0.5) * a;
+  const double *lo = pgeom + 8 * bprob[b];
+  double a = side[b];
+  double cx = lo[0] + ((double)g.ix + 0.5) * a, cy = lo[1] + ((double)g.iy + 0.5) * a,
+         cz = lo[2] + ((double)g.iz + 0.5) * a;
   int32_t f = first[b], c = count[b];
   for (int32_t i = f + threadIdx.x; i < f + c; i += blockDim.x) {
     double x = xyz[3 * (int64_t)i] - cx, y = xyz[3 * (int64_t)i + 1] - cy,
@@ -270,11 +365,13 @@ __device__ __forceinline__ bool adjacent(const BoxGeo &A, const BoxGeo &B) {
 
 // colleagues: same-level boxes adjacent to B (excluding B), ascending
 __global__ void k_colleagues(int64_t nb, const BoxGeo *__restrict__ geo,
-                             const uint64_t *__restrict__ bkey, const int32_t *__restrict__ loff,
-                             int32_t *__restrict__ col, int32_t *__restrict__ ncol) {
+                             const uint64_t *__restrict__ bkey, const int32_t *__restrict__ bprob,
+                             const int32_t *__restrict__ loff, int32_t *__restrict__ col,
+                             int32_t *__restrict__ ncol) {
   int64_t b = (int64_t)blockIdx.x * kT + threadIdx.x;
   if (b >= nb) return;
   BoxGeo g = geo[b];
+  const int32_t pb = bprob[b];  // boxes of a level are ordered by (problem, key)
   int32_t found[26];
   int k = 0;
   if (g.level > 0) {
@@ -290,10 +387,10 @@ __global__ void k_colleagues(int64_t nb, const BoxGeo *__restrict__ geo,
           int32_t f = lo, e = hi;
           while (f < e) {
             int32_t m = f + ((e - f) >> 1);
-            if (bkey[m] < key) f = m + 1;
+            if (bprob[m] < pb || (bprob[m] == pb && bkey[m] < key)) f = m + 1;
             else e = m;
           }
-          if (f < hi && bkey[f] == key) {
+          if (f < hi && bprob[f] == pb && bkey[f] == key) {
             int j = k++;  // insertion sort
             while (j > 0 && found[j - 1] > f) {
               found[j] = found[j - 1];
@@ -509,7 +606,7 @@ void morton_keys_raw(const double *d_xyz, int64_t n, double *partial, double *ge
   FMM_LAUNCH_CHECK();
   k_bbox_final<<<1, kT, 0, s>>>(partial, nbb, geom);
   FMM_LAUNCH_CHECK();
-  k_morton<<<grid(n), kT, 0, s>>>(d_xyz, n, geom, keys, perm);
+  k_morton<<<grid(n), kT, 0, s>>>(d_xyz, n, geom, nullptr, 1, keys, perm);
   FMM_LAUNCH_CHECK();
 }
 
@@ -520,13 +617,14 @@ void set_points(fmm_plan_impl &P, const double *d_xyz) {
   k_gather_xyz<<<grid(n), kT, 0, s>>>(d_xyz, P.perm.p, n, P.xyz_sorted.p);
   FMM_LAUNCH_CHECK();
   k_leaf_points<<<(int)P.nleaves, 128, 0, s>>>(P.leaves.p, P.box_geo.p, P.box_first.p,
-                                                P.box_count.p, P.xyz_sorted.p, P.lo[0], P.lo[1],
-                                                P.lo[2], P.D, P.pl64.p, P.pl32.p);
+                                                P.box_count.p, P.xyz_sorted.p, P.box_prob.p,
+                                                P.prob_geom.p, P.box_side.p, P.pl64.p, P.pl32.p);
   FMM_LAUNCH_CHECK();
 }
 
 void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   cudaStream_t s = P.stream;
+  drop_graph(P);  // a captured graph refers to the old layout
   P.n = n;
   P.nboxes = 0;
   P.nlevels = 0;
@@ -536,37 +634,64 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   if (n == 0) return;
   std::unique_ptr<PassScope> scope(new PassScope(P, kPassSort));
 
-  // ---- root cube
-  int nbb = std::min(ceil_div(n, kT * 8), 1024);
-  P.partial.resize((size_t)7 * nbb, s);
-  P.geom.resize(8, s);
-  k_bbox_partial<<<nbb, kT, 0, s>>>(d_xyz, n, P.partial.p);
-  FMM_LAUNCH_CHECK();
-  k_bbox_final<<<1, kT, 0, s>>>(P.partial.p, nbb, P.geom.p);
-  FMM_LAUNCH_CHECK();
-  double hg[5];
-  FMM_CUDA(cudaMemcpyAsync(hg, P.geom.p, sizeof(hg), cudaMemcpyDeviceToHost, s));
+  // ---- root cube(s)
+  const int B = P.nproblems;
+  if ((int64_t)P.prob_off_h.size() != B + 1 || P.prob_off_h[B] != n) P.prob_off_h = {0, n};
+  P.prob_geom.resize((size_t)8 * B, s);
+  if (B == 1) {
+    int nbb = std::min(ceil_div(n, kT * 8), 1024);
+    P.partial.resize((size_t)7 * nbb, s);
+    k_bbox_partial<<<nbb, kT, 0, s>>>(d_xyz, n, P.partial.p);
+    FMM_LAUNCH_CHECK();
+    k_bbox_final<<<1, kT, 0, s>>>(P.partial.p, nbb, P.prob_geom.p);
+    FMM_LAUNCH_CHECK();
+  } else {
+    P.prob_off.resize(B + 1, s);
+    FMM_CUDA(cudaMemcpyAsync(P.prob_off.p, P.prob_off_h.data(), sizeof(int64_t) * (B + 1),
+                             cudaMemcpyHostToDevice, s));
+    k_bbox_problems<<<B, kT, 0, s>>>(d_xyz, P.prob_off.p, P.prob_geom.p);
+    FMM_LAUNCH_CHECK();
+  }
+  P.prob_geom_h.resize((size_t)8 * B);
+  FMM_CUDA(cudaMemcpyAsync(P.prob_geom_h.data(), P.prob_geom.p, sizeof(double) * 8 * B,
+                           cudaMemcpyDeviceToHost, s));
   FMM_CUDA(cudaStreamSynchronize(s));
-  if (hg[4] != 0.0) throw Error(FMM_ERR_NONFINITE_INPUT, "a coordinate is NaN or infinite");
-  P.lo[0] = hg[0];
-  P.lo[1] = hg[1];
-  P.lo[2] = hg[2];
-  P.D = hg[3];
+  for (int b = 0; b < B; ++b)
+    if (P.prob_geom_h[8 * b + 4] != 0.0)
+      throw Error(FMM_ERR_NONFINITE_INPUT, "a coordinate is NaN or infinite");
+  P.lo[0] = P.prob_geom_h[0];
+  P.lo[1] = P.prob_geom_h[1];
+  P.lo[2] = P.prob_geom_h[2];
+  P.D = P.prob_geom_h[3];
 
-  // ---- keys and stable sort
+  // ---- keys and stable sort (by key; for a batch, then stably by problem)
   P.keys.resize(n, s);
   P.perm.resize(n, s);
-  k_morton<<<grid(n), kT, 0, s>>>(d_xyz, n, P.geom.p, P.keys.p, P.perm.p);
+  k_morton<<<grid(n), kT, 0, s>>>(d_xyz, n, P.prob_geom.p, B > 1 ? P.prob_off.p : nullptr, B,
+                                   P.keys.p, P.perm.p);
   FMM_LAUNCH_CHECK();
   radix_sort(P.keys, P.perm, P.keys_tmp, P.perm_tmp, n, digit_shifts(0, 3 * kMaxDepth), P.s_hist,
              P.s_scan, s);
+  if (B > 1) {
+    P.s_u64a.resize(n, s);
+    P.s_i32a.resize(n, s);
+    k_problem_keys<<<grid(n), kT, 0, s>>>(n, P.perm.p, P.prob_off.p, B, P.s_u64a.p, P.s_i32a.p);
+    FMM_LAUNCH_CHECK();
+    radix_sort(P.s_u64a, P.s_i32a, P.s_u64b, P.s_i32b, n, digit_shifts(0, bits_for(B)), P.s_hist,
+               P.s_scan, s);
+    k_apply_perm<<<grid(n), kT, 0, s>>>(n, P.s_i32a.p, P.keys.p, P.perm.p, P.keys_tmp.p,
+                                         P.perm_tmp.p);
+    FMM_LAUNCH_CHECK();
+    std::swap(P.keys, P.keys_tmp);
+    std::swap(P.perm, P.perm_tmp);
+  }
   P.xyz_sorted.resize(3 * n, s);
   k_gather_xyz<<<grid(n), kT, 0, s>>>(d_xyz, P.perm.p, n, P.xyz_sorted.p);
   FMM_LAUNCH_CHECK();
 
-  // ---- boxes, level by level
+  // ---- boxes, level by level; level 0 holds one root per non-empty problem
   scope.reset(new PassScope(P, kPassBoxes));
-  size_t cap0 = std::max<size_t>(1024, 2 * (size_t)n / (size_t)P.leaf_size + 64);
+  size_t cap0 = std::max<size_t>(1024 + B, 2 * (size_t)n / (size_t)P.leaf_size + 64 + B);
   auto grow_boxes = [&](size_t need, size_t keep) {
     P.box_key.grow(std::max(need, cap0), keep, s);
     P.box_level.grow(std::max(need, cap0), keep, s);
@@ -575,20 +700,31 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
     P.box_parent.grow(std::max(need, cap0), keep, s);
     P.box_child.grow(std::max(need, cap0), keep, s);
     P.box_nchild.grow(std::max(need, cap0), keep, s);
+    P.box_prob.grow(std::max(need, cap0), keep, s);
   };
-  grow_boxes(1, 0);
-  {
-    uint64_t k0 = 0;
-    int32_t z = 0, m1 = -1, cnt = (int32_t)n;
-    FMM_CUDA(cudaMemcpyAsync(P.box_key.p, &k0, sizeof k0, cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaMemcpyAsync(P.box_level.p, &z, sizeof z, cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaMemcpyAsync(P.box_first.p, &z, sizeof z, cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaMemcpyAsync(P.box_count.p, &cnt, sizeof cnt, cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaMemcpyAsync(P.box_parent.p, &m1, sizeof m1, cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaStreamSynchronize(s));  // the host values above are stack variables
+  std::vector<uint64_t> rk;
+  std::vector<int32_t> rz, rf, rc, rm, rp;
+  for (int b = 0; b < B; ++b) {
+    const int64_t c = P.prob_off_h[b + 1] - P.prob_off_h[b];
+    if (c == 0) continue;
+    rk.push_back(0);
+    rz.push_back(0);
+    rf.push_back((int32_t)P.prob_off_h[b]);
+    rc.push_back((int32_t)c);
+    rm.push_back(-1);
+    rp.push_back(b);
   }
-  P.level_off = {0, 1};
-  int64_t nb = 1;
+  const int64_t nroots = (int64_t)rk.size();
+  grow_boxes(nroots, 0);
+  FMM_CUDA(cudaMemcpyAsync(P.box_key.p, rk.data(), 8 * nroots, cudaMemcpyHostToDevice, s));
+  FMM_CUDA(cudaMemcpyAsync(P.box_level.p, rz.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  FMM_CUDA(cudaMemcpyAsync(P.box_first.p, rf.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  FMM_CUDA(cudaMemcpyAsync(P.box_count.p, rc.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  FMM_CUDA(cudaMemcpyAsync(P.box_parent.p, rm.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  FMM_CUDA(cudaMemcpyAsync(P.box_prob.p, rp.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  FMM_CUDA(cudaStreamSynchronize(s));  // the host vectors above are temporaries
+  P.level_off = {0, (int32_t)nroots};
+  int64_t nb = nroots;
   for (int l = 0;; ++l) {
     int32_t b0 = P.level_off[l], nbl = P.level_off[l + 1] - b0;
     P.s_i32a.resize(nbl + 1, s);
@@ -601,7 +737,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
     if (nnew > 0) grow_boxes(nb + nnew, nb);
     k_split_make<<<grid(nbl), kT, 0, s>>>(l, b0, nbl, (int32_t)nb, P.s_i32a.p, P.s_i32b.p, P.keys.p,
                                            P.box_first.p, P.box_count.p, P.box_key.p, P.box_level.p,
-                                           P.box_parent.p, P.box_child.p, P.box_nchild.p);
+                                           P.box_parent.p, P.box_child.p, P.box_nchild.p,
+                                           P.box_prob.p);
     FMM_LAUNCH_CHECK();
     if (nnew == 0) break;
     nb += nnew;
@@ -613,6 +750,9 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   P.box_geo.resize(nb, s);
   k_box_geo<<<grid(nb), kT, 0, s>>>(nb, P.box_key.p, P.box_level.p, P.box_geo.p);
   FMM_LAUNCH_CHECK();
+  P.box_side.resize(nb, s);
+  k_box_side<<<grid(nb), kT, 0, s>>>(nb, P.box_level.p, P.box_prob.p, P.prob_geom.p, P.box_side.p);
+  FMM_LAUNCH_CHECK();
 
   // ---- leaves and leaf-local coordinates
   P.s_i32a.resize(nb, s);
@@ -622,8 +762,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   P.pl64.resize(n, s);
   P.pl32.resize(n, s);
   k_leaf_points<<<(int)P.nleaves, 128, 0, s>>>(P.leaves.p, P.box_geo.p, P.box_first.p,
-                                                P.box_count.p, P.xyz_sorted.p, P.lo[0], P.lo[1],
-                                                P.lo[2], P.D, P.pl64.p, P.pl32.p);
+                                                P.box_count.p, P.xyz_sorted.p, P.box_prob.p,
+                                                P.prob_geom.p, P.box_side.p, P.pl64.p, P.pl32.p);
   FMM_LAUNCH_CHECK();
 
   // ---- colleagues
@@ -634,8 +774,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
                            cudaMemcpyHostToDevice, s));
   P.colleagues.resize((size_t)26 * nb, s);
   P.ncolleagues.resize(nb, s);
-  k_colleagues<<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_key.p, loff.p, P.colleagues.p,
-                                        P.ncolleagues.p);
+  k_colleagues<<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_key.p, P.box_prob.p, loff.p,
+                                        P.colleagues.p, P.ncolleagues.p);
   FMM_LAUNCH_CHECK();
   FMM_CUDA(cudaStreamSynchronize(s));  // level_off host vector must outlive the copy
 
