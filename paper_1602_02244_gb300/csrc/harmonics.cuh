@@ -44,6 +44,7 @@ template <typename T, typename F>
 __device__ __forceinline__ void regular_stream(int p, T x, T y, T z, F &&f) {
   const T r2 = x * x + y * y + z * z;
   T dre = T(1), dim = T(0);
+#pragma unroll
   for (int m = 0; m <= p; ++m) {
     if (m > 0) {
       const T c = T(-0.5) / T(m);
@@ -53,6 +54,7 @@ __device__ __forceinline__ void regular_stream(int p, T x, T y, T z, F &&f) {
     }
     f(m, m, dre, dim);
     T pre = T(0), pim = T(0), cre = dre, cim = dim;
+#pragma unroll
     for (int n = m + 1; n <= p; ++n) {
       const T a = T(2 * n - 1) * z, s = recip_nm<T>(n, m);
       const T nre = (a * cre - r2 * pre) * s, nim = (a * cim - r2 * pim) * s;
@@ -70,6 +72,7 @@ __device__ __forceinline__ void irregular_stream(int p, T x, T y, T z, F &&f) {
   const T r2 = x * x + y * y + z * z;
   const T inv = T(1) / r2;
   T dre = T(1) / sqrt(r2), dim = T(0);
+#pragma unroll
   for (int m = 0; m <= p; ++m) {
     if (m > 0) {
       const T c = -T(2 * m - 1) * inv;
@@ -79,6 +82,7 @@ __device__ __forceinline__ void irregular_stream(int p, T x, T y, T z, F &&f) {
     }
     f(m, m, dre, dim);
     T pre = T(0), pim = T(0), cre = dre, cim = dim;
+#pragma unroll
     for (int n = m + 1; n <= p; ++n) {
       const T a = T(2 * n - 1) * z, b = T((n - 1) * (n - 1) - m * m);
       const T nre = (a * cre - b * pre) * inv, nim = (a * cim - b * pim) * inv;

@@ -9,6 +9,8 @@
 #include "eval_kernels.cuh"
 #include "harmonics.cuh"
 
+#include <type_traits>
+
 namespace fmm {
 
 namespace {
@@ -20,6 +22,48 @@ __device__ __forceinline__ double center_delta(int32_t ia, double sa, int32_t ib
 }
 
 constexpr int kAccSlots = 14;  // ceil(441 / 32): coefficients per lane for p <= 20
+
+// Per-lane coefficient sums fit in registers (at most 128 32-bit words) when
+// the order is a compile-time constant.
+template <typename T, int PT>
+constexpr bool reg_accumulate() {
+  return PT > 0 && ncoef(PT) * (int)sizeof(T) <= 4 * 128;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce every coefficient over the warp; lane k % 32 writes coefficient k
+// (and zero into the row padding up to ld).
+template <typename T, int NC>
+__device__ __forceinline__ void write_warp_sums(const T (&racc)[NC], int lane, T *row, int ld,
+                                                double *row64) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const T v = warp_sum(racc[k]);
+    if (lane == (k & 31)) {
+      row[k] = v;
+      if (row64) row64[k] = (double)v;
+    }
+  }
+  for (int k = NC + lane; k < ld; k += 32) {
+    row[k] = T(0);
+    if (row64) row64[k] = 0.0;
+  }
+}
+
+template <typename T, int NC>
+__device__ __forceinline__ void add_warp_sums(const T (&racc)[NC], int lane, T *row) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const T v = warp_sum(racc[k]);
+    if (lane == (k & 31)) row[k] += v;
+  }
+}
 
 template <typename T>
 __global__ void k_permute_charges(int64_t n, const int32_t *__restrict__ perm,
@@ -35,12 +79,13 @@ __global__ void k_permute_charges(int64_t n, const int32_t *__restrict__ perm,
 // P2M: M^_n^m = sum_j q_j conj(R_n^m((x_j - c)/a)); one warp per leaf, lanes
 // over points, a warp-private shared buffer transposes per-point harmonics
 // into per-coefficient sums.
-template <typename T>
-__global__ void k_p2m(int p, int64_t nleaves, const int32_t *__restrict__ leaves,
+template <typename T, int PT>
+__global__ void k_p2m(int p_rt, int64_t nleaves, const int32_t *__restrict__ leaves,
                       const int32_t *__restrict__ first, const int32_t *__restrict__ count,
                       const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
                       const double *__restrict__ side, T *__restrict__ M, double *__restrict__ M64,
                       int coarse) {
+  const int p = PT > 0 ? PT : p_rt;  // compile-time order unrolls the harmonic streams
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = ncoef(p), ld = coef_pitch(p), pitch = 33, lane = threadIdx.x & 31;
   T *buf = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * nc * pitch;
@@ -49,6 +94,24 @@ __global__ void k_p2m(int p, int64_t nleaves, const int32_t *__restrict__ leaves
   const int32_t b = leaves[w];
   const BoxGeo g = geo[b];
   const T inva = (T)(1.0 / side[b]);
+  if constexpr (reg_accumulate<T, PT>()) {  // per-lane sums in registers, one warp reduction
+    constexpr int NC = ncoef(PT);
+    T racc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) racc[k] = T(0);
+    const int32_t f = first[b], c = count[b];
+    for (int32_t j = lane; j < c; j += 32) {
+      const typename V4<T>::type s = src[f + j];
+      const T q = s.w;
+      regular_stream<T>(PT, s.x * inva, s.y * inva, s.z * inva, [&](int n, int m, T re, T im) {
+        racc[cidx(n, m)] += q * re;
+        if (m > 0) racc[cidx(n, -m)] -= q * im;
+      });
+    }
+    write_warp_sums<T, NC>(racc, lane, M + (int64_t)b * ld, ld,
+                           (M64 && g.level <= coarse) ? M64 + (int64_t)b * ld : nullptr);
+    return;
+  }
   T acc[kAccSlots];
 #pragma unroll
   for (int t = 0; t < kAccSlots; ++t) acc[t] = T(0);
@@ -88,12 +151,13 @@ __global__ void k_p2m(int p, int64_t nleaves, const int32_t *__restrict__ leaves
 }
 
 // P2L over X lists: L^_n^m(C) += sum_{A in X(C)} sum_{j in A} q_j conj(I_n^m((x_j - c_C)/a_C))
-template <typename T>
-__global__ void k_p2l(int p, int64_t nboxes_x, const int32_t *__restrict__ xboxes,
+template <typename T, int PT>
+__global__ void k_p2l(int p_rt, int64_t nboxes_x, const int32_t *__restrict__ xboxes,
                       const int32_t *__restrict__ xoff, const int32_t *__restrict__ xidx,
                       const int32_t *__restrict__ first, const int32_t *__restrict__ count,
                       const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
                       const double *__restrict__ side, T *__restrict__ L) {
+  const int p = PT > 0 ? PT : p_rt;  // compile-time order unrolls the harmonic streams
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = ncoef(p), ld = coef_pitch(p), pitch = 33, lane = threadIdx.x & 31;
   T *buf = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * nc * pitch;
@@ -103,6 +167,31 @@ __global__ void k_p2l(int p, int64_t nboxes_x, const int32_t *__restrict__ xboxe
   const BoxGeo gc = geo[C];
   const double ac = side[C];
   const T inva = (T)(1.0 / ac);
+  if constexpr (reg_accumulate<T, PT>()) {  // per-lane sums in registers, one warp reduction
+    constexpr int NC = ncoef(PT);
+    T racc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) racc[k] = T(0);
+    for (int32_t e = xoff[C]; e < xoff[C + 1]; ++e) {
+      const int32_t A = xidx[e];
+      const BoxGeo ga = geo[A];
+      const T sx = (T)center_delta(ga.ix, side[A], gc.ix, ac);
+      const T sy = (T)center_delta(ga.iy, side[A], gc.iy, ac);
+      const T sz = (T)center_delta(ga.iz, side[A], gc.iz, ac);
+      const int32_t f = first[A], c = count[A];
+      for (int32_t j = lane; j < c; j += 32) {
+        const typename V4<T>::type s = src[f + j];
+        const T q = s.w;
+        irregular_stream<T>(PT, (s.x + sx) * inva, (s.y + sy) * inva, (s.z + sz) * inva,
+                            [&](int n, int m, T re, T im) {
+                              racc[cidx(n, m)] += q * re;
+                              if (m > 0) racc[cidx(n, -m)] -= q * im;
+                            });
+      }
+    }
+    add_warp_sums<T, NC>(racc, lane, L + (int64_t)C * ld);
+    return;
+  }
   T acc[kAccSlots];
 #pragma unroll
   for (int t = 0; t < kAccSlots; ++t) acc[t] = T(0);
@@ -216,12 +305,13 @@ __global__ void k_to_f64(int64_t count, const Tin *__restrict__ in, double *__re
 // With X_n^{-m} = (-1)^m conj(X_n^m) every sum over m is Re(m=0) + 2 Re(m>0);
 // the gradient uses d/dz R_n^m = R_{n-1}^m, d/dx R_n^m = (R_{n-1}^{m+1} - R_{n-1}^{m-1})/2,
 // d/dy R_n^m = -i (R_{n-1}^{m-1} + R_{n-1}^{m+1})/2, regrouped per R_n^m.
-template <typename T>
-__global__ void k_l2p(int p, const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
+template <typename T, int PT>
+__global__ void k_l2p(int p_rt, const int32_t *__restrict__ leaves, const int32_t *__restrict__ first,
                       const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
                       const typename V4<T>::type *__restrict__ src,
                       const double *__restrict__ side, const T *__restrict__ L, int64_t n,
                       double *__restrict__ far) {
+  const int p = PT > 0 ? PT : p_rt;  // compile-time order unrolls the harmonic streams
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Ls = reinterpret_cast<T *>(smem_raw);
   const int nc = ncoef(p);
@@ -312,14 +402,15 @@ __global__ void k_m2p_prep(int p, int64_t nx, const int32_t *__restrict__ xboxes
 // split its W list; partial sums are combined in FP64.
 constexpr int kM2PThreads = 128;
 
-template <typename T>
+template <typename T, int PT>
 __global__ void __launch_bounds__(kM2PThreads)
-    k_m2p(int p, const int32_t *__restrict__ wleaves, const int32_t *__restrict__ woff,
+    k_m2p(int p_rt, const int32_t *__restrict__ wleaves, const int32_t *__restrict__ woff,
           const int32_t *__restrict__ widx, const int32_t *__restrict__ xslot,
           const int32_t *__restrict__ first, const int32_t *__restrict__ count,
           const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
           const double *__restrict__ side, const T *__restrict__ K, int64_t n,
           double *__restrict__ far) {
+  const int p = PT > 0 ? PT : p_rt;  // compile-time order unrolls the harmonic streams
   __shared__ double red[4][kM2PThreads];
   const int tid = threadIdx.x, ld1 = coef_pitch(p + 1);
   const int32_t B = wleaves[blockIdx.x];
@@ -426,6 +517,19 @@ void allow_smem(K kernel, size_t bytes) {
 }  // namespace
 
 // ------------------------------------------------------------ launchers
+// Calls f(std::integral_constant<int, P>) with P = p for the orders compiled
+// with a fixed trip count, else with P = 0 (runtime order).
+template <typename F>
+void with_order(int p, F &&f) {
+  switch (p) {
+    case 4: return f(std::integral_constant<int, 4>());
+    case 6: return f(std::integral_constant<int, 6>());
+    case 8: return f(std::integral_constant<int, 8>());
+    case 10: return f(std::integral_constant<int, 10>());
+    default: return f(std::integral_constant<int, 0>());
+  }
+}
+
 template <typename T>
 void launch_permute_charges(int64_t n, const int32_t *perm, const double *q,
                             const typename V4<T>::type *pl, typename V4<T>::type *src, cudaStream_t s) {
@@ -441,9 +545,15 @@ void launch_p2m(int p, int64_t nleaves, const int32_t *leaves, const int32_t *fi
   if (nleaves == 0) return;
   size_t per = (size_t)ncoef(p) * 33 * sizeof(T);
   int w = warps_for(per);
-  allow_smem(k_p2m<T>, per * w);
-  k_p2m<T><<<ceil_div(nleaves, w), 32 * w, per * w, s>>>(p, nleaves, leaves, first, count, geo, src,
-                                                          side, M, M64, coarse);
+  with_order(p, [&](auto PC) {
+    constexpr int P = decltype(PC)::value;
+    auto kern = k_p2m<T, P>;
+    const int wk = reg_accumulate<T, P>() ? 4 : w;
+    const size_t sm = reg_accumulate<T, P>() ? 0 : per * w;
+    allow_smem(kern, sm);
+    kern<<<ceil_div(nleaves, wk), 32 * wk, sm, s>>>(p, nleaves, leaves, first, count, geo, src, side,
+                                                    M, M64, coarse);
+  });
   FMM_LAUNCH_CHECK();
 }
 
@@ -454,9 +564,15 @@ void launch_p2l(int p, int64_t nx, const int32_t *xboxes, const int32_t *xoff, c
   if (nx == 0) return;
   size_t per = (size_t)ncoef(p) * 33 * sizeof(T);
   int w = warps_for(per);
-  allow_smem(k_p2l<T>, per * w);
-  k_p2l<T><<<ceil_div(nx, w), 32 * w, per * w, s>>>(p, nx, xboxes, xoff, xidx, first, count, geo,
-                                                     src, side, L);
+  with_order(p, [&](auto PC) {
+    constexpr int P = decltype(PC)::value;
+    auto kern = k_p2l<T, P>;
+    const int wk = reg_accumulate<T, P>() ? 4 : w;
+    const size_t sm = reg_accumulate<T, P>() ? 0 : per * w;
+    allow_smem(kern, sm);
+    kern<<<ceil_div(nx, wk), 32 * wk, sm, s>>>(p, nx, xboxes, xoff, xidx, first, count, geo, src,
+                                               side, L);
+  });
   FMM_LAUNCH_CHECK();
 }
 
@@ -496,7 +612,10 @@ void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *fi
                 const T *L, int64_t n, double *far, cudaStream_t s) {
   if (nleaves == 0) return;
   size_t sm = (size_t)ncoef(p) * sizeof(T);
-  k_l2p<T><<<(unsigned)nleaves, 64, sm, s>>>(p, leaves, first, count, geo, src, side, L, n, far);
+  with_order(p, [&](auto PC) {
+    k_l2p<T, decltype(PC)::value><<<(unsigned)nleaves, 64, sm, s>>>(p, leaves, first, count, geo, src,
+                                                                    side, L, n, far);
+  });
   FMM_LAUNCH_CHECK();
 }
 
@@ -509,8 +628,10 @@ void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, 
   const int64_t tot = nx * ncoef(p + 1);
   k_m2p_prep<T><<<ceil_div(tot, 256), 256, 0, s>>>(p, nx, xboxes, M, K);
   FMM_LAUNCH_CHECK();
-  k_m2p<T><<<(unsigned)nw, kM2PThreads, 0, s>>>(p, wleaves, woff, widx, xslot, first, count, geo, src,
-                                                side, K, n, far);
+  with_order(p, [&](auto PC) {
+    k_m2p<T, decltype(PC)::value><<<(unsigned)nw, kM2PThreads, 0, s>>>(
+        p, wleaves, woff, widx, xslot, first, count, geo, src, side, K, n, far);
+  });
   FMM_LAUNCH_CHECK();
 }
 
