@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--leaf", type=int, default=0, help="leaf size; 0 = autotune (default)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--m2l-path", default="auto", choices=["auto", "simt", "tensor"],
+                    help="M2L engine of the mixed path: auto (tensor cores), simt (FP32 CUDA "
+                         "cores), tensor")
     ap.add_argument("--cpu-sample", type=int, default=1048576,
                     help="points in the oracle's CPU-baseline sample")
     ap.add_argument("--ref-sample", type=int, default=262144,
@@ -59,6 +62,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-problem leg")
+    ap.add_argument("--lattice", action="store_true",
+                    help="add plan/eval time and peak device memory vs N on uniform lattices")
     return ap.parse_args()
 
 
@@ -241,6 +246,51 @@ def batched_leg(dev, steps, warmup):
                     "launch per step over all 256 problems"}
 
 
+def lattice_leg(dev, order=8):
+    """The paper's FMM workload (§4.1): uniform lattices of growing N, time of
+    the precalculation (plan) and of the mat-vec (eval), and the peak device
+    memory of the plan, all in FP64 and mixed precision."""
+    import torch
+    from paper_1602_02244_gb300 import binding
+    L = binding.library()
+    L.fmm_memory_usage.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                   ctypes.c_int]
+    rows = []
+    for side in (16, 32, 64, 128, 160):
+        g = (np.arange(side) + 0.5) / side
+        xyz = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+        n = len(xyz)
+        X = torch.tensor(xyz, device=dev)
+        Q = torch.ones(n, dtype=torch.float64, device=dev)
+        for prec in ("mixed", "fp64"):
+            torch.cuda.synchronize()
+            cur, peak = ctypes.c_uint64(), ctypes.c_uint64()
+            L.fmm_memory_usage(ctypes.byref(cur), ctypes.byref(peak), 1)
+            base = cur.value
+            t0 = time.perf_counter()
+            plan = binding.Plan(X, leaf_size=64, order=order, precision=prec)
+            plan.eval(Q)  # operators and workspace
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.rebuild(X)
+            e1.record()
+            e1.synchronize()
+            t_plan = e0.elapsed_time(e1)
+            e0.record()
+            plan.eval(Q)
+            e1.record()
+            e1.synchronize()
+            t_eval = e0.elapsed_time(e1)
+            L.fmm_memory_usage(ctypes.byref(cur), ctypes.byref(peak), 0)
+            rows.append({"n": n, "precision": prec, "plan_ms": t_plan, "eval_ms": t_eval,
+                         "peak_bytes": int(peak.value - base),
+                         "bytes_per_point": (peak.value - base) / n})
+            plan.close()
+    return rows
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -267,7 +317,8 @@ def run_ours(args):
     xyz_np, q_np = workloads.plummer_problem(n, rank)
     X = torch.tensor(xyz_np, device=dev)
     Q = torch.tensor(q_np, device=dev)
-    plan = binding.Plan(X, leaf_size=S, order=p, precision=args.precision)  # S = 0: autotune
+    plan = binding.Plan(X, leaf_size=S, order=p, precision=args.precision,
+                        m2l_path=args.m2l_path)  # S = 0: autotune
     S = plan.sizes()["leaf_size"]
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     grad = torch.empty(n, 3, dtype=torch.float64, device=dev)
@@ -326,6 +377,13 @@ def run_ours(args):
     nc = (p + 1) ** 2
     work = {"P2P": ("alu", 20.0 * pairs / 1e12, "TFLOP/s", fp32_peak),
             "M2L": ("alu", 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s", fp32_peak)}
+    m2l_tensor = args.precision == "mixed" and p <= 10 and args.m2l_path != "simt"
+    if m2l_tensor:
+        # TF32 tensor peak: the measured sustained bf16 rate x the nominal
+        # tf32/bf16 ratio (1.1 / 2.25 dense PFLOP/s); algorithmic flops count
+        # one product, not the three of the hi/lo split
+        tf32_peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
+        work["M2L"] = ("tensor", 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s", tf32_peak)
     dom = max(pass_ms, key=pass_ms.get)
     if dom in work:
         bound, units, unit, peak = work[dom]
@@ -335,9 +393,12 @@ def run_ours(args):
         achieved = None
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "peak_source": "FP32: %d SMs x %d lanes x 2 flop x %.0f MHz" % (sms, FP32_LANES_PER_SM, max_mhz)
-            if bound == "alu" else "MEASURED_PEAKS.json hbm_gbs"}
-    other = {k: {"achieved": v[1] / (pass_ms[k] / 1e3), "unit": v[2], "frac": v[1] / (pass_ms[k] / 1e3) / v[3]}
+            "peak_source": ("FP32: %d SMs x %d lanes x 2 flop x %.0f MHz" % (sms, FP32_LANES_PER_SM, max_mhz)
+                            if bound == "alu" else
+                            "TF32 = measured sustained bf16 x 1.1/2.25 (of measured)" if bound == "tensor"
+                            else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
+    other = {k: {"bound": v[0], "achieved": v[1] / (pass_ms[k] / 1e3), "unit": v[2],
+                 "peak": v[3], "frac": v[1] / (pass_ms[k] / 1e3) / v[3]}
              for k, v in work.items() if pass_ms.get(k)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -348,6 +409,8 @@ def run_ours(args):
                                    "step = plan (keys, sort, octree, U/V/W/X lists) + eval (phi and "
                                    "grad)" % (n, p, S, "autotuned" if args.leaf == 0 else "fixed",
                                               args.precision),
+                       "m2l": "tensor cores (tcgen05 TF32, 3-product split)" if m2l_tensor
+                              else "CUDA cores",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MB flush between steps; working set >> L2",
                        "boxes": sizes["nboxes"], "levels": sizes["nlevels"], "U": sizes["nu"],
@@ -423,6 +486,8 @@ def run_ours(args):
 
     if not args.no_batch:
         line["batched"] = batched_leg(dev, args.steps, args.warmup)
+    if args.lattice:
+        line["lattice"] = lattice_leg(dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, ref = cpu_baseline(args.cpu_sample, p, S, (xyz_np, q_np, sel))

@@ -66,7 +66,10 @@ typedef struct {
   int coarse_fp64_levels; /* MIXED: M2M/L2L into levels <= this run in FP64;
                              0 = default (3), negative = none                 */
   int max_depth;          /* deepest level, 1..21; 0 = default (21)           */
-  int reserved[5];        /* must be zero                                     */
+  int m2l_path;           /* MIXED, order <= 10: 0 = default (tensor cores),
+                             1 = FP32 CUDA cores, 2 = tensor cores (tcgen05,
+                             three-product TF32 split)                        */
+  int reserved[4];        /* must be zero                                     */
 } fmm_opts;
 
 /* Build a plan for n points (d_xyz: device, n x 3 FP64).
@@ -174,6 +177,26 @@ fmm_status fmm_plan_export(fmm_plan_t plan, int which, void *h_dst, size_t bytes
 #define FMM_NPASS 12
 fmm_status fmm_profile(fmm_plan_t plan, int enable);
 fmm_status fmm_profile_read(fmm_plan_t plan, double ms[FMM_NPASS], int64_t launches[FMM_NPASS]);
+
+/* Diagnostic of the tensor-core path: one CTA computes D[128][n] =
+ * A[128][k] B[n][k]^T with tcgen05.mma (kind::tf32).  mode 1: one TF32
+ * product; mode 3: the three-product TF32 split with FP32-level accuracy.
+ * Device pointers, row-major FP32; n a multiple of 16 in 16..256, k a
+ * multiple of 8, and the four operand halves (2*128*k + 2*n*k floats) at most
+ * 200 KB, else FMM_ERR_INVALID_ARG.  Synchronous.  FMM_ERR_TIMEOUT if the bounded wait for MMA
+ * completion gave up. */
+fmm_status fmm_tc_selftest(int n, int k, const float *d_a, const float *d_b, float *d_d, int mode,
+                           void *stream);
+
+/* Synchronise `stream`, then report FMM_ERR_TIMEOUT (once) if a bounded
+ * device-side wait of this plan's kernels gave up since the last call, else
+ * FMM_OK.  Results of an evaluation that timed out are not valid. */
+fmm_status fmm_sync(fmm_plan_t plan, void *stream);
+
+/* Device memory held by this library's plans on the current device: bytes
+ * in use now and the high-water mark since the last reset (reset_peak != 0
+ * resets it after reading).  Either output may be NULL. */
+fmm_status fmm_memory_usage(uint64_t *current, uint64_t *peak, int reset_peak);
 
 /* Number of kernels this library has launched in this process so far. */
 uint64_t fmm_kernel_launches(void);

@@ -19,7 +19,7 @@ _STATUS = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_CUDA", 3: "FMM_ERR
            4: "FMM_ERR_TIMEOUT", 5: "FMM_ERR_NONFINITE_INPUT", 6: "FMM_ERR_UNSUPPORTED"}
 
 EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_plan_set_points",
-           "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_plan_sizes", "fmm_plan_export", "fmm_plan_destroy",
+           "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_sync", "fmm_plan_sizes", "fmm_plan_export", "fmm_plan_destroy",
            "fmm_status_string", "fmm_last_error_message")
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
@@ -35,7 +35,8 @@ class FMMError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("coarse_fp64_levels", ctypes.c_int),
-                ("max_depth", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("max_depth", ctypes.c_int), ("m2l_path", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -61,6 +62,7 @@ def library():
         L.fmm_eval.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.fmm_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.fmm_eval_graph.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.fmm_sync.argtypes = [_vp, _vp]
         L.fmm_solve_host.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _vp]
         L.fmm_plan_sizes.argtypes = [_vp, ctypes.POINTER(_i64)]
         L.fmm_plan_export.argtypes = [_vp, _int, _vp, ctypes.c_size_t]
@@ -108,7 +110,7 @@ class Plan:
     """
 
     def __init__(self, points, leaf_size=64, order=8, precision="fp64", coarse_fp64_levels=0,
-                 max_depth=0, stream=None, offsets=None):
+                 max_depth=0, stream=None, offsets=None, m2l_path="auto"):
         L = library()
         self.device = points.device
         self.n = int(points.shape[0])
@@ -117,6 +119,7 @@ class Plan:
         opts.precision = {"fp64": FMM_FP64, "mixed": FMM_MIXED}[precision]
         opts.coarse_fp64_levels = coarse_fp64_levels
         opts.max_depth = max_depth
+        opts.m2l_path = {"auto": 0, "simt": 1, "tensor": 2}[m2l_path]
         self.precision, self.order, self.leaf_size = precision, order, leaf_size
         h = _vp()
         self.nproblems = 1 if offsets is None else len(offsets) - 1
@@ -191,6 +194,12 @@ class Plan:
         with torch.cuda.device(self.device):
             _check(library().fmm_eval_graph(self._h, _ptr(q), _ptr(phi), _ptr(grad), _ptr(w),
                                             _ptr(dq), _ptr(dx), _vp(s.cuda_stream)))
+
+    def sync(self, stream=None):
+        """Synchronise the stream; raises FMMError(FMM_ERR_TIMEOUT) if a
+        bounded device-side wait of this plan gave up since the last call."""
+        with torch.cuda.device(self.device):
+            _check(library().fmm_sync(self._h, _stream(stream)))
 
     def solve_host(self, xyz, q, grad=True, stream=None):
         """End to end on host arrays: H2D, rebuild, eval, D2H (fmm_solve_host)."""

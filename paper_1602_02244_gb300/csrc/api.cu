@@ -65,6 +65,8 @@ void check_opts(const fmm_opts *o) {
     throw Error(FMM_ERR_INVALID_ARG, "opts.precision must be FMM_FP64 or FMM_MIXED");
   if (o->max_depth < 0 || o->max_depth > kMaxDepth)
     throw Error(FMM_ERR_INVALID_ARG, "opts.max_depth must be in 0..21");
+  if (o->m2l_path < 0 || o->m2l_path > 2)
+    throw Error(FMM_ERR_INVALID_ARG, "opts.m2l_path must be 0, 1 or 2");
   for (int r : o->reserved)
     if (r != 0) throw Error(FMM_ERR_INVALID_ARG, "opts.reserved must be zero");
 }
@@ -116,7 +118,8 @@ void release_plan(fmm_plan_impl &P) {
   P.s_i32a.release(); P.s_i32b.release(); P.s_i32c.release(); P.s_hist.release();
   P.s_scan.release(); P.s_u64a.release(); P.s_u64b.release(); P.s_total.release();
   P.ca_off.release(); P.ca_idx.release(); P.m2l_src.release(); P.m2l_slots.release();
-  P.m2l_nslots.release(); P.ops.m2l32p.release();
+  P.m2l_nslots.release(); P.ops.m2l32p.release(); P.ops.m2l_tc.release(); P.Mhi.release();
+  P.Mlo.release(); P.dev_err.release();
   P.xslot.release(); P.K64.release(); P.K32.release(); P.box_prob.release();
   P.box_side.release(); P.prob_off.release(); P.prob_geom.release();
 }
@@ -144,6 +147,7 @@ fmm_status fmm_plan_create(const double *d_xyz, int64_t n, int leaf_size, int or
     P->autotune = leaf_size == 0;
     P->stream = (cudaStream_t)stream;
     if (opts) {
+      P->m2l_path = opts->m2l_path;
       P->precision = opts->precision;
       P->coarse_fp64_levels = opts->coarse_fp64_levels == 0 ? 3 : opts->coarse_fp64_levels;
       P->max_depth = opts->max_depth == 0 ? kMaxDepth : opts->max_depth;
@@ -188,6 +192,7 @@ fmm_status fmm_plan_create_batch(const double *d_xyz, const int64_t *h_offsets, 
     P->nproblems = nproblems;
     P->prob_off_h.assign(h_offsets, h_offsets + nproblems + 1);
     if (opts) {
+      P->m2l_path = opts->m2l_path;
       P->precision = opts->precision;
       P->coarse_fp64_levels = opts->coarse_fp64_levels == 0 ? 3 : opts->coarse_fp64_levels;
       P->max_depth = opts->max_depth == 0 ? kMaxDepth : opts->max_depth;
@@ -424,6 +429,39 @@ fmm_status fmm_profile_read(fmm_plan_t plan, double ms[FMM_NPASS], int64_t launc
 }
 
 uint64_t fmm_kernel_launches(void) { return launch_count(); }
+
+fmm_status fmm_memory_usage(uint64_t *current, uint64_t *peak, int reset_peak) {
+  return guarded([&] {
+    cudaMemPool_t pool = pool_for_current_device();
+    uint64_t c = 0, h = 0;
+    FMM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &c));
+    FMM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &h));
+    if (current) *current = c;
+    if (peak) *peak = h;
+    if (reset_peak) {
+      uint64_t z = 0;
+      FMM_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &z));
+    }
+  });
+}
+
+fmm_status fmm_sync(fmm_plan_t plan, void *stream) {
+  if (!plan) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
+  fmm_status st = FMM_OK;
+  fmm_status g = guarded([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    FMM_CUDA(cudaStreamSynchronize(s));
+    if (plan->dev_err.p) {
+      int h = 0;
+      FMM_CUDA(cudaMemcpy(&h, plan->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+      if (h) {
+        FMM_CUDA(cudaMemset(plan->dev_err.p, 0, sizeof(int)));
+        st = fail(FMM_ERR_TIMEOUT, "a bounded device-side wait gave up (tensor-core M2L)");
+      }
+    }
+  });
+  return g != FMM_OK ? g : st;
+}
 
 fmm_status fmm_plan_destroy(fmm_plan_t plan) {
   if (!plan) return FMM_OK;

@@ -121,7 +121,14 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   }
   {
     PassScope ps_(P, kPassM2L);
-    if (p <= kM2LStagedMaxOrder)
+    if (P.m2l_tc) {
+      const size_t kt = m2l_tc_pitch(p);
+      P.Mhi.resize((size_t)P.nboxes * kt, s);
+      P.Mlo.resize((size_t)P.nboxes * kt, s);
+      launch_m2l_tc(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_src.p, P.m2l_slots.p, P.m2l_nslots.p,
+                    P.m2l_order.p, P.nboxes, P.M32.p, P.Mhi.p, P.Mlo.p, P.ops.m2l_tc.p, P.L32.p,
+                    P.dev_err.p, s);
+    } else if (p <= kM2LStagedMaxOrder)
       launch_m2l_staged(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_src.p, P.m2l_slots.p, P.m2l_nslots.p,
                         P.m2l_order.p, P.M32.p, P.ops.m2l32p.p, P.L32.p, s);
     else
@@ -178,6 +185,10 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
 void eval_fmm(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad) {
   if (P.n == 0) return;
   build_operators(P);
+  if (!P.dev_err.p) {
+    P.dev_err.resize(1, P.stream);
+    FMM_CUDA(cudaMemsetAsync(P.dev_err.p, 0, sizeof(int), P.stream));
+  }
   if (P.precision == FMM_FP64) eval_fp64(P, d_q, d_phi, d_grad);
   else eval_mixed(P, d_q, d_phi, d_grad);
 }

@@ -61,6 +61,13 @@ void launch_m2l_staged(int p, int64_t ntiles, const M2LTile *tiles, const int32_
                        const int16_t *slots, const int32_t *nslots, const int32_t *order,
                        const float *M, const float *opsp, float *L, cudaStream_t s);
 
+// m2l_tc.cu: splits M into Mhi/Mlo (pitch m2l_rows(p)), then contracts on
+// the tensor cores; err is set if a bounded wait gave up
+void launch_m2l_tc(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *table,
+                   const int16_t *slots, const int32_t *nslots, const int32_t *order, int64_t nb,
+                   const float *M, float *Mhi, float *Mlo, const float *opt, float *L, int *err,
+                   cudaStream_t s);
+
 // p2p.cu
 template <typename T>
 void launch_p2p(int64_t nleaves, const int32_t *leaves, const int32_t *uoff, const int32_t *uidx,

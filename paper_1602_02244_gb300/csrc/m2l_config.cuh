@@ -31,6 +31,7 @@ inline M2LShape m2l_shape(int order) {
 }
 
 inline int m2l_tile_size(int order, int /*precision*/) { return m2l_shape(order).tile; }
+constexpr int kM2LTensorTile = 128;  // targets per CTA of the tensor-core path (MMA M)
 
 // Staged FP32 kernel (orders up to 10): 64 targets x 16*RPT rows per CTA,
 // one whole slot (operator + gathered multipoles) per pipeline stage.

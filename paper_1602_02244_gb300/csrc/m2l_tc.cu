@@ -1,0 +1,360 @@
+// m2l_tc.cu -- per-level M2L on the 5th-generation tensor cores (§2.2: the
+// translation that dominates FMM run time, applied as a dense contraction
+// with one precomputed operator per relative offset).
+//
+// A CTA owns 128 target boxes of one level with the same octant parity (the
+// M = 128 rows of the MMA).  For every occupied offset slot it contracts
+//   D[t][n] += sum_k M_src(t)[k] T_slot[n][k]     (N = rows of the operator)
+// with tcgen05.mma kind::tf32, accumulating all slots in one tensor-memory
+// tile.  FP32 accuracy comes from the three-product split
+//   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// where X_hi is X rounded to TF32 and X_lo is X - X_hi rounded to TF32.  The multipoles are split once per evaluation
+// (k_split_tf32) and the operators at plan time, already in the K-major
+// core-matrix order the MMA reads.  Each slot is contracted in K chunks of 32;
+// chunks are copied into a ring of shared-memory stages with cp.async while
+// the tensor core works on earlier stages, and a stage is refilled only after
+// the mbarrier signalled by tcgen05.commit says its MMAs have finished.  All
+// waits are bounded; a timeout sets an error word and the CTA still frees its
+// tensor memory.
+#include <cstring>
+#include <type_traits>
+
+#include "eval_kernels.cuh"
+#include "m2l_config.cuh"
+#include "tcgen05.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int kTcTile = 128;     // targets per CTA = MMA M
+constexpr int kTcKC = 32;        // K per stage
+constexpr long long kTcWaitCycles = 400000000ll;  // ~0.2 s: far beyond any legitimate wait
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(tc::smem_addr(smem)),
+               "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Mhi/Mlo[b][k] (pitch kt, zero beyond the nc coefficients) from M[b][k] (pitch ld)
+__global__ void k_split_tf32(int64_t nb, int nc, int ld, int kt, const float *__restrict__ M,
+                             float *__restrict__ Mhi, float *__restrict__ Mlo) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb * kt) return;
+  const int64_t b = i / kt;
+  const int k = (int)(i - b * kt);
+  float hi = 0.f, lo = 0.f;
+  if (k < nc) tc::split_tf32(M[b * ld + k], hi, lo);
+  Mhi[i] = hi;
+  Mlo[i] = lo;
+}
+
+__host__ __device__ constexpr int tc_k(int p) { return (ncoef(p) + kTcKC - 1) / kTcKC * kTcKC; }
+
+// The tensor core's FP32 accumulation does not round to nearest, so its error
+// grows with the number of accumulations into one tile.  Every slot therefore
+// starts a fresh accumulator (two in tensor memory, by slot parity), and the
+// finished slot is drained with tcgen05.ld into per-thread FP32 registers
+// (round-to-nearest adds) while the tensor core works on the next slot.
+//
+// Warp roles (no block-wide barrier between setup and teardown):
+//   warps 0-3  drain: warp w owns tensor-memory lanes 32w..32w+31, i.e. the
+//              targets 32w..32w+31 of the tile, and adds finished slots into
+//              registers; they write L at the end;
+//   warp 4     one thread issues the MMAs and the tcgen05.commit arrivals;
+//   warps 5-6  producers: gather the A rows (source multipoles) and copy the
+//              operator slab of each (slot, K chunk) stage with cp.async, then
+//              fence their writes into the async proxy and arrive on the
+//              stage's `full` barrier.
+// Barriers: full[s] (64 producer arrivals) -> MMA; empty[s] (commit) ->
+// producers; accf[a] (commit after a slot) -> drain; acce[a] (128 drain
+// arrivals) -> MMA before it overwrites accumulator a.
+constexpr int kTcDrainWarps = 4;
+constexpr int kTcProdWarps = 2;
+constexpr int kTcProdThreads = 32 * kTcProdWarps;
+constexpr int kTcThreads = 32 * (kTcDrainWarps + 1 + kTcProdWarps);
+constexpr int kTcRowsPerProd = kTcTile * (kTcKC / 4) / kTcProdThreads;  // 16
+
+// Wait for a phase of an mbarrier; gives up after kTcWaitCycles or as soon as
+// another thread of the CTA gave up (the abort word), so that one timeout does
+// not make every later wait of the CTA run to its own limit.
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity, volatile int *abort) {
+  const long long t0 = clock64();
+  while (!tc::mbar_try_wait(mbar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kTcWaitCycles) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+template <int NT, int NSTAGE>
+__global__ void __launch_bounds__(kTcThreads)
+    k_m2l_tc(int p, int kt, const M2LTile *__restrict__ tiles, const int32_t *__restrict__ table,
+             const int16_t *__restrict__ slots, const int32_t *__restrict__ nslots,
+             const int32_t *__restrict__ order, const float *__restrict__ Mhi,
+             const float *__restrict__ Mlo, const float *__restrict__ opt, float *__restrict__ L,
+             int *__restrict__ err) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t full[NSTAGE], empty[NSTAGE], accf[2], acce[2], done;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_word;
+  volatile int *abort = &abort_word;
+  constexpr int N = NT;
+  constexpr uint32_t kCols = N <= 32 ? 32 : N <= 64 ? 64 : 128;  // per accumulator
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nc = ncoef(p), ld = coef_pitch(p), nch = kt / kTcKC;
+  constexpr uint32_t a_bytes = kTcTile * kTcKC * 4, b_bytes = (uint32_t)N * kTcKC * 4;
+  constexpr uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  const M2LTile tile = tiles[blockIdx.x];
+  const int ns = nslots[blockIdx.x];
+  const int total = ns * nch;
+
+  if (total == 0) {  // no interaction-list source anywhere in the tile
+    for (int i = tid; i < tile.count * nc; i += kTcThreads) {
+      const int tt = i / nc, r = i - tt * nc;
+      L[(size_t)order[tile.start + tt] * ld + r] = 0.f;
+    }
+    return;
+  }
+  if (tid == 0) {
+    for (int q = 0; q < NSTAGE; ++q) {
+      tc::mbar_init(&full[q], kTcProdThreads);
+      tc::mbar_init(&empty[q], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&accf[a], 1);
+      tc::mbar_init(&acce[a], 32 * kTcDrainWarps);
+    }
+    tc::mbar_init(&done, 1);
+    abort_word = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, 2 * kCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+
+  float acc[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) acc[i] = 0.f;
+
+  if (warp < kTcDrainWarps) {
+    // ---------------------------------------------------------------- drain
+    for (int j = 0; j < ns; ++j) {
+      const int a = j & 1;
+      // warp-uniform outcome: tcgen05.ld is a warp-collective instruction
+      const bool ok = __all_sync(0xffffffffu, tc_wait(&accf[a], (uint32_t)(j >> 1) & 1, abort));
+      if (!ok) break;
+      tc::fence_after_sync();
+      const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * kCols);
+#pragma unroll
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(base + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(&acce[a]);
+    }
+  } else if (warp == kTcDrainWarps) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_tf32(kTcTile, N);
+      constexpr uint32_t sbo = (kTcKC / 4) * 128;
+      bool ok = true;
+      for (int j = 0; j < ns && ok; ++j) {
+        const int a = j & 1;
+        if (j >= 2) {
+          ok = tc_wait(&acce[a], (uint32_t)((j >> 1) - 1) & 1, abort);
+          if (!ok) break;
+          tc::fence_after_sync();
+        }
+        const uint32_t dtm = tmem + (uint32_t)(a * kCols);
+        for (int c = 0; c < nch; ++c) {
+          const int st = j * nch + c;
+          ok = tc_wait(&full[st % NSTAGE], (uint32_t)(st / NSTAGE) & 1, abort);
+          if (!ok) break;
+          tc::fence_after_sync();
+          const uint32_t base = tc::smem_addr(sm + (st % NSTAGE) * stage_bytes);
+          const uint32_t ah = base, al = base + a_bytes, bh = base + 2 * a_bytes,
+                         bl = base + 2 * a_bytes + b_bytes;
+#pragma unroll
+          for (int ks = 0; ks < kTcKC / 8; ++ks) {
+            const uint32_t off = (uint32_t)ks * 256;
+            const uint64_t dah = tc::smem_desc(ah + off, 128, sbo);
+            const uint64_t dal = tc::smem_desc(al + off, 128, sbo);
+            const uint64_t dbh = tc::smem_desc(bh + off, 128, sbo);
+            const uint64_t dbl = tc::smem_desc(bl + off, 128, sbo);
+            tc::mma_tf32(dtm, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            tc::mma_tf32(dtm, dah, dbl, idesc, 1u);
+            tc::mma_tf32(dtm, dal, dbh, idesc, 1u);
+          }
+          tc::mma_commit(&empty[st % NSTAGE]);
+        }
+        if (ok) tc::mma_commit(&accf[a]);
+      }
+      // every MMA issued above has completed before tensor memory is freed
+      tc::mma_commit(&done);
+      tc::mbar_wait_bounded(&done, 0, kTcWaitCycles);
+    }
+  } else {
+    // ---------------------------------------------------------------- producers
+    const int pt = tid - 32 * (kTcDrainWarps + 1);
+    const int rlo = pt & 7, kk = pt >> 3;  // rows rlo + 8i, K piece kk (4 floats)
+    const int px = tile.parity & 1, py = (tile.parity >> 1) & 1, pz = (tile.parity >> 2) & 1;
+    const int32_t *tab = table + (size_t)blockIdx.x * 216 * kTcTile;
+    const int16_t *sl = slots + (size_t)blockIdx.x * 216;
+    int32_t rows[kTcRowsPerProd], next[kTcRowsPerProd];
+    int code = 0, next_code = 0;
+    auto fetch = [&](int j) {  // source rows and operator code of slot j
+      const int slot = sl[j];
+      const int sx = slot / 36, sy = (slot / 6) % 6, sz = slot % 6;
+      next_code = (2 + px - sx + 3) * 49 + (2 + py - sy + 3) * 7 + (2 + pz - sz + 3);
+#pragma unroll
+      for (int i = 0; i < kTcRowsPerProd; ++i) next[i] = tab[slot * kTcTile + rlo + 8 * i];
+    };
+    fetch(0);
+    int st = 0, signalled = 0;
+    for (; st < total; ++st) {
+      const int j = st / nch, c = st - j * nch, s = st % NSTAGE;
+      if (st >= NSTAGE && !tc_wait(&empty[s], (uint32_t)(st / NSTAGE - 1) & 1, abort)) break;
+      if (c == 0) {
+#pragma unroll
+        for (int i = 0; i < kTcRowsPerProd; ++i) rows[i] = next[i];
+        code = next_code;
+        if (j + 1 < ns) fetch(j + 1);  // consumed one slot later
+      }
+      unsigned char *base = sm + s * stage_bytes;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float *Ms = h ? Mlo : Mhi;
+#pragma unroll
+        for (int i = 0; i < kTcRowsPerProd; ++i) {
+          const int r = rlo + 8 * i;
+          const int32_t A = rows[i];
+          const float *src = Ms + (size_t)(A >= 0 ? A : 0) * kt + c * kTcKC + 4 * kk;
+          cp_async16(base + h * a_bytes + tc::kmajor_offset(r, 4 * kk, kTcKC), src, A >= 0 ? 16 : 0);
+        }
+      }
+      const float *bsrc = opt + ((size_t)code * nch + c) * 2 * N * kTcKC;
+#pragma unroll
+      for (uint32_t q = pt; q < 2 * b_bytes / 16; q += kTcProdThreads)
+        cp_async16(base + 2 * a_bytes + 16 * q, bsrc + 4 * q, 16);
+      cp_async_commit();
+      if (st >= NSTAGE - 1) {  // the stage issued NSTAGE - 1 steps ago has landed
+        cp_async_wait<NSTAGE - 1>();
+        tc::fence_async_shared();
+        tc::mbar_arrive(&full[(st - (NSTAGE - 1)) % NSTAGE]);
+        ++signalled;
+      }
+    }
+    cp_async_wait<0>();
+    if (!*abort) {
+      tc::fence_async_shared();
+      for (; signalled < st; ++signalled) tc::mbar_arrive(&full[signalled % NSTAGE]);
+    }
+  }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  const bool failed = *abort != 0;
+  if (failed && tid == 0) atomicExch(err, 1);
+  if (!failed && warp < kTcDrainWarps) {
+    const int t = warp * 32 + lane;
+    if (t < tile.count) {
+      const int32_t B = order[tile.start + t];
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < nc) L[(size_t)B * ld + i] = acc[i];
+    }
+  }
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * kCols);
+}
+
+// round to the nearest TF32 value, ties away from zero (as cvt.rna.tf32.f32)
+float round_tf32_host(float v) {
+  uint32_t bits;
+  std::memcpy(&bits, &v, 4);
+  bits = (bits + 0x1000u) & 0xFFFFE000u;
+  float h;
+  std::memcpy(&h, &bits, 4);
+  return h;
+}
+
+}  // namespace
+
+// operand sizes: N = m2l_rows(p) output rows (a multiple of 16, the MMA N and
+// tensor-memory columns), K = tc_k(p) input coefficients (a multiple of the
+// 32-wide K stage)
+size_t m2l_tc_operator_floats(int p) {
+  return (size_t)343 * (tc_k(p) / kTcKC) * 2 * m2l_rows(p) * kTcKC;
+}
+
+size_t m2l_tc_pitch(int p) { return (size_t)tc_k(p); }
+
+// operators for the tensor-core path: per offset code and K chunk, the hi and
+// lo halves of T[n][k] (n, k < nc; zero padded to N rows and K columns) in
+// the K-major core-matrix layout of an N x 32 operand
+void pack_m2l_tc_operators(int p, const double *m2l_in_major, float *out) {
+  const int nc = ncoef(p), N = m2l_rows(p), nch = tc_k(p) / kTcKC;
+  const size_t nn = (size_t)nc * nc, slab = (size_t)N * kTcKC;
+  for (int code = 0; code < 343; ++code)
+    for (int c = 0; c < nch; ++c) {
+      float *hi = out + ((size_t)code * nch + c) * 2 * slab, *lo = hi + slab;
+      for (int n = 0; n < N; ++n)
+        for (int kl = 0; kl < kTcKC; ++kl) {
+          const int k = c * kTcKC + kl;
+          const float v = (n < nc && k < nc) ? (float)m2l_in_major[code * nn + (size_t)k * nc + n] : 0.f;
+          const float h = round_tf32_host(v);
+          const uint32_t o = tc::kmajor_offset(n, kl, kTcKC) / 4;
+          hi[o] = h;
+          lo[o] = round_tf32_host(v - h);
+        }
+    }
+}
+
+void launch_m2l_tc(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *table,
+                   const int16_t *slots, const int32_t *nslots, const int32_t *order, int64_t nb,
+                   const float *M, float *Mhi, float *Mlo, const float *opt, float *L, int *err,
+                   cudaStream_t s) {
+  if (ntiles == 0) return;
+  const int nc = ncoef(p), ld = coef_pitch(p), kt = tc_k(p), N = m2l_rows(p);
+  k_split_tf32<<<ceil_div(nb * kt, 256), 256, 0, s>>>(nb, nc, ld, kt, M, Mhi, Mlo);
+  FMM_LAUNCH_CHECK();
+  // four stages where they fit in the 227 KB of shared memory per CTA, else three
+  auto run = [&](auto NC) {
+    constexpr int NTT = decltype(NC)::value;
+    constexpr size_t stage = (size_t)2 * (kTcTile + NTT) * kTcKC * 4;
+    constexpr int kStages = 4 * stage + 1024 <= 227 * 1024 ? 4 : 3;
+    const size_t smem = kStages * stage;
+    auto kern = k_m2l_tc<NTT, kStages>;
+    FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)ntiles, kTcThreads, smem, s>>>(p, kt, tiles, table, slots, nslots, order, Mhi,
+                                                    Mlo, opt, L, err);
+  };
+  switch (N) {
+    case 16: run(std::integral_constant<int, 16>()); break;
+    case 32: run(std::integral_constant<int, 32>()); break;
+    case 48: run(std::integral_constant<int, 48>()); break;
+    case 64: run(std::integral_constant<int, 64>()); break;
+    case 96: run(std::integral_constant<int, 96>()); break;
+    case 112: run(std::integral_constant<int, 112>()); break;
+    case 128: run(std::integral_constant<int, 128>()); break;
+    default: throw Error(FMM_ERR_UNSUPPORTED, "tensor-core M2L: unsupported operator size");
+  }
+  FMM_LAUNCH_CHECK();
+}
+
+}  // namespace fmm

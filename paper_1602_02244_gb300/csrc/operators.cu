@@ -172,6 +172,14 @@ void build_operators(fmm_plan_impl &P) {
                              cudaMemcpyHostToDevice, s));
     FMM_CUDA(cudaStreamSynchronize(s));
   }
+  if (p <= kM2LStagedMaxOrder) {  // tensor-core operators: TF32 halves, core-matrix order
+    std::vector<float> packed(m2l_tc_operator_floats(p));
+    pack_m2l_tc_operators(p, m2l.data(), packed.data());
+    P.ops.m2l_tc.resize(packed.size(), s);
+    FMM_CUDA(cudaMemcpyAsync(P.ops.m2l_tc.p, packed.data(), packed.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
+  }
   up(m2m, P.ops.m2m64, P.ops.m2m32);
   up(l2l, P.ops.l2l64, P.ops.l2l32);
   P.ops.order = p;

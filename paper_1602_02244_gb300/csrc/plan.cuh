@@ -21,6 +21,8 @@ struct Operators {
   DBuf<float> m2l32, m2m32, l2l32;
   // FP32 M2L, output-major and zero padded: m2l32p[343][m2l_rows(p)][coef_pitch(p)]
   DBuf<float> m2l32p;
+  // tensor-core M2L: TF32 hi/lo halves in the MMA's core-matrix order
+  DBuf<float> m2l_tc;
 };
 
 // passes timed by the optional profiler (fmm_profile / fmm_profile_read)
@@ -31,6 +33,8 @@ uint64_t launch_count();
 
 struct fmm_plan_impl {
   // configuration
+  int m2l_path = 0;                  // 0 auto, 1 CUDA cores, 2 tensor cores
+  bool m2l_tc = false;               // this plan's M2L runs on the tensor cores
   int order = 0, leaf_size = 1, autotune = 0, precision = FMM_FP64, coarse_fp64_levels = 3, max_depth = kMaxDepth;
   cudaStream_t stream = nullptr;
 
@@ -96,6 +100,8 @@ struct fmm_plan_impl {
   DBuf<float4> src32;
   DBuf<double> M64, L64;            // nboxes x NC
   DBuf<float> M32, L32;
+  DBuf<float> Mhi, Mlo;             // TF32 split of M32 for the tensor-core M2L
+  DBuf<int> dev_err;                // set by a bounded device wait that gave up
   DBuf<double> K64;                 // M2P coefficient sets of the W sources
   DBuf<float> K32;
   DBuf<double> far_acc, near_acc;   // 4 x n each: phi, gx, gy, gz (sorted order)
@@ -170,6 +176,10 @@ void set_points(fmm_plan_impl &P, const double *d_xyz);
 void build_operators(fmm_plan_impl &P);
 // m2l.cu
 void build_m2l_tables(fmm_plan_impl &P);
+// m2l_tc.cu
+size_t m2l_tc_operator_floats(int p);
+size_t m2l_tc_pitch(int p);  // row pitch of the TF32-split multipoles
+void pack_m2l_tc_operators(int p, const double *m2l_in_major, float *out);
 // tune.cu: fastest leaf size for these points (cached per size bucket, order, precision)
 int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n);
 // eval.cu

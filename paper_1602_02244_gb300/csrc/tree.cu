@@ -854,7 +854,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   P.nwleaves = compact(P, nb, P.s_i32a.p, P.wleaves);
 
   // ---- M2L tiles: boxes of level >= 2 grouped by (level, octant parity)
-  P.m2l_tile_size = m2l_tile_size(P.order, P.precision);
+  P.m2l_tc = P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder && P.m2l_path != 1;
+  P.m2l_tile_size = P.m2l_tc ? kM2LTensorTile : m2l_tile_size(P.order, P.precision);
   int64_t b2 = P.nlevels > 2 ? P.level_off[2] : nb;
   int64_t n2 = nb - b2;
   if (n2 > 0) {
