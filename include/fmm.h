@@ -182,8 +182,9 @@ fmm_status fmm_profile_read(fmm_plan_t plan, double ms[FMM_NPASS], int64_t launc
  * A[128][k] B[n][k]^T with tcgen05.mma (kind::tf32).  mode 1: one TF32
  * product; mode 3: the three-product TF32 split with FP32-level accuracy.
  * Device pointers, row-major FP32; n a multiple of 16 in 16..256, k a
- * multiple of 8, and the four operand halves (2*128*k + 2*n*k floats) at most
- * 200 KB, else FMM_ERR_INVALID_ARG.  Synchronous.  FMM_ERR_TIMEOUT if the bounded wait for MMA
+ * multiple of 8, and the four operand halves (2*128*kp + 2*n*k floats, kp = k
+ * rounded up to a multiple of 32) at most 200 KB, else FMM_ERR_INVALID_ARG.
+ * Synchronous.  FMM_ERR_TIMEOUT if the bounded wait for MMA
  * completion gave up. */
 fmm_status fmm_tc_selftest(int n, int k, const float *d_a, const float *d_b, float *d_d, int mode,
                            void *stream);

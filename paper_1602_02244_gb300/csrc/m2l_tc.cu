@@ -70,18 +70,20 @@ __host__ __device__ constexpr int tc_k(int p) { return (ncoef(p) + kTcKC - 1) / 
 //              targets 32w..32w+31 of the tile, and adds finished slots into
 //              registers; they write L at the end;
 //   warp 4     one thread issues the MMAs and the tcgen05.commit arrivals;
-//   warps 5-6  producers: gather the A rows (source multipoles) and copy the
-//              operator slab of each (slot, K chunk) stage with cp.async, then
-//              fence their writes into the async proxy and arrive on the
-//              stage's `full` barrier.
-// Barriers: full[s] (64 producer arrivals) -> MMA; empty[s] (commit) ->
+//   warps 5-8  producers: gather the A rows (source multipoles) of each
+//              (slot, K chunk) stage with cp.async, fence their writes into
+//              the async proxy and arrive on the stage's `full` barrier; one
+//              of them also moves the stage's operator slab with a bulk async
+//              copy that completes its bytes on the same barrier.
+// Barriers: full[s] (128 producer arrivals) and bfull[s] (the slab's bytes)
+// -> MMA; empty[s] (commit) ->
 // producers; accf[a] (commit after a slot) -> drain; acce[a] (128 drain
 // arrivals) -> MMA before it overwrites accumulator a.
 constexpr int kTcDrainWarps = 4;
-constexpr int kTcProdWarps = 2;
+constexpr int kTcProdWarps = 4;
 constexpr int kTcProdThreads = 32 * kTcProdWarps;
 constexpr int kTcThreads = 32 * (kTcDrainWarps + 1 + kTcProdWarps);
-constexpr int kTcRowsPerProd = kTcTile * (kTcKC / 4) / kTcProdThreads;  // 16
+constexpr int kTcRowsPerProd = kTcTile * (kTcKC / 4) / kTcProdThreads;  // 8
 
 // Wait for a phase of an mbarrier; gives up after kTcWaitCycles or as soon as
 // another thread of the CTA gave up (the abort word), so that one timeout does
@@ -99,14 +101,15 @@ __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity, volatil
 }
 
 template <int NT, int NSTAGE>
-__global__ void __launch_bounds__(kTcThreads)
-    k_m2l_tc(int p, int kt, const M2LTile *__restrict__ tiles, const int32_t *__restrict__ table,
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_m2l_tc(int p, int kt, const M2LTile *__restrict__ tiles,
+             const int32_t *__restrict__ table,
              const int16_t *__restrict__ slots, const int32_t *__restrict__ nslots,
              const int32_t *__restrict__ order, const float *__restrict__ Mhi,
              const float *__restrict__ Mlo, const float *__restrict__ opt, float *__restrict__ L,
              int *__restrict__ err) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint64_t full[NSTAGE], empty[NSTAGE], accf[2], acce[2], done;
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  __shared__ uint64_t full[NSTAGE], bfull[NSTAGE], empty[NSTAGE], accf[2], acce[2], done;
   __shared__ uint32_t tslot;
   __shared__ int abort_word;
   volatile int *abort = &abort_word;
@@ -115,7 +118,9 @@ __global__ void __launch_bounds__(kTcThreads)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nc = ncoef(p), ld = coef_pitch(p), nch = kt / kTcKC;
   constexpr uint32_t a_bytes = kTcTile * kTcKC * 4, b_bytes = (uint32_t)N * kTcKC * 4;
-  constexpr uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  constexpr uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;  // a multiple of 1024
+  // the swizzled A tiles need a 1024-byte-aligned base (1 KB of slack is allocated)
+  unsigned char *sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
   const M2LTile tile = tiles[blockIdx.x];
   const int ns = nslots[blockIdx.x];
   const int total = ns * nch;
@@ -130,6 +135,7 @@ __global__ void __launch_bounds__(kTcThreads)
   if (tid == 0) {
     for (int q = 0; q < NSTAGE; ++q) {
       tc::mbar_init(&full[q], kTcProdThreads);
+      tc::mbar_init(&bfull[q], 1);
       tc::mbar_init(&empty[q], 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -184,7 +190,8 @@ __global__ void __launch_bounds__(kTcThreads)
         const uint32_t dtm = tmem + (uint32_t)(a * kCols);
         for (int c = 0; c < nch; ++c) {
           const int st = j * nch + c;
-          ok = tc_wait(&full[st % NSTAGE], (uint32_t)(st / NSTAGE) & 1, abort);
+          ok = tc_wait(&full[st % NSTAGE], (uint32_t)(st / NSTAGE) & 1, abort) &&
+               tc_wait(&bfull[st % NSTAGE], (uint32_t)(st / NSTAGE) & 1, abort);
           if (!ok) break;
           tc::fence_after_sync();
           const uint32_t base = tc::smem_addr(sm + (st % NSTAGE) * stage_bytes);
@@ -193,8 +200,8 @@ __global__ void __launch_bounds__(kTcThreads)
 #pragma unroll
           for (int ks = 0; ks < kTcKC / 8; ++ks) {
             const uint32_t off = (uint32_t)ks * 256;
-            const uint64_t dah = tc::smem_desc(ah + off, 128, sbo);
-            const uint64_t dal = tc::smem_desc(al + off, 128, sbo);
+            const uint64_t dah = tc::smem_desc_sw128(ah + (uint32_t)ks * 32);
+            const uint64_t dal = tc::smem_desc_sw128(al + (uint32_t)ks * 32);
             const uint64_t dbh = tc::smem_desc(bh + off, 128, sbo);
             const uint64_t dbl = tc::smem_desc(bl + off, 128, sbo);
             tc::mma_tf32(dtm, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
@@ -211,19 +218,33 @@ __global__ void __launch_bounds__(kTcThreads)
     }
   } else {
     // ---------------------------------------------------------------- producers
+    // Thread pt copies 16-byte chunk kk of rows rq + 16 i, i < 8, in both
+    // halves: the 8 lanes of a row read one 128-byte line of the source and
+    // fill the row's 128 swizzled bytes (no bank conflicts).
+    // The full barrier of a stage is signalled kLag stages after its copies
+    // were issued, so the producer never waits on the MMAs of a stage it has
+    // only just handed over.
+    constexpr int kLag = NSTAGE - 2;
     const int pt = tid - 32 * (kTcDrainWarps + 1);
-    const int rlo = pt & 7, kk = pt >> 3;  // rows rlo + 8i, K piece kk (4 floats)
+    const int kk = pt & 7, rq = pt >> 3;
     const int px = tile.parity & 1, py = (tile.parity >> 1) & 1, pz = (tile.parity >> 2) & 1;
     const int32_t *tab = table + (size_t)blockIdx.x * 216 * kTcTile;
     const int16_t *sl = slots + (size_t)blockIdx.x * 216;
-    int32_t rows[kTcRowsPerProd], next[kTcRowsPerProd];
+    const size_t lo_off = (size_t)(Mlo - Mhi);
+    // missing sources (row -1) are zero-filled by the copy itself (source
+    // size 0): pointing them at a shared zero row would make every SM hit the
+    // same L2 lines
+    const float *rp[kTcRowsPerProd];
+    int rsz[kTcRowsPerProd];
+    int32_t next[kTcRowsPerProd];
     int code = 0, next_code = 0;
     auto fetch = [&](int j) {  // source rows and operator code of slot j
       const int slot = sl[j];
       const int sx = slot / 36, sy = (slot / 6) % 6, sz = slot % 6;
       next_code = (2 + px - sx + 3) * 49 + (2 + py - sy + 3) * 7 + (2 + pz - sz + 3);
 #pragma unroll
-      for (int i = 0; i < kTcRowsPerProd; ++i) next[i] = tab[slot * kTcTile + rlo + 8 * i];
+      for (int i = 0; i < kTcRowsPerProd; ++i)
+        next[i] = tab[slot * kTcTile + rq + 16 * i];
     };
     fetch(0);
     int st = 0, signalled = 0;
@@ -232,31 +253,31 @@ __global__ void __launch_bounds__(kTcThreads)
       if (st >= NSTAGE && !tc_wait(&empty[s], (uint32_t)(st / NSTAGE - 1) & 1, abort)) break;
       if (c == 0) {
 #pragma unroll
-        for (int i = 0; i < kTcRowsPerProd; ++i) rows[i] = next[i];
+        for (int i = 0; i < kTcRowsPerProd; ++i) {
+          rp[i] = Mhi + (size_t)(next[i] >= 0 ? next[i] : 0) * kt + 4 * kk;
+          rsz[i] = next[i] >= 0 ? 16 : 0;
+        }
         code = next_code;
         if (j + 1 < ns) fetch(j + 1);  // consumed one slot later
       }
-      unsigned char *base = sm + s * stage_bytes;
+      // rows rq + 16 i share (row & 7) = rq & 7, hence the chunk position
+      unsigned char *base = sm + s * stage_bytes + tc::sw128_offset(rq, 4 * kk);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float *Ms = h ? Mlo : Mhi;
-#pragma unroll
-        for (int i = 0; i < kTcRowsPerProd; ++i) {
-          const int r = rlo + 8 * i;
-          const int32_t A = rows[i];
-          const float *src = Ms + (size_t)(A >= 0 ? A : 0) * kt + c * kTcKC + 4 * kk;
-          cp_async16(base + h * a_bytes + tc::kmajor_offset(r, 4 * kk, kTcKC), src, A >= 0 ? 16 : 0);
-        }
+      for (int i = 0; i < kTcRowsPerProd; ++i) {
+        const float *src = rp[i] + c * kTcKC;
+        cp_async16(base + i * 16 * 128, src, rsz[i]);
+        cp_async16(base + a_bytes + i * 16 * 128, src + lo_off, rsz[i]);
       }
-      const float *bsrc = opt + ((size_t)code * nch + c) * 2 * N * kTcKC;
-#pragma unroll
-      for (uint32_t q = pt; q < 2 * b_bytes / 16; q += kTcProdThreads)
-        cp_async16(base + 2 * a_bytes + 16 * q, bsrc + 4 * q, 16);
+      if (pt == 0) {  // the operator slab (hi and lo halves) is contiguous: one bulk copy
+        const float *bsrc = opt + ((size_t)code * nch + c) * 2 * N * kTcKC;
+        tc::mbar_arrive_expect_tx(&bfull[s], 2 * b_bytes);
+        tc::bulk_g2s(sm + s * stage_bytes + 2 * a_bytes, bsrc, 2 * b_bytes, &bfull[s]);
+      }
       cp_async_commit();
-      if (st >= NSTAGE - 1) {  // the stage issued NSTAGE - 1 steps ago has landed
-        cp_async_wait<NSTAGE - 1>();
+      if (st >= kLag) {  // the stage issued kLag steps ago has landed
+        cp_async_wait<kLag>();
         tc::fence_async_shared();
-        tc::mbar_arrive(&full[(st - (NSTAGE - 1)) % NSTAGE]);
+        tc::mbar_arrive(&full[(st - kLag) % NSTAGE]);
         ++signalled;
       }
     }
@@ -264,6 +285,11 @@ __global__ void __launch_bounds__(kTcThreads)
     if (!*abort) {
       tc::fence_async_shared();
       for (; signalled < st; ++signalled) tc::mbar_arrive(&full[signalled % NSTAGE]);
+    } else if (pt == 0) {
+      // slabs of the last NSTAGE issued stages may still be in flight: let
+      // them land before the CTA's shared memory is released
+      for (int q = st - NSTAGE > 0 ? st - NSTAGE : 0; q < st; ++q)
+        tc::mbar_wait_bounded(&bfull[q % NSTAGE], (uint32_t)(q / NSTAGE) & 1, kTcWaitCycles);
     }
   }
 
@@ -337,8 +363,8 @@ void launch_m2l_tc(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *t
   auto run = [&](auto NC) {
     constexpr int NTT = decltype(NC)::value;
     constexpr size_t stage = (size_t)2 * (kTcTile + NTT) * kTcKC * 4;
-    constexpr int kStages = 4 * stage + 1024 <= 227 * 1024 ? 4 : 3;
-    const size_t smem = kStages * stage;
+    constexpr int kStages = 4 * stage + 1024 + 512 <= 227 * 1024 ? 4 : 3;
+    const size_t smem = kStages * stage + 1024;  // + alignment slack
     auto kern = k_m2l_tc<NTT, kStages>;
     FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)ntiles, kTcThreads, smem, s>>>(p, kt, tiles, table, slots, nslots, order, Mhi,

@@ -19,8 +19,11 @@ namespace fmm {
 
 namespace {
 
-constexpr int kP2PWarps = 4;
+// One warp per CTA: a CTA's resources are released as soon as its leaf is
+// done, so uneven leaf costs leave no idle warps holding an SM slot.
+constexpr int kP2PWarps = 1;
 constexpr int kP2PThreads = 32 * kP2PWarps;
+constexpr int kP2PMinCtas = 16;  // resident CTAs per SM: caps registers at 128
 constexpr int kMaxTPL = 4;  // targets per lane
 
 template <typename T>
@@ -66,7 +69,7 @@ __device__ __forceinline__ void sweep(const V *ss, int j0, int j1, bool self, co
 }
 
 template <typename T, int CAP>
-__global__ void __launch_bounds__(kP2PThreads)
+__global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
     k_p2p(int64_t nleaves, const int32_t *__restrict__ leaves, const int32_t *__restrict__ uoff,
           const int32_t *__restrict__ uidx, const int32_t *__restrict__ first,
           const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
@@ -191,7 +194,7 @@ void launch_p2p(int64_t nleaves, const int32_t *leaves, const int32_t *uoff, con
                 const typename V4<T>::type *src, const double *side, int64_t n, double *near,
                 cudaStream_t s) {
   if (nleaves == 0) return;
-  constexpr int CAP = sizeof(T) == 4 ? 640 : 320;  // 40 KB of static shared memory per CTA
+  constexpr int CAP = sizeof(T) == 4 ? 640 : 320;  // 10 KB of staged sources per warp
   k_p2p<T, CAP><<<ceil_div(nleaves, kP2PWarps), kP2PThreads, 0, s>>>(nleaves, leaves, uoff, uidx,
                                                                       first, count, geo, src, side,
                                                                       n, near);

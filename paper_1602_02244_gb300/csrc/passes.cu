@@ -362,11 +362,12 @@ __global__ void k_l2p(int p_rt, const int32_t *__restrict__ leaves, const int32_
 //   Kz_n^m = -M_{n-1}^m,  Kx_n^m = (M_{n-1}^{m-1} - M_{n-1}^{m+1})/2,
 //   Ky_n^m = -i (M_{n-1}^{m-1} + M_{n-1}^{m+1})/2,
 // which obey the same X_n^{-m} = (-1)^m conj(X_n^m) symmetry.  A prepass writes
-// (M, Kx, Ky, Kz) of every W source box in the real layout (pitch
-// coef_pitch(p+1)); the evaluation is then four branch-free dot products.
+// (M, Kx, Ky, Kz) of every W source box in the real layout, interleaved as
+// one 4-vector per coefficient (pitch coef_pitch(p+1)); the evaluation is
+// then four dot products that share one harmonic stream.
 template <typename T>
 __global__ void k_m2p_prep(int p, int64_t nx, const int32_t *__restrict__ xboxes,
-                           const T *__restrict__ M, T *__restrict__ K) {
+                           const T *__restrict__ M, typename V4<T>::type *__restrict__ K) {
   const int ld = coef_pitch(p), ld1 = coef_pitch(p + 1), nc1 = ncoef(p + 1);
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nx * nc1) return;
@@ -391,69 +392,104 @@ __global__ void k_m2p_prep(int p, int64_t nx, const int32_t *__restrict__ xboxes
   kz = -(im_part ? ai : ar);
   kx = T(0.5) * (im_part ? (bi - ci) : (br - cr));
   ky = im_part ? T(-0.5) * (br + cr) : T(0.5) * (bi + ci);
-  T *Kj = K + j * 4 * ld1;
-  Kj[r] = k0;
-  Kj[ld1 + r] = kx;
-  Kj[2 * ld1 + r] = ky;
-  Kj[3 * ld1 + r] = kz;
+  // a real expansion sums Re(X_n^0 I_n^0) + 2 sum_{m>0} Re(X_n^m I_n^m):
+  // the factor 2 of the m > 0 terms is applied here, once per coefficient
+  const T w = m > 0 ? T(2) : T(1);
+  typename V4<T>::type v;
+  v.x = w * k0;
+  v.y = w * kx;
+  v.z = w * ky;
+  v.w = w * kz;
+  K[j * ld1 + r] = v;
 }
 
-// One CTA per target leaf; k = floor(128 / targets) threads share a target and
-// split its W list; partial sums are combined in FP64.
+// One CTA of 128 threads per target leaf (chunks of 128 targets).  Targets
+// sit on lanes; the 4 warps form k = 4 / ceil(targets / 32) replicas that
+// split the W list, so all lanes of a warp work on the same source box and
+// read its (M, Kx, Ky, Kz) coefficients from shared memory as broadcasts.
+// W boxes are staged kM2PStage at a time with their centre offsets and
+// scale; per-box sums are taken in T and accumulated in FP64.
 constexpr int kM2PThreads = 128;
+constexpr int kM2PStage = 16;
 
 template <typename T, int PT>
 __global__ void __launch_bounds__(kM2PThreads)
-    k_m2p(int p_rt, const int32_t *__restrict__ wleaves, const int32_t *__restrict__ woff,
+    k_m2p(int p_rt, int nstage, const int32_t *__restrict__ wleaves, const int32_t *__restrict__ woff,
           const int32_t *__restrict__ widx, const int32_t *__restrict__ xslot,
           const int32_t *__restrict__ first, const int32_t *__restrict__ count,
           const BoxGeo *__restrict__ geo, const typename V4<T>::type *__restrict__ src,
-          const double *__restrict__ side, const T *__restrict__ K, int64_t n,
+          const double *__restrict__ side, const typename V4<T>::type *__restrict__ K, int64_t n,
           double *__restrict__ far) {
+  using V = typename V4<T>::type;
   const int p = PT > 0 ? PT : p_rt;  // compile-time order unrolls the harmonic streams
+  extern __shared__ __align__(32) unsigned char m2p_smem[];
+  V *ks = reinterpret_cast<V *>(m2p_smem);  // [nstage][ld1]
+  __shared__ T s_off[kM2PStage][3], s_inva[kM2PStage];
+  __shared__ double s_ia[kM2PStage];
+  __shared__ int32_t s_slot[kM2PStage];
   __shared__ double red[4][kM2PThreads];
-  const int tid = threadIdx.x, ld1 = coef_pitch(p + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ld1 = coef_pitch(p + 1), nc1 = ncoef(p + 1);
   const int32_t B = wleaves[blockIdx.x];
   const BoxGeo gb = geo[B];
+  const double sb = side[B];
   const int32_t f = first[B], c = count[B], e0 = woff[B], e1 = woff[B + 1];
   for (int32_t tc = 0; tc < c; tc += kM2PThreads) {
     const int tcount = min(kM2PThreads, c - tc);
-    const int k = max(1, min(min(32, kM2PThreads / tcount), e1 - e0));
-    const int ti = tid / k, sl = tid - ti * k;
+    const int wpr = (tcount + 31) / 32;  // warps per replica
+    const int k = 4 / wpr;               // replicas
+    const int rep = warp / wpr, ti = (warp - rep * wpr) * 32 + lane;
+    const bool act = rep < k && ti < tcount;
+    V s;
+    s.x = s.y = s.z = s.w = T(0);
+    if (act) s = src[f + tc + ti];
     double phi = 0, gx = 0, gy = 0, gz = 0;
-    if (ti < tcount) {
-      const typename V4<T>::type s = src[f + tc + ti];
-      for (int32_t e = e0 + sl; e < e1; e += k) {
-        const int32_t A = widx[e];
+    for (int32_t e = e0; e < e1; e += nstage) {
+      const int nb = min(nstage, e1 - e);
+      __syncthreads();  // the previous batch has been consumed
+      if (tid < nb) {
+        const int32_t A = widx[e + tid];
         const BoxGeo ga = geo[A];
         const double aa = side[A];
-        const T inva = (T)(1.0 / aa);
-        const T sx = (T)center_delta(gb.ix, side[B], ga.ix, aa);
-        const T sy = (T)center_delta(gb.iy, side[B], ga.iy, aa);
-        const T sz = (T)center_delta(gb.iz, side[B], ga.iz, aa);
-        const T *K0 = K + (int64_t)xslot[A] * 4 * ld1;
-        const T *Kx = K0 + ld1, *Ky = K0 + 2 * ld1, *Kz = K0 + 3 * ld1;
-        T fp = 0, fx = 0, fy = 0, fz = 0;
-        irregular_stream<T>(p + 1, (s.x + sx) * inva, (s.y + sy) * inva, (s.z + sz) * inva,
-                            [&](int nn, int m, T re, T im) {
-                              const int rp = cidx(nn, m), rn = cidx(nn, -m);
-                              if (m == 0) {
-                                fp += K0[rp] * re;
-                                fx += Kx[rp] * re;
-                                fy += Ky[rp] * re;
-                                fz += Kz[rp] * re;
-                              } else {
-                                fp += T(2) * (K0[rp] * re - K0[rn] * im);
-                                fx += T(2) * (Kx[rp] * re - Kx[rn] * im);
-                                fy += T(2) * (Ky[rp] * re - Ky[rn] * im);
-                                fz += T(2) * (Kz[rp] * re - Kz[rn] * im);
-                              }
-                            });
-        const double ia = 1.0 / aa;
-        phi += (double)fp * ia;
-        gx += (double)fx * ia * ia;
-        gy += (double)fy * ia * ia;
-        gz += (double)fz * ia * ia;
+        s_slot[tid] = xslot[A];
+        s_off[tid][0] = (T)center_delta(gb.ix, sb, ga.ix, aa);
+        s_off[tid][1] = (T)center_delta(gb.iy, sb, ga.iy, aa);
+        s_off[tid][2] = (T)center_delta(gb.iz, sb, ga.iz, aa);
+        s_inva[tid] = (T)(1.0 / aa);
+        s_ia[tid] = 1.0 / aa;
+      }
+      __syncthreads();
+      for (int q = tid; q < nb * nc1; q += kM2PThreads) {
+        const int b = q / nc1, r = q - b * nc1;
+        ks[b * ld1 + r] = K[(int64_t)s_slot[b] * ld1 + r];
+      }
+      __syncthreads();
+      if (act) {
+        for (int b = rep; b < nb; b += k) {
+          const V *kb = ks + b * ld1;
+          const T inva = s_inva[b];
+          T fp = 0, fx = 0, fy = 0, fz = 0;
+          irregular_stream<T>(p + 1, (s.x + s_off[b][0]) * inva, (s.y + s_off[b][1]) * inva,
+                              (s.z + s_off[b][2]) * inva, [&](int nn, int m, T re, T im) {
+                                const V kp = kb[cidx(nn, m)];
+                                fp += kp.x * re;
+                                fx += kp.y * re;
+                                fy += kp.z * re;
+                                fz += kp.w * re;
+                                if (m > 0) {
+                                  const V kn = kb[cidx(nn, -m)];
+                                  fp -= kn.x * im;
+                                  fx -= kn.y * im;
+                                  fy -= kn.z * im;
+                                  fz -= kn.w * im;
+                                }
+                              });
+          const double ia = s_ia[b];
+          phi += (double)fp * ia;
+          gx += (double)fx * ia * ia;
+          gy += (double)fy * ia * ia;
+          gz += (double)fz * ia * ia;
+        }
       }
     }
     red[0][tid] = phi;
@@ -461,13 +497,14 @@ __global__ void __launch_bounds__(kM2PThreads)
     red[2][tid] = gy;
     red[3][tid] = gz;
     __syncthreads();
-    if (tid < tcount) {
+    if (tid < tcount) {  // target tid: replica r holds it at thread r * 32 * wpr + tid
       double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-      for (int s2 = 0; s2 < k; ++s2) {
-        a0 += red[0][tid * k + s2];
-        a1 += red[1][tid * k + s2];
-        a2 += red[2][tid * k + s2];
-        a3 += red[3][tid * k + s2];
+      for (int r = 0; r < k; ++r) {
+        const int o = r * 32 * wpr + tid;
+        a0 += red[0][o];
+        a1 += red[1][o];
+        a2 += red[2][o];
+        a3 += red[3][o];
       }
       const int64_t i = f + tc + tid;
       far[i] += a0;
@@ -475,7 +512,7 @@ __global__ void __launch_bounds__(kM2PThreads)
       far[2 * n + i] += a2;
       far[3 * n + i] += a3;
     }
-    __syncthreads();
+    __syncthreads();  // red is rewritten by the next chunk
   }
 }
 
@@ -625,12 +662,20 @@ void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, 
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 const T *M, T *K, int64_t n, double *far, cudaStream_t s) {
   if (nw == 0) return;
+  using V = typename V4<T>::type;
+  V *K4 = reinterpret_cast<V *>(K);  // nx x coef_pitch(p+1) 4-vectors
   const int64_t tot = nx * ncoef(p + 1);
-  k_m2p_prep<T><<<ceil_div(tot, 256), 256, 0, s>>>(p, nx, xboxes, M, K);
+  k_m2p_prep<T><<<ceil_div(tot, 256), 256, 0, s>>>(p, nx, xboxes, M, K4);
   FMM_LAUNCH_CHECK();
+  // stage as many W boxes as fit in 64 KB (at most kM2PStage)
+  const size_t per_box = (size_t)coef_pitch(p + 1) * sizeof(V);
+  const int nstage = (int)std::max<size_t>(1, std::min<size_t>(kM2PStage, (64 << 10) / per_box));
+  const size_t sm = nstage * per_box;
   with_order(p, [&](auto PC) {
-    k_m2p<T, decltype(PC)::value><<<(unsigned)nw, kM2PThreads, 0, s>>>(
-        p, wleaves, woff, widx, xslot, first, count, geo, src, side, K, n, far);
+    auto kern = k_m2p<T, decltype(PC)::value>;
+    FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    kern<<<(unsigned)nw, kM2PThreads, sm, s>>>(p, nstage, wleaves, woff, widx, xslot, first, count,
+                                               geo, src, side, K4, n, far);
   });
   FMM_LAUNCH_CHECK();
 }

@@ -2,7 +2,9 @@
 // contraction: one CTA computes D[128][N] = A[128][K] B[N][K]^T with
 // tcgen05.mma (kind::tf32, accumulator in tensor memory), either as one TF32
 // product or as the three-product split (A_hi B_hi + A_hi B_lo + A_lo B_hi)
-// that carries FP32 accuracy.  Every wait is bounded; a timeout is reported.
+// that carries FP32 accuracy.  The operands use the layouts of the M2L
+// kernel: A in 128-byte-swizzle tiles of 32 K values, B without swizzle.
+// Every wait is bounded; a timeout is reported.
 #include "plan.cuh"
 #include "tcgen05.cuh"
 
@@ -15,17 +17,21 @@ constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 __global__ void __launch_bounds__(128)
     k_tc_probe(int N, int K, const float *__restrict__ A, const float *__restrict__ B,
                float *__restrict__ D, int mode, int *__restrict__ err) {
-  extern __shared__ __align__(128) unsigned char sm[];
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  unsigned char *Ahi = sm, *Alo = Ahi + 128 * K * 4, *Bhi = Alo + 128 * K * 4, *Blo = Bhi + N * K * 4;
+  // swizzled tiles need a 1024-byte-aligned base (1 KB of slack is allocated)
+  unsigned char *sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
+  const int Kp = (K + 31) / 32 * 32;
+  unsigned char *Ahi = sm, *Alo = Ahi + 128 * Kp * 4, *Bhi = Alo + 128 * Kp * 4, *Blo = Bhi + N * K * 4;
   for (int e = tid; e < 128 * K; e += 128) {
     const int r = e / K, k = e - r * K;
     float hi, lo;
     tc::split_tf32(A[e], hi, lo);
-    *reinterpret_cast<float *>(Ahi + tc::kmajor_offset(r, k, K)) = hi;
-    *reinterpret_cast<float *>(Alo + tc::kmajor_offset(r, k, K)) = lo;
+    const uint32_t o = (uint32_t)(k / 32) * 128 * 128 + tc::sw128_offset(r, k % 32);
+    *reinterpret_cast<float *>(Ahi + o) = hi;
+    *reinterpret_cast<float *>(Alo + o) = lo;
   }
   for (int e = tid; e < N * K; e += 128) {
     const int r = e / K, k = e - r * K;
@@ -47,8 +53,9 @@ __global__ void __launch_bounds__(128)
     const uint32_t sbo = (uint32_t)(K / 4) * 128;
     for (int ks = 0; ks < K / 8; ++ks) {
       const uint32_t off = (uint32_t)ks * 256;
-      const uint64_t ah = tc::smem_desc(tc::smem_addr(Ahi) + off, 128, sbo);
-      const uint64_t al = tc::smem_desc(tc::smem_addr(Alo) + off, 128, sbo);
+      const uint32_t aoff = (uint32_t)(ks / 4) * 128 * 128 + (uint32_t)(ks % 4) * 32;
+      const uint64_t ah = tc::smem_desc_sw128(tc::smem_addr(Ahi) + aoff);
+      const uint64_t al = tc::smem_desc_sw128(tc::smem_addr(Alo) + aoff);
       const uint64_t bh = tc::smem_desc(tc::smem_addr(Bhi) + off, 128, sbo);
       const uint64_t bl = tc::smem_desc(tc::smem_addr(Blo) + off, 128, sbo);
       tc::mma_tf32(tmem, ah, bh, idesc, ks > 0);
@@ -89,8 +96,9 @@ extern "C" fmm_status fmm_tc_selftest(int n, int k, const float *d_a, const floa
       !d_a || !d_b || !d_d)
     return record_error(FMM_ERR_INVALID_ARG,
                         "fmm_tc_selftest: n in 16..256 (multiple of 16), k multiple of 8, mode 1 or 3");
-  const size_t smem = (size_t)(2 * 128 * k + 2 * n * k) * sizeof(float);
-  if (smem > 200 * 1024) return record_error(FMM_ERR_INVALID_ARG, "fmm_tc_selftest: operands too large");
+  const size_t kp = (size_t)(k + 31) / 32 * 32;
+  const size_t smem = (2 * 128 * kp + 2 * (size_t)n * k) * sizeof(float) + 1024;
+  if (smem > 201 * 1024) return record_error(FMM_ERR_INVALID_ARG, "fmm_tc_selftest: operands too large");
   try {
     cudaStream_t s = (cudaStream_t)stream;
     DBuf<int> err;

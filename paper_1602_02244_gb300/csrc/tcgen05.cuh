@@ -2,10 +2,15 @@
 // (tcgen05.mma with the accumulator in tensor memory) used by the M2L
 // contraction.
 //
-// Operands live in shared memory in the no-swizzle K-major layout: the matrix
-// is cut into 8-row x 16-byte core matrices stored as contiguous 128-byte
-// blocks; LBO is the byte distance between core matrices adjacent along K,
-// SBO the distance between core matrices adjacent along M (or N).
+// Operands live in shared memory K-major, in one of two layouts:
+//  - no swizzle: the matrix is cut into 8-row x 16-byte core matrices stored
+//    as contiguous 128-byte blocks; LBO is the byte distance between core
+//    matrices adjacent along K, SBO the distance between core matrices
+//    adjacent along M (or N);
+//  - 128-byte swizzle: each row holds 32 tf32 values in 128 contiguous bytes
+//    whose 16-byte chunks are permuted as chunk ^ (row & 7), 8-row groups are
+//    1024 bytes apart and the tile starts on a 1024-byte boundary.  A row is
+//    then one 128-byte line, which makes row gathers cheap.
 #pragma once
 #include <stdint.h>
 
@@ -20,6 +25,19 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// shared-memory matrix descriptor: 128-byte swizzle, K-major (layout type 2,
+// SBO = 1024 bytes, LBO unused); within a row the start address advances by
+// 32 bytes per MMA K step of 8 tf32 values
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
+// byte offset of element (row, k), k < 32, in a 128-byte-swizzle tile
+__host__ __device__ constexpr uint32_t sw128_offset(int row, int k) {
+  return (uint32_t)(row * 128 + ((((k >> 2) ^ row) & 7) << 4) + (k & 3) * 4);
 }
 
 // instruction descriptor for kind::tf32: D f32, A and B tf32, both K-major
@@ -74,6 +92,25 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
 // one arrival of the calling thread (release semantics at CTA scope)
 __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(mbar)) : "memory");
+}
+
+// one arrival that also raises the transaction count of the current phase by
+// `bytes` (the phase then completes when the bytes have landed)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// bulk copy of `bytes` contiguous bytes global -> shared through the async
+// proxy, completing `bytes` transactions on `mbar` (both addresses 16-byte
+// aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+      : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t phase) {
