@@ -199,6 +199,18 @@ fmm_status fmm_sync(fmm_plan_t plan, void *stream);
  * resets it after reading).  Either output may be NULL. */
 fmm_status fmm_memory_usage(uint64_t *current, uint64_t *peak, int reset_peak);
 
+/* Brute-force reference: for m targets t (d_tgt: device, m x 3 FP64)
+ *   phi(t) = sum_j q_j / |t - x_j|,  grad(t) = -sum_j q_j (t - x_j) / |t - x_j|^3
+ * over the n sources x_j (d_src: device, n x 3 FP64; d_q: n), skipping pairs
+ * at zero distance -- the plain definition the FMM approximates (§2, Eq. 1,
+ * kernel 1/r).  FP64, O(n m) work; the sum over sources is taken in a fixed
+ * order (deterministic).  d_grad (m x 3) may be NULL.  Stream-ordered and
+ * asynchronous; scratch comes from the library pool.  FMM_ERR_INVALID_ARG
+ * for negative sizes or NULL required pointers; non-finite inputs give
+ * non-finite outputs.  n = 0 gives zeros; m = 0 is a no-op. */
+fmm_status fmm_direct(const double *d_src, const double *d_q, int64_t n, const double *d_tgt,
+                      int64_t m, double *d_phi, double *d_grad, void *stream);
+
 /* Number of kernels this library has launched in this process so far. */
 uint64_t fmm_kernel_launches(void);
 

@@ -8,7 +8,7 @@
  * What it computes (Yokota, Ibeid & Keyes, "Fast Multipole Method as a
  * Matrix-Free Hierarchical Low-Rank Approximation"):
  *   - the O(N^2) direct sum phi_i = sum_{j != i} q_j / |x_i - x_j| and its
- *     gradient g_i = grad phi(x_i) (the "dense diagonal blocks" of the
+ *     gradient g_i = grad phi(x_i) (the dense diagonal blocks of the
  *     hierarchical matrix are exactly this Green's-function operator, §2.2);
  *   - the analytic FMM (Greengard & Rokhlin, cited in §2.1) as a matrix-free
  *     H^2 mat-vec (§1, §2.4): octree over a Morton (3D->1D) ordering (§3.1),

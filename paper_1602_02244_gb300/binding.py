@@ -19,8 +19,9 @@ _STATUS = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_CUDA", 3: "FMM_ERR
            4: "FMM_ERR_TIMEOUT", 5: "FMM_ERR_NONFINITE_INPUT", 6: "FMM_ERR_UNSUPPORTED"}
 
 EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_plan_set_points",
-           "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_sync", "fmm_plan_sizes", "fmm_plan_export", "fmm_plan_destroy",
-           "fmm_status_string", "fmm_last_error_message")
+           "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_sync", "fmm_plan_sizes",
+           "fmm_plan_export", "fmm_plan_destroy", "fmm_direct", "fmm_status_string",
+           "fmm_last_error_message")
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
                  "box_parent", "box_child", "box_nchild", "u_off", "u_idx", "v_off", "v_idx",
@@ -67,6 +68,7 @@ def library():
         L.fmm_plan_sizes.argtypes = [_vp, ctypes.POINTER(_i64)]
         L.fmm_plan_export.argtypes = [_vp, _int, _vp, ctypes.c_size_t]
         L.fmm_plan_destroy.argtypes = [_vp]
+        L.fmm_direct.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _vp]
         L.fmm_status_string.argtypes = [_int]
         L.fmm_status_string.restype = ctypes.c_char_p
         L.fmm_last_error_message.restype = ctypes.c_char_p
@@ -278,3 +280,21 @@ def evaluate(points, q, leaf_size=64, order=8, precision="fp64"):
         return plan.eval(q)
     finally:
         plan.close()
+
+
+def direct(points, q, targets, grad=True, stream=None):
+    """Brute-force potential and gradient at ``targets`` (M, 3) of the charges
+    ``q`` (N,) at ``points`` (N, 3): the plain definition the FMM approximates,
+    evaluated on the GPU in FP64 (``fmm_direct``).  Returns (phi, grad)."""
+    if not isinstance(points, torch.Tensor) or points.dim() != 2:
+        raise TypeError("points must be an (N, 3) CUDA float64 tensor")
+    n, m = points.shape[0], targets.shape[0] if isinstance(targets, torch.Tensor) else -1
+    pts = _dev_f64(points, (n, 3), "points")
+    qq = _dev_f64(q, (n,), "q")
+    tgt = _dev_f64(targets, (m, 3), "targets")
+    phi = torch.empty(m, dtype=torch.float64, device=tgt.device)
+    g = torch.empty(m, 3, dtype=torch.float64, device=tgt.device) if grad else None
+    with torch.cuda.device(tgt.device):
+        _check(library().fmm_direct(_ptr(pts), _ptr(qq), n, _ptr(tgt), m, _ptr(phi), _ptr(g),
+                                    _stream(stream)))
+    return phi, g

@@ -5,17 +5,20 @@
 // A CTA owns 128 target boxes of one level with the same octant parity (the
 // M = 128 rows of the MMA).  For every occupied offset slot it contracts
 //   D[t][n] += sum_k M_src(t)[k] T_slot[n][k]     (N = rows of the operator)
-// with tcgen05.mma kind::tf32, accumulating all slots in one tensor-memory
-// tile.  FP32 accuracy comes from the three-product split
+// with tcgen05.mma kind::tf32.  FP32 accuracy comes from the three-product
+// split
 //   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
-// where X_hi is X rounded to TF32 and X_lo is X - X_hi rounded to TF32.  The multipoles are split once per evaluation
-// (k_split_tf32) and the operators at plan time, already in the K-major
-// core-matrix order the MMA reads.  Each slot is contracted in K chunks of 32;
-// chunks are copied into a ring of shared-memory stages with cp.async while
-// the tensor core works on earlier stages, and a stage is refilled only after
-// the mbarrier signalled by tcgen05.commit says its MMAs have finished.  All
-// waits are bounded; a timeout sets an error word and the CTA still frees its
-// tensor memory.
+// where X_hi is X rounded to TF32 and X_lo is X - X_hi rounded to TF32.  The
+// hi and lo operator halves are stored one after the other, so they form a
+// single 2N-row operand: per K step one MMA computes [A_hi B_hi | A_hi B_lo]
+// into 2N accumulator columns and a second adds A_lo B_hi to the first N.
+// The multipoles are split once per evaluation (k_split_tf32) and the
+// operators at plan time, already in the layouts the MMA reads.  Each slot is
+// contracted in K chunks of 32; chunks are copied into a ring of
+// shared-memory stages while the tensor core works on earlier stages, and a
+// stage is refilled only after the mbarrier signalled by tcgen05.commit says
+// its MMAs have finished.  All waits are bounded; a timeout sets an error
+// word and the CTA still frees its tensor memory.
 #include <cstring>
 #include <type_traits>
 
@@ -114,7 +117,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ int abort_word;
   volatile int *abort = &abort_word;
   constexpr int N = NT;
-  constexpr uint32_t kCols = N <= 32 ? 32 : N <= 64 ? 64 : 128;  // per accumulator
+  // an accumulator holds [A_hi B_hi + A_lo B_hi | A_hi B_lo]: 2N columns
+  constexpr uint32_t kCols = 2 * N <= 32 ? 32 : 2 * N <= 64 ? 64 : 2 * N <= 128 ? 128 : 256;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nc = ncoef(p), ld = coef_pitch(p), nch = kt / kTcKC;
   constexpr uint32_t a_bytes = kTcTile * kTcKC * 4, b_bytes = (uint32_t)N * kTcKC * 4;
@@ -166,10 +170,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * kCols);
 #pragma unroll
       for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
+        float v[16], w[16];
         tc::tmem_ld16(base + (uint32_t)c0, v);
+        tc::tmem_ld16(base + (uint32_t)(N + c0), w);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+        for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i] + w[i];
       }
       tc::fence_before_sync();
       tc::mbar_arrive(&acce[a]);
@@ -177,7 +182,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp == kTcDrainWarps) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_tf32(kTcTile, N);
+      // the hi and lo operator slabs are contiguous, i.e. one 2N-row operand
+      const uint32_t idesc2 = tc::idesc_tf32(kTcTile, 2 * N), idesc1 = tc::idesc_tf32(kTcTile, N);
       constexpr uint32_t sbo = (kTcKC / 4) * 128;
       bool ok = true;
       for (int j = 0; j < ns && ok; ++j) {
@@ -195,18 +201,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (!ok) break;
           tc::fence_after_sync();
           const uint32_t base = tc::smem_addr(sm + (st % NSTAGE) * stage_bytes);
-          const uint32_t ah = base, al = base + a_bytes, bh = base + 2 * a_bytes,
-                         bl = base + 2 * a_bytes + b_bytes;
+          const uint32_t ah = base, al = base + a_bytes, bh = base + 2 * a_bytes;
 #pragma unroll
           for (int ks = 0; ks < kTcKC / 8; ++ks) {
-            const uint32_t off = (uint32_t)ks * 256;
             const uint64_t dah = tc::smem_desc_sw128(ah + (uint32_t)ks * 32);
             const uint64_t dal = tc::smem_desc_sw128(al + (uint32_t)ks * 32);
-            const uint64_t dbh = tc::smem_desc(bh + off, 128, sbo);
-            const uint64_t dbl = tc::smem_desc(bl + off, 128, sbo);
-            tc::mma_tf32(dtm, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-            tc::mma_tf32(dtm, dah, dbl, idesc, 1u);
-            tc::mma_tf32(dtm, dal, dbh, idesc, 1u);
+            const uint64_t dbh = tc::smem_desc(bh + (uint32_t)ks * 256, 128, sbo);
+            // A_hi [B_hi; B_lo] into all 2N columns, then A_lo B_hi into the first N
+            tc::mma_tf32(dtm, dah, dbh, idesc2, (c > 0 || ks > 0) ? 1u : 0u);
+            tc::mma_tf32(dtm, dal, dbh, idesc1, 1u);
           }
           tc::mma_commit(&empty[st % NSTAGE]);
         }
