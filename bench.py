@@ -131,10 +131,10 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ oracle
-def cpu_baseline(n_sample, order, leaf, gpu_phi_at=None):
-    """The CPU oracle (FP64 plan + FMM) on a bounded Plummer sample.  Also
-    returns the oracle's direct sum at `gpu_phi_at` targets of the full
-    problem (for the error statement)."""
+def cpu_baseline(n_sample, order, leaf, n_one_core=131072):
+    """The CPU oracle (FP64 plan + FMM with gradients) on a bounded Plummer
+    sample, on all host cores, and on one core (a subprocess with
+    OMP_NUM_THREADS=1) on a smaller sample."""
     import oracle
     from paper_1602_02244_gb300 import workloads
     xyz, q = workloads.plummer_problem(n_sample, 0)
@@ -145,11 +145,24 @@ def cpu_baseline(n_sample, order, leaf, gpu_phi_at=None):
     out = {"value": n_sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
            "sample": "Plummer N=%d (same distribution, charges 1/N), p=%d, leaf %d: plan + FP64 "
                      "FMM eval with gradients, %.1f s" % (n_sample, order, leaf, dt)}
-    ref = None
-    if gpu_phi_at is not None:
-        xyz_full, q_full, sel = gpu_phi_at
-        ref = oracle.direct(xyz_full, q_full, xyz_full[sel])
-    return out, ref
+    code = ("import json, time, oracle\n"
+            "from paper_1602_02244_gb300 import workloads\n"
+            "xyz, q = workloads.plummer_problem(%d, 0)\n"
+            "t0 = time.perf_counter()\n"
+            "oracle.Tree(xyz, %d).eval(%d, q, grad=True)\n"
+            "print(json.dumps({'s': time.perf_counter() - t0, 'cores': oracle.num_threads()}))\n"
+            % (n_one_core, leaf, order))
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                           text=True, timeout=300)
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        out["one_core"] = {"value": n_one_core / one["s"], "unit": UNIT, "cores": one["cores"],
+                           "sample": "Plummer N=%d, same order and leaf, %.1f s" % (n_one_core,
+                                                                                    one["s"])}
+    except Exception as e:  # reported, not fatal
+        out["one_core"] = {"error": str(e)[:200]}
+    return out
 
 
 def run_reference(args):
@@ -363,10 +376,19 @@ def run_ours(args):
     ms = max_over_ranks(float(np.mean(step_ms)), world, dev)
     value = n * world / (ms / 1e3)
 
-    # error statement: GPU result vs the direct sum on sampled targets
-    sel = workloads.sample_targets(n, 1024, 1)
-    phi_s = phi.cpu().numpy()[sel]
-    grad_s = grad.cpu().numpy()[sel]
+    # error statement: the result against the FP64 brute-force sum (fmm_direct)
+    # on 4096 sampled targets
+    sel = workloads.sample_targets(n, 4096, 1)
+    sel_t = torch.tensor(sel, device=dev)
+    pd, gd = binding.direct(X, Q, X[sel_t])
+    pd, gd = pd.cpu().numpy(), gd.cpu().numpy()
+
+    def rel_err(ph, gr):
+        return {"phi": float(np.linalg.norm(ph.cpu().numpy()[sel] - pd) / np.linalg.norm(pd)),
+                "grad": float(np.linalg.norm(gr.cpu().numpy()[sel] - gd) / np.linalg.norm(gd)),
+                "targets": int(len(sel)), "reference": "fmm_direct (FP64 brute force)"}
+
+    err_mixed = rel_err(phi, grad)
 
     # roofline of the dominant pass
     peaks = measured_peaks()
@@ -384,6 +406,19 @@ def run_ours(args):
         # one product, not the three of the hi/lo split
         tf32_peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
         work["M2L"] = ("tensor", 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s", tf32_peak)
+    # bandwidth-bound passes: algorithmic bytes (read + write once) per pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    nleaves = int(np.sum(layout["box_nchild"] == 0))
+    nb = sizes["nboxes"]
+    cb = 4 if args.precision == "mixed" else 8
+    hbm_bytes = {"keys+sort": n * (24 + 12) + 8 * 2 * n * 12,   # keys; 8 radix passes
+                 "P2M": n * 16 + nleaves * nc * cb,
+                 "M2M": 2 * nb * nc * cb,
+                 "L2L": 2 * nb * nc * cb,
+                 "L2P": n * 16 + nleaves * nc * cb + n * 32,
+                 "reduce": n * 64 + n * 32}
+    for k, b in hbm_bytes.items():
+        work[k] = ("hbm", b / 1e9, "GB/s", hbm)
     dom = max(pass_ms, key=pass_ms.get)
     if dom in work:
         bound, units, unit, peak = work[dom]
@@ -409,7 +444,8 @@ def run_ours(args):
                                    "step = plan (keys, sort, octree, U/V/W/X lists) + eval (phi and "
                                    "grad)" % (n, p, S, "autotuned" if args.leaf == 0 else "fixed",
                                               args.precision),
-                       "m2l": "tensor cores (tcgen05 TF32, 3-product split)" if m2l_tensor
+                       "m2l": "tensor cores (tcgen05 TF32, three-product split in two MMAs)"
+                              if m2l_tensor
                               else "CUDA cores",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MB flush between steps; working set >> L2",
@@ -418,7 +454,7 @@ def run_ours(args):
                        "p2p_pairs": pairs},
             "clocks": clk, "gpu_launches": launches, "wall_s_timed": t_wall,
             "pass_ms": pass_ms, "pass_launches": pass_launch, "roofline": roof,
-            "pass_roofline": other}
+            "pass_roofline": other, "rel_error_vs_direct": err_mixed}
 
     # plan-reused eval only (the paper's mat-vec application time)
     L.fmm_profile(plan._h, 0)
@@ -462,12 +498,20 @@ def run_ours(args):
         line["e2e"] = {"value": n * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                        "d2h_bytes_per_step": 32 * n, "ms": 1e3 * t_e2e}
 
-    # plain FP64 GPU FMM on the same problem (same order), for comparison
+    # plain FP64 GPU FMM at the smallest order whose direct-sum error is no
+    # larger than the mixed-precision result's, for comparison
     if not args.no_fp64 and args.precision == "mixed":
-        plan64 = binding.Plan(X, leaf_size=S, order=p, precision="fp64")
         phi64 = torch.empty_like(phi)
         g64 = torch.empty_like(grad)
-        plan64.eval(Q, out=(phi64, g64))
+        tried = []
+        for p64 in range(max(2, p - 3), 13):
+            plan64 = binding.Plan(X, leaf_size=S, order=p64, precision="fp64")
+            plan64.eval(Q, out=(phi64, g64))
+            e64 = rel_err(phi64, g64)
+            tried.append({"order": p64, "phi": e64["phi"]})
+            if e64["phi"] <= err_mixed["phi"] or p64 == 12:
+                break
+            plan64.close()
         barrier()
         reps = 2
         e0.record(stream)
@@ -477,11 +521,16 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         ms64 = e0.elapsed_time(e1) / reps
-        d64 = phi64.cpu().numpy()
-        line["fp64_same_order"] = {"value": n / (ms64 / 1e3), "unit": UNIT, "ms": ms64,
-                                   "mixed_speedup": ms64 / ms,
-                                   "mixed_vs_fp64_rel_l2": float(np.linalg.norm(phi.cpu().numpy() - d64)
-                                                                 / np.linalg.norm(d64))}
+        e0.record(stream)
+        plan64.eval(Q, out=(phi64, g64))
+        e1.record(stream)
+        e1.synchronize()
+        ms64_eval = e0.elapsed_time(e1)
+        line["fp64_equal_error"] = {"order": p64, "value": n / (ms64 / 1e3), "unit": UNIT,
+                                    "ms": ms64, "eval_only_ms": ms64_eval,
+                                    "rel_error_vs_direct": e64, "orders_tried": tried,
+                                    "mixed_speedup": ms64 / ms,
+                                    "mixed_speedup_eval_only": ms64_eval / ms_eval}
         plan64.close()
 
     if not args.no_batch:
@@ -490,14 +539,7 @@ def run_ours(args):
         line["lattice"] = lattice_leg(dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, ref = cpu_baseline(args.cpu_sample, p, S, (xyz_np, q_np, sel))
-        line["cpu_baseline"] = cb
-        if ref is not None:
-            pd, gd = ref
-            line["rel_error_vs_direct"] = {
-                "phi": float(np.linalg.norm(phi_s - pd) / np.linalg.norm(pd)),
-                "grad": float(np.linalg.norm(grad_s - gd) / np.linalg.norm(gd)),
-                "targets": int(len(sel))}
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample, p, S)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
