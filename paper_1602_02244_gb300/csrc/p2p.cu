@@ -13,6 +13,8 @@
 // points share a Morton key, hence a leaf), so only the leaf's own points go
 // through the masked loop (rinv = 0 at r2 = 0).  Each lane accumulates a
 // staged batch in T (FP32 in mixed mode) and adds batch totals in FP64.
+// The FP64 kernel below is the plain form; the FP32 kernel further down packs
+// the sources in pairs.
 #include "eval_kernels.cuh"
 
 namespace fmm {
@@ -28,8 +30,6 @@ constexpr int kMaxTPL = 4;  // targets per lane
 
 template <typename T>
 __device__ __forceinline__ T rsqrt_t(T x);
-template <>
-__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
@@ -186,6 +186,192 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
   }
 }
 
+// ---------------------------------------------------------------- FP32
+// Mixed precision: the same warp-per-leaf structure, with the sources packed
+// in pairs so that every FP32 instruction works on two pairs at once
+// (fadd2/fmul2/ffma2).  A staged pair is two 16-byte vectors
+//   (-x0, -x1, -y0, -y1) and (-z0, -z1, q0, q1)
+// (negated coordinates: x_i - x_j is one packed add).  Each source leaf's
+// piece is padded to an even length with a zero-charge source 1e18 away
+// (finite r2, rinv ~ 1e-18, contribution exactly 0), so pairs never straddle
+// pieces and only the leaf's own piece needs the zero-distance mask.  The
+// gradient is accumulated as +sum q rinv^3 (x_i - x_j) and negated once.
+__device__ __forceinline__ float rsqrt_approx_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+constexpr float kPadFar = 1e18f;
+
+template <int TPL, bool kMask>
+__device__ __forceinline__ void interact2(const float4 &a, const float4 &b, const float2 (&tx)[kMaxTPL],
+                                          const float2 (&ty)[kMaxTPL], const float2 (&tz)[kMaxTPL],
+                                          float2 (&acc)[kMaxTPL][4]) {
+  const float2 nsx = make_float2(a.x, a.y), nsy = make_float2(a.z, a.w);
+  const float2 nsz = make_float2(b.x, b.y), q = make_float2(b.z, b.w);
+#pragma unroll
+  for (int t = 0; t < TPL; ++t) {
+    const float2 dx = __fadd2_rn(tx[t], nsx), dy = __fadd2_rn(ty[t], nsy), dz = __fadd2_rn(tz[t], nsz);
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    float2 rinv = make_float2(rsqrt_approx_ftz(r2.x), rsqrt_approx_ftz(r2.y));
+    if (kMask) {
+      rinv.x = r2.x > 0.f ? rinv.x : 0.f;
+      rinv.y = r2.y > 0.f ? rinv.y : 0.f;
+    }
+    const float2 qr = __fmul2_rn(q, rinv);
+    const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(rinv, rinv));
+    acc[t][0] = __fadd2_rn(acc[t][0], qr);
+    acc[t][1] = __ffma2_rn(qr3, dx, acc[t][1]);
+    acc[t][2] = __ffma2_rn(qr3, dy, acc[t][2]);
+    acc[t][3] = __ffma2_rn(qr3, dz, acc[t][3]);
+  }
+}
+
+template <int TPL>
+__device__ __forceinline__ void sweep2(const float4 *sa, const float4 *sb, int k0, int k1, bool self,
+                                       const float2 (&tx)[kMaxTPL], const float2 (&ty)[kMaxTPL],
+                                       const float2 (&tz)[kMaxTPL], float2 (&acc)[kMaxTPL][4]) {
+  if (self) {
+    for (int k = k0; k < k1; ++k) interact2<TPL, true>(sa[k], sb[k], tx, ty, tz, acc);
+  } else {
+#pragma unroll 2
+    for (int k = k0; k < k1; ++k) interact2<TPL, false>(sa[k], sb[k], tx, ty, tz, acc);
+  }
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
+    k_p2p_f32(int64_t nleaves, const int32_t *__restrict__ leaves, const int32_t *__restrict__ uoff,
+              const int32_t *__restrict__ uidx, const int32_t *__restrict__ first,
+              const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
+              const float4 *__restrict__ src, const double *__restrict__ side, int64_t n,
+              double *__restrict__ near) {
+  static_assert(CAP % 2 == 0, "pairs");
+  __shared__ float4 sa_all[kP2PWarps][CAP / 2], sb_all[kP2PWarps][CAP / 2];
+  __shared__ int32_t s_incl_all[kP2PWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t li = (int64_t)blockIdx.x * kP2PWarps + warp;
+  if (li >= nleaves) return;  // whole warp: there are no block-wide barriers below
+  float4 *sa = sa_all[warp], *sb = sb_all[warp];
+  float *saf = reinterpret_cast<float *>(sa), *sbf = reinterpret_cast<float *>(sb);
+  int32_t *s_incl = s_incl_all[warp];
+  const int32_t B = leaves[li];
+  const BoxGeo gb = geo[B];
+  const double sbs = side[B];
+  const int32_t fb = first[B], cb = count[B];
+  const int32_t e0 = uoff[B], e1 = uoff[B + 1];
+  for (int32_t tc = 0; tc < cb; tc += 32 * kMaxTPL) {
+    const int tcount = min(32 * kMaxTPL, cb - tc);
+    const int tpl = (tcount + 31) / 32;
+    float2 tx[kMaxTPL], ty[kMaxTPL], tz[kMaxTPL];
+#pragma unroll
+    for (int t = 0; t < kMaxTPL; ++t) {
+      const int i = lane + 32 * t;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < tcount) v = src[fb + tc + i];
+      tx[t] = make_float2(v.x, v.x);
+      ty[t] = make_float2(v.y, v.y);
+      tz[t] = make_float2(v.z, v.z);
+    }
+    double tot[kMaxTPL][4] = {};
+    int32_t e = e0, off = 0;  // next source: leaf uidx[e], point `off` within it
+    while (e < e1) {
+      // ---- metadata of up to 32 source leaves, one per lane
+      int32_t c = 0, f = 0, A = -1;
+      float sx = 0.f, sy = 0.f, sz = 0.f;
+      if (e + lane < e1) {
+        A = uidx[e + lane];
+        const BoxGeo ga = geo[A];
+        const int32_t skip = lane == 0 ? off : 0;
+        f = first[A] + skip;
+        c = count[A] - skip;
+        const double sa_ = side[A];
+        sx = (float)center_delta(ga.ix, sa_, gb.ix, sbs);
+        sy = (float)center_delta(ga.iy, sa_, gb.iy, sbs);
+        sz = (float)center_delta(ga.iz, sa_, gb.iz, sbs);
+      }
+      int32_t incl = c + (c & 1);  // padded to an even length
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const unsigned fit = __ballot_sync(0xffffffffu, e + lane < e1 && incl <= CAP);
+      const int m = __popc(fit);  // incl is non-decreasing: the first m leaves fit
+      const int npiece = m == 0 ? 1 : m;
+      s_incl[lane] = m == 0 ? CAP : incl;  // m == 0: take CAP points of one oversized leaf
+      __syncwarp();
+      // ---- copy the points piece by piece, shifted into the target leaf's frame
+      for (int k = 0; k < npiece; ++k) {
+        const int32_t pf = __shfl_sync(0xffffffffu, f, k);
+        const int32_t pc = __shfl_sync(0xffffffffu, c, k);
+        const float px = __shfl_sync(0xffffffffu, sx, k);
+        const float py = __shfl_sync(0xffffffffu, sy, k);
+        const float pz = __shfl_sync(0xffffffffu, sz, k);
+        const int32_t p0 = k > 0 ? s_incl[k - 1] : 0, p1 = s_incl[k];
+        for (int idx = p0 + lane; idx < p1; idx += 32) {
+          const int j = idx - p0;
+          float nx = -kPadFar, ny = -kPadFar, nz = -kPadFar, q = 0.f;
+          if (j < pc) {
+            const float4 v = src[pf + j];
+            nx = -(v.x + px);
+            ny = -(v.y + py);
+            nz = -(v.z + pz);
+            q = v.w;
+          }
+          const int pr = idx >> 1, h = idx & 1;
+          saf[4 * pr + h] = nx;
+          saf[4 * pr + 2 + h] = ny;
+          sbf[4 * pr + h] = nz;
+          sbf[4 * pr + 2 + h] = q;
+        }
+      }
+      __syncwarp();
+      // ---- sweep the staged pairs piece by piece
+      float2 acc[kMaxTPL][4];
+#pragma unroll
+      for (int t = 0; t < kMaxTPL; ++t)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[t][a] = make_float2(0.f, 0.f);
+      for (int k = 0; k < npiece; ++k) {
+        const bool self = __shfl_sync(0xffffffffu, A, k) == B;
+        const int32_t k0 = (k > 0 ? s_incl[k - 1] : 0) >> 1, k1 = s_incl[k] >> 1;
+        switch (tpl) {
+          case 1: sweep2<1>(sa, sb, k0, k1, self, tx, ty, tz, acc); break;
+          case 2: sweep2<2>(sa, sb, k0, k1, self, tx, ty, tz, acc); break;
+          case 3: sweep2<3>(sa, sb, k0, k1, self, tx, ty, tz, acc); break;
+          default: sweep2<4>(sa, sb, k0, k1, self, tx, ty, tz, acc); break;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kMaxTPL; ++t)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) tot[t][a] += (double)acc[t][a].x + (double)acc[t][a].y;
+      if (m == 0) {
+        off += CAP;
+      } else {
+        e += m;
+        off = 0;
+      }
+      __syncwarp();  // the staged batch is consumed before it is overwritten
+    }
+#pragma unroll
+    for (int t = 0; t < kMaxTPL; ++t) {
+      const int i = lane + 32 * t;
+      if (i < tcount) {
+        const int64_t g = fb + tc + i;
+        near[g] = tot[t][0];
+        near[n + g] = -tot[t][1];
+        near[2 * n + g] = -tot[t][2];
+        near[3 * n + g] = -tot[t][3];
+      }
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -195,9 +381,13 @@ void launch_p2p(int64_t nleaves, const int32_t *leaves, const int32_t *uoff, con
                 cudaStream_t s) {
   if (nleaves == 0) return;
   constexpr int CAP = sizeof(T) == 4 ? 640 : 320;  // 10 KB of staged sources per warp
-  k_p2p<T, CAP><<<ceil_div(nleaves, kP2PWarps), kP2PThreads, 0, s>>>(nleaves, leaves, uoff, uidx,
-                                                                      first, count, geo, src, side,
-                                                                      n, near);
+  if constexpr (sizeof(T) == 4) {
+    k_p2p_f32<CAP><<<ceil_div(nleaves, kP2PWarps), kP2PThreads, 0, s>>>(
+        nleaves, leaves, uoff, uidx, first, count, geo, src, side, n, near);
+  } else {
+    k_p2p<T, CAP><<<ceil_div(nleaves, kP2PWarps), kP2PThreads, 0, s>>>(
+        nleaves, leaves, uoff, uidx, first, count, geo, src, side, n, near);
+  }
   FMM_LAUNCH_CHECK();
 }
 
