@@ -115,8 +115,8 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
                                                   P.box_geo.p, P.M32.p, P.ops.m2m64.p, P.M64.p,
                                                   P.M32.p, s);
     } else {
-      launch_m2m<float, float, float, float>(p, b0, nbl, P.box_child.p, P.box_nchild.p, P.box_geo.p,
-                                             P.M32.p, P.ops.m2m32.p, P.M32.p, nullptr, s);
+      launch_m2m_f32q(p, b0, nbl, P.box_child.p, P.box_nchild.p, P.box_geo.p, P.M32.p,
+                      P.ops.m2m32t.p, P.M32.p, s);
     }
   }
   {
@@ -154,8 +154,7 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
                                                         P.L32.p, P.L64.p, P.ops.l2l64.p, P.L64.p,
                                                         P.L32.p, s);
     else
-      launch_l2l<float, float, float, float, float>(p, b0, nbl, P.box_parent.p, P.box_geo.p, P.L32.p,
-                                                    P.L32.p, P.ops.l2l32.p, P.L32.p, nullptr, s);
+      launch_l2l_f32q(p, b0, nbl, P.box_parent.p, P.box_geo.p, P.ops.l2l32t.p, P.L32.p, s);
   }
   {
     PassScope ps_(P, kPassL2P);

@@ -46,6 +46,11 @@ void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, 
                 int64_t nx, const int32_t *xboxes, const int32_t *xslot, const int32_t *first,
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 const T *M, T *K, int64_t n, double *far, cudaStream_t s);
+void launch_m2m_f32q(int p, int32_t b0, int32_t nbl, const int32_t *child, const int32_t *nchild,
+                     const BoxGeo *geo, const float *Mc, const float *opT, float *Mp,
+                     cudaStream_t s);
+void launch_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *parent, const BoxGeo *geo,
+                     const float *opT, float *L, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *perm, const double *far, const double *near,
                     double *phi, double *grad, cudaStream_t s);
 void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double *gq,

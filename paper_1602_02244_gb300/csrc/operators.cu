@@ -182,6 +182,22 @@ void build_operators(fmm_plan_impl &P) {
   }
   up(m2m, P.ops.m2m64, P.ops.m2m32);
   up(l2l, P.ops.l2l64, P.ops.l2l32);
+  {  // transposed FP32 copies: t[o][k][r] = op[o][r][k], r padded to coef_pitch(p)
+    const int ld = coef_pitch(p);
+    std::vector<float> t((size_t)8 * nc * ld);
+    auto tr = [&](const std::vector<double> &h, DBuf<float> &d) {
+      std::fill(t.begin(), t.end(), 0.f);
+      for (int o = 0; o < 8; ++o)
+        for (int r = 0; r < nc; ++r)
+          for (int k = 0; k < nc; ++k)
+            t[((size_t)o * nc + k) * ld + r] = (float)h[(size_t)o * nn + (size_t)r * nc + k];
+      d.resize(t.size(), s);
+      FMM_CUDA(cudaMemcpyAsync(d.p, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+      FMM_CUDA(cudaStreamSynchronize(s));  // t is reused
+    };
+    tr(m2m, P.ops.m2m32t);
+    tr(l2l, P.ops.l2l32t);
+  }
   P.ops.order = p;
 }
 

@@ -295,6 +295,67 @@ __global__ void k_l2l(int p, int32_t b0, int32_t nbl, const int32_t *__restrict_
   if (Lout32) Lout32[(int64_t)b * ld + r] = (float)acc;
 }
 
+// FP32 M2M and L2L with four outputs per thread: thread (box, quad q) owns
+// coefficients 4q..4q+3 and reads the input-major operator as one 16-byte
+// load per input coefficient.  The triangular structure bounds the loops:
+// M2M output degree n uses inputs of degree <= n, L2L inputs of degree >= n.
+__global__ void k_m2m_f32q(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ child,
+                           const int32_t *__restrict__ nchild, const BoxGeo *__restrict__ geo,
+                           const float *__restrict__ Mc, const float4 *__restrict__ opT,
+                           float *__restrict__ Mp) {
+  const int nc = ncoef(p), ld = coef_pitch(p), nq = ld / 4;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nbl * nq) return;
+  const int32_t b = b0 + (int32_t)(t / nq);
+  const int q = (int)(t % nq);
+  const int nch = nchild[b];
+  if (nch == 0) return;  // a leaf keeps its P2M multipole
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (4 * q < nc) {  // rows beyond nc are the zero padding
+    const int kmax = ncoef(degree_of(min(4 * q + 3, nc - 1)));
+    const int32_t c0 = child[b];
+    for (int32_t cc = c0; cc < c0 + nch; ++cc) {
+      const float4 *col = opT + (size_t)octant(geo[cc]) * nc * nq + q;
+      const float *m = Mc + (int64_t)cc * ld;
+      for (int k = 0; k < kmax; ++k) {
+        const float mk = m[k];
+        const float4 w = col[(size_t)k * nq];
+        acc.x = fmaf(w.x, mk, acc.x);
+        acc.y = fmaf(w.y, mk, acc.y);
+        acc.z = fmaf(w.z, mk, acc.z);
+        acc.w = fmaf(w.w, mk, acc.w);
+      }
+    }
+  }
+  reinterpret_cast<float4 *>(Mp + (int64_t)b * ld)[q] = acc;
+}
+
+__global__ void k_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ parent,
+                           const BoxGeo *__restrict__ geo, const float4 *__restrict__ opT,
+                           float *L) {
+  const int nc = ncoef(p), ld = coef_pitch(p), nq = ld / 4;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nbl * nq) return;
+  const int32_t b = b0 + (int32_t)(t / nq);
+  const int q = (int)(t % nq);
+  if (4 * q >= nc) return;
+  const int32_t P = parent[b];
+  const int n0 = degree_of(4 * q);
+  const float4 *col = opT + (size_t)octant(geo[b]) * nc * nq + q;
+  const float *lp = L + (int64_t)P * ld;
+  float4 *out = reinterpret_cast<float4 *>(L + (int64_t)b * ld) + q;
+  float4 acc = *out;
+  for (int k = n0 * n0; k < nc; ++k) {
+    const float lk = lp[k];
+    const float4 w = col[(size_t)k * nq];
+    acc.x = fmaf(w.x, lk, acc.x);
+    acc.y = fmaf(w.y, lk, acc.y);
+    acc.z = fmaf(w.z, lk, acc.z);
+    acc.w = fmaf(w.w, lk, acc.w);
+  }
+  *out = acc;
+}
+
 template <typename Tin>
 __global__ void k_to_f64(int64_t count, const Tin *__restrict__ in, double *__restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -633,6 +694,25 @@ void launch_l2l(int p, int32_t b0, int32_t nbl, const int32_t *parent, const Box
   k_l2l<Tself, Tpar, Tout, Top, Tacc><<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, parent, geo,
                                                                          Lself, Lpar, ops, Lout,
                                                                          Lout32);
+  FMM_LAUNCH_CHECK();
+}
+
+void launch_m2m_f32q(int p, int32_t b0, int32_t nbl, const int32_t *child, const int32_t *nchild,
+                     const BoxGeo *geo, const float *Mc, const float *opT, float *Mp,
+                     cudaStream_t s) {
+  if (nbl == 0) return;
+  const int64_t tot = (int64_t)nbl * (coef_pitch(p) / 4);
+  k_m2m_f32q<<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, child, nchild, geo, Mc,
+                                                reinterpret_cast<const float4 *>(opT), Mp);
+  FMM_LAUNCH_CHECK();
+}
+
+void launch_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *parent, const BoxGeo *geo,
+                     const float *opT, float *L, cudaStream_t s) {
+  if (nbl == 0) return;
+  const int64_t tot = (int64_t)nbl * (coef_pitch(p) / 4);
+  k_l2l_f32q<<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, parent, geo,
+                                                reinterpret_cast<const float4 *>(opT), L);
   FMM_LAUNCH_CHECK();
 }
 

@@ -19,6 +19,9 @@ struct Operators {
   //   d = anchor(target) - anchor(source); m2m[8], l2l[8] by child octant.
   DBuf<double> m2l64, m2m64, l2l64;
   DBuf<float> m2l32, m2m32, l2l32;
+  // FP32 M2M / L2L, input-major with the outputs contiguous and zero padded:
+  // [8][(p+1)^2][coef_pitch(p)] (4 outputs per 16-byte load)
+  DBuf<float> m2m32t, l2l32t;
   // FP32 M2L, output-major and zero padded: m2l32p[343][m2l_rows(p)][coef_pitch(p)]
   DBuf<float> m2l32p;
   // tensor-core M2L: TF32 hi/lo halves in the MMA's core-matrix order
