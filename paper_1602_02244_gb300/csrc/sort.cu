@@ -4,8 +4,13 @@
 // digits of its 4096-key tile; (2) one device-wide exclusive scan over the
 // digit-major count table gives every (digit, tile) its output base; (3) every
 // CTA ranks its keys stably (warp match_any per 32-key round, warp-ordered
-// digit counters in shared memory) and scatters.  No inter-CTA waits.
+// digit counters in shared memory), stages the tile in shared memory in digit
+// order and writes each digit's run contiguously.  No inter-CTA waits.
 #include "sort.cuh"
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
 
 namespace fmm {
 
@@ -102,6 +107,8 @@ constexpr int kRsItems = 16;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 4096 keys per CTA
 constexpr int kRsWarpSeg = 32 * kRsItems;       // 512 keys per warp
+constexpr int kRsSmemKeys = kRsTile * 8;        // staged tile: keys
+constexpr int kRsSmemVals = kRsTile * 12;       // keys and 32-bit values
 
 __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
                              int32_t *__restrict__ hist, int nblocks) {
@@ -117,19 +124,29 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int s
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// Scatter one 8-bit digit pass.  Each warp ranks its 512 keys per digit
+// (match_any), the CTA turns the per-warp counts into tile-local digit
+// offsets, places its 4096 keys in shared memory in digit order, and then
+// writes each digit's run to its global slot with consecutive threads on
+// consecutive addresses.  The order within a digit is (warp, item, lane),
+// i.e. input order: the sort is stable.
 template <bool kVals>
 __global__ void __launch_bounds__(kRsThreads)
     k_radix_scatter(const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, int64_t n,
                     int shift, const int32_t *__restrict__ offs, int nblocks,
                     uint64_t *__restrict__ kout, int32_t *__restrict__ vout) {
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(rs_smem);  // kRsTile keys
+  int32_t *sv = reinterpret_cast<int32_t *>(sk + kRsTile);  // kRsTile values
   __shared__ int32_t whist[kRsWarps][256];
-  __shared__ int32_t gbase[256];
+  __shared__ int32_t gbase[256], dstart[256], wsum[kRsWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int w = 0; w < kRsWarps; ++w) whist[w][threadIdx.x] = 0;
   gbase[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
   __syncthreads();
   const unsigned lt_mask = (1u << lane) - 1u;
-  const int64_t seg = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * kRsWarpSeg;
+  const int64_t tile0 = (int64_t)blockIdx.x * kRsTile;
+  const int64_t seg = tile0 + (int64_t)warp * kRsWarpSeg;
   uint64_t key[kRsItems];
   int32_t val[kRsItems];
   int32_t rank[kRsItems];
@@ -148,13 +165,24 @@ __global__ void __launch_bounds__(kRsThreads)
     rank[r] = prev + __popc(peers & lt_mask);
   }
   __syncthreads();
-  {  // exclusive scan over warps, per digit
-    int32_t s = 0;
+  {  // per digit (thread = digit): exclusive scan over warps, then over digits
+    int32_t tot = 0;
     for (int w = 0; w < kRsWarps; ++w) {
       int32_t c = whist[w][threadIdx.x];
-      whist[w][threadIdx.x] = s;
-      s += c;
+      whist[w][threadIdx.x] = tot;
+      tot += c;
     }
+    int32_t v = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    int32_t woff = 0;
+    for (int w = 0; w < warp; ++w) woff += wsum[w];
+    dstart[threadIdx.x] = woff + v - tot;
   }
   __syncthreads();
 #pragma unroll
@@ -162,10 +190,19 @@ __global__ void __launch_bounds__(kRsThreads)
     int64_t i = seg + r * 32 + lane;
     if (i < n) {
       unsigned d = (unsigned)((key[r] >> shift) & 255u);
-      int64_t pos = (int64_t)gbase[d] + whist[warp][d] + rank[r];
-      kout[pos] = key[r];
-      if (kVals) vout[pos] = val[r];
+      const int32_t lp = dstart[d] + whist[warp][d] + rank[r];
+      sk[lp] = key[r];
+      if (kVals) sv[lp] = val[r];
     }
+  }
+  __syncthreads();
+  const int cnt = (int)min((int64_t)kRsTile, n - tile0);
+  for (int i = threadIdx.x; i < cnt; i += kRsThreads) {
+    const uint64_t k = sk[i];
+    const unsigned d = (unsigned)((k >> shift) & 255u);
+    const int64_t pos = (int64_t)gbase[d] + (i - dstart[d]);
+    kout[pos] = k;
+    if (kVals) vout[pos] = sv[i];
   }
 }
 
@@ -206,22 +243,46 @@ void scan_exclusive_raw(const int32_t *in, int32_t *out, int64_t n, int32_t *d_t
   FMM_LAUNCH_CHECK();
 }
 
+// The staged scatter needs more than the default 48 KB of dynamic shared
+// memory; the opt-in is set once per device.
+static void launch_scatter(const uint64_t *keys, const int32_t *vals, int64_t n, int sh,
+                    const int32_t *hist, int nb, uint64_t *tkeys, int32_t *tvals, cudaStream_t s) {
+  static std::mutex mu;
+  static std::vector<int> configured;
+  int dev = 0;
+  FMM_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(configured.begin(), configured.end(), dev) == configured.end()) {
+      FMM_CUDA(cudaFuncSetAttribute(k_radix_scatter<true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kRsSmemVals));
+      FMM_CUDA(cudaFuncSetAttribute(k_radix_scatter<false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kRsSmemKeys));
+      configured.push_back(dev);
+    }
+  }
+  if (vals)
+    k_radix_scatter<true><<<nb, kRsThreads, kRsSmemVals, s>>>(keys, vals, n, sh, hist, nb, tkeys,
+                                                               tvals);
+  else
+    k_radix_scatter<false><<<nb, kRsThreads, kRsSmemKeys, s>>>(keys, nullptr, n, sh, hist, nb,
+                                                                tkeys, nullptr);
+  FMM_LAUNCH_CHECK();
+}
+
 void radix_sort_raw(uint64_t *keys, int32_t *vals, uint64_t *tkeys, int32_t *tvals, int64_t n,
                     const int *shifts, int nshifts, int32_t *hist, int32_t *scan_tmp,
                     cudaStream_t s) {
   if (n <= 1 || nshifts <= 0) return;
   if (nshifts % 2 != 0) throw Error(FMM_ERR_INVALID_ARG, "radix_sort_raw needs an even pass count");
+
   int nb = ceil_div(n, kRsTile);
   for (int ip = 0; ip < nshifts; ++ip) {
     const int sh = shifts[ip];
     k_radix_hist<<<nb, kRsThreads, 0, s>>>(keys, n, sh, hist, nb);
     FMM_LAUNCH_CHECK();
     scan_exclusive_raw(hist, hist, (int64_t)256 * nb, nullptr, scan_tmp, s);
-    if (vals)
-      k_radix_scatter<true><<<nb, kRsThreads, 0, s>>>(keys, vals, n, sh, hist, nb, tkeys, tvals);
-    else
-      k_radix_scatter<false><<<nb, kRsThreads, 0, s>>>(keys, nullptr, n, sh, hist, nb, tkeys, nullptr);
-    FMM_LAUNCH_CHECK();
+    launch_scatter(keys, vals, n, sh, hist, nb, tkeys, tvals, s);
     std::swap(keys, tkeys);
     std::swap(vals, tvals);
   }
@@ -246,13 +307,8 @@ void radix_sort(DBuf<uint64_t> &keys, DBuf<int32_t> &vals, DBuf<uint64_t> &tkeys
     k_radix_hist<<<nb, kRsThreads, 0, s>>>(keys.p, n, sh, hist.p, nb);
     FMM_LAUNCH_CHECK();
     scan_exclusive(hist.p, hist.p, (int64_t)256 * nb, nullptr, tmp, s);
-    if (has_vals)
-      k_radix_scatter<true><<<nb, kRsThreads, 0, s>>>(keys.p, vals.p, n, sh, hist.p, nb, tkeys.p,
-                                                      tvals.p);
-    else
-      k_radix_scatter<false><<<nb, kRsThreads, 0, s>>>(keys.p, nullptr, n, sh, hist.p, nb,
-                                                       tkeys.p, nullptr);
-    FMM_LAUNCH_CHECK();
+    launch_scatter(keys.p, has_vals ? vals.p : nullptr, n, sh, hist.p, nb, tkeys.p,
+                   has_vals ? tvals.p : nullptr, s);
     std::swap(keys, tkeys);
     if (has_vals) std::swap(vals, tvals);
   }

@@ -225,30 +225,36 @@ __device__ __forceinline__ int32_t lower_bound_digit(const uint64_t *keys, int32
   return f;
 }
 
+// One warp per box of the level: lanes 0-7 find the 8 child boundaries (first
+// key whose next 3-bit digit is >= o + 1) with independent binary searches,
+// so the dependent-load chain of a box is one search deep, not eight.  The
+// boundaries are kept for k_split_make.
 __global__ void k_split_count(int level, int32_t b0, int32_t nbl, const int32_t *__restrict__ first,
                               const int32_t *__restrict__ count, const uint64_t *__restrict__ keys,
-                              int leaf_size, int max_depth, int32_t *__restrict__ nchild) {
-  int32_t t = blockIdx.x * kT + threadIdx.x;
-  if (t >= nbl) return;
-  int32_t b = b0 + t;
-  int32_t c = count[b];
+                              int leaf_size, int max_depth, int32_t *__restrict__ nchild,
+                              int32_t *__restrict__ bnd) {
+  const int lane = threadIdx.x & 31;
+  const int32_t t = blockIdx.x * (kT / 32) + (threadIdx.x >> 5);
+  if (t >= nbl) return;  // whole warp
+  const int32_t b = b0 + t;
+  const int32_t c = count[b];
   if (c <= leaf_size || level >= max_depth) {
-    nchild[t] = 0;
+    if (lane == 0) nchild[t] = 0;
     return;
   }
-  int shift = 3 * (kMaxDepth - (level + 1));
-  int32_t f = first[b], e = f + c, k = 0, s = f;
-  for (uint32_t o = 0; o < 8; ++o) {
-    int32_t s1 = lower_bound_digit(keys, s, e, shift, o + 1);
-    k += (s1 > s);
-    s = s1;
-  }
-  nchild[t] = k;
+  const int shift = 3 * (kMaxDepth - (level + 1));
+  const int32_t f = first[b], e = f + c;
+  const int32_t s1 = lane < 8 ? lower_bound_digit(keys, f, e, shift, (uint32_t)lane + 1) : e;
+  int32_t s0 = __shfl_up_sync(0xffffffffu, s1, 1);
+  if (lane == 0) s0 = f;
+  const unsigned nonempty = __ballot_sync(0xffffffffu, lane < 8 && s1 > s0);
+  if (lane < 8) bnd[(int64_t)t * 8 + lane] = s1;
+  if (lane == 0) nchild[t] = __popc(nonempty);
 }
 
 __global__ void k_split_make(int level, int32_t b0, int32_t nbl, int32_t child0,
                              const int32_t *__restrict__ nchild, const int32_t *__restrict__ coff,
-                             const uint64_t *__restrict__ keys, int32_t *first, int32_t *count,
+                             const int32_t *__restrict__ bnd, int32_t *first, int32_t *count,
                              uint64_t *bkey, int32_t *blevel, int32_t *parent, int32_t *child,
                              int32_t *bnchild, int32_t *bprob) {
   int32_t t = blockIdx.x * kT + threadIdx.x;
@@ -262,11 +268,10 @@ __global__ void k_split_make(int level, int32_t b0, int32_t nbl, int32_t child0,
   }
   int32_t c = child0 + coff[t];
   child[b] = c;
-  int shift = 3 * (kMaxDepth - (level + 1));
-  int32_t f = first[b], e = f + count[b], s = f;
+  int32_t s = first[b];
   uint64_t pk = bkey[b];
   for (uint32_t o = 0; o < 8; ++o) {
-    int32_t s1 = lower_bound_digit(keys, s, e, shift, o + 1);
+    const int32_t s1 = bnd[(int64_t)t * 8 + o];
     if (s1 > s) {
       first[c] = s;
       count[c] = s1 - s;
@@ -729,16 +734,18 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
     int32_t b0 = P.level_off[l], nbl = P.level_off[l + 1] - b0;
     P.s_i32a.resize(nbl + 1, s);
     P.s_i32b.resize(nbl + 1, s);
-    k_split_count<<<grid(nbl), kT, 0, s>>>(l, b0, nbl, P.box_first.p, P.box_count.p, P.keys.p,
-                                            P.leaf_size, P.max_depth, P.s_i32a.p);
+    P.s_i32c.resize((size_t)nbl * 8, s);  // child boundaries, 8 per box
+    k_split_count<<<ceil_div((int64_t)nbl, (int64_t)(kT / 32)), kT, 0, s>>>(
+        l, b0, nbl, P.box_first.p, P.box_count.p, P.keys.p, P.leaf_size, P.max_depth, P.s_i32a.p,
+        P.s_i32c.p);
     FMM_LAUNCH_CHECK();
     scan_exclusive(P.s_i32a.p, P.s_i32b.p, nbl, P.s_i32b.p + nbl, P.s_scan, s);
     int32_t nnew = read_scalar(P.s_i32b.p + nbl, s);
     if (nnew > 0) grow_boxes(nb + nnew, nb);
-    k_split_make<<<grid(nbl), kT, 0, s>>>(l, b0, nbl, (int32_t)nb, P.s_i32a.p, P.s_i32b.p, P.keys.p,
-                                           P.box_first.p, P.box_count.p, P.box_key.p, P.box_level.p,
-                                           P.box_parent.p, P.box_child.p, P.box_nchild.p,
-                                           P.box_prob.p);
+    k_split_make<<<grid(nbl), kT, 0, s>>>(l, b0, nbl, (int32_t)nb, P.s_i32a.p, P.s_i32b.p,
+                                           P.s_i32c.p, P.box_first.p, P.box_count.p, P.box_key.p,
+                                           P.box_level.p, P.box_parent.p, P.box_child.p,
+                                           P.box_nchild.p, P.box_prob.p);
     FMM_LAUNCH_CHECK();
     if (nnew == 0) break;
     nb += nnew;
