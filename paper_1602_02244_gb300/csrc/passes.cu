@@ -30,40 +30,37 @@ constexpr bool reg_accumulate() {
   return PT > 0 && ncoef(PT) * (int)sizeof(T) <= 4 * 128;
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
-// Reduce every coefficient over the warp; lane k % 32 writes coefficient k
-// (and zero into the row padding up to ld).
-template <typename T, int NC>
-__device__ __forceinline__ void write_warp_sums(const T (&racc)[NC], int lane, T *row, int ld,
-                                                double *row64) {
+// Warp reduction of NC per-lane sums through a shared-memory transpose: every
+// lane writes its column of buf (NC x 33), then lane l adds up rows l, l + 32,
+// ... over the 32 columns.  ~3 NC instructions per lane instead of the ~10 NC
+// of a shuffle tree.  ADD: add into row[k]; else store and zero the padding
+// up to ld (and mirror into row64 when given).
+template <bool ADD, typename T, int NC>
+__device__ __forceinline__ void transpose_sums(const T (&racc)[NC], int lane, T *buf, T *row, int ld,
+                                               double *row64) {
 #pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    const T v = warp_sum(racc[k]);
-    if (lane == (k & 31)) {
+  for (int k = 0; k < NC; ++k) buf[k * 33 + lane] = racc[k];
+  __syncwarp();
+  for (int k = lane; k < NC; k += 32) {
+    T v = T(0);
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) v += buf[k * 33 + j];
+    if (ADD) {
+      row[k] += v;
+    } else {
       row[k] = v;
       if (row64) row64[k] = (double)v;
     }
   }
-  for (int k = NC + lane; k < ld; k += 32) {
-    row[k] = T(0);
-    if (row64) row64[k] = 0.0;
-  }
+  if (!ADD)
+    for (int k = NC + lane; k < ld; k += 32) {
+      row[k] = T(0);
+      if (row64) row64[k] = 0.0;
+    }
+  __syncwarp();
 }
 
-template <typename T, int NC>
-__device__ __forceinline__ void add_warp_sums(const T (&racc)[NC], int lane, T *row) {
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    const T v = warp_sum(racc[k]);
-    if (lane == (k & 31)) row[k] += v;
-  }
-}
 
 template <typename T>
 __global__ void k_permute_charges(int64_t n, const int32_t *__restrict__ perm,
@@ -108,8 +105,8 @@ __global__ void k_p2m(int p_rt, int64_t nleaves, const int32_t *__restrict__ lea
         if (m > 0) racc[cidx(n, -m)] -= q * im;
       });
     }
-    write_warp_sums<T, NC>(racc, lane, M + (int64_t)b * ld, ld,
-                           (M64 && g.level <= coarse) ? M64 + (int64_t)b * ld : nullptr);
+    transpose_sums<false, T, NC>(racc, lane, buf, M + (int64_t)b * ld, ld,
+                                 (M64 && g.level <= coarse) ? M64 + (int64_t)b * ld : nullptr);
     return;
   }
   T acc[kAccSlots];
@@ -172,24 +169,54 @@ __global__ void k_p2l(int p_rt, int64_t nboxes_x, const int32_t *__restrict__ xb
     T racc[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) racc[k] = T(0);
-    for (int32_t e = xoff[C]; e < xoff[C + 1]; ++e) {
-      const int32_t A = xidx[e];
-      const BoxGeo ga = geo[A];
-      const T sx = (T)center_delta(ga.ix, side[A], gc.ix, ac);
-      const T sy = (T)center_delta(ga.iy, side[A], gc.iy, ac);
-      const T sz = (T)center_delta(ga.iz, side[A], gc.iz, ac);
-      const int32_t f = first[A], c = count[A];
-      for (int32_t j = lane; j < c; j += 32) {
-        const typename V4<T>::type s = src[f + j];
-        const T q = s.w;
-        irregular_stream<T>(PT, (s.x + sx) * inva, (s.y + sy) * inva, (s.z + sz) * inva,
-                            [&](int n, int m, T re, T im) {
-                              racc[cidx(n, m)] += q * re;
-                              if (m > 0) racc[cidx(n, -m)] -= q * im;
-                            });
+    // The X list's source points are taken as one concatenated range, 32 at
+    // a time, so small source leaves do not leave lanes idle: up to 32 leaves'
+    // metadata sit one per lane, and a lane finds the leaf of its point by a
+    // binary search over the inclusive counts (shuffles).
+    const int32_t x1 = xoff[C + 1];
+    for (int32_t eb = xoff[C]; eb < x1; eb += 32) {
+      int32_t c = 0, f = 0;
+      T sx = T(0), sy = T(0), sz = T(0);
+      if (eb + lane < x1) {
+        const int32_t A = xidx[eb + lane];
+        const BoxGeo ga = geo[A];
+        c = count[A];
+        f = first[A];
+        sx = (T)center_delta(ga.ix, side[A], gc.ix, ac);
+        sy = (T)center_delta(ga.iy, side[A], gc.iy, ac);
+        sz = (T)center_delta(ga.iz, side[A], gc.iz, ac);
+      }
+      int32_t incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      const int32_t excl = incl - c;
+      for (int32_t base = 0; base < total; base += 32) {  // warp-uniform trip count
+        const int32_t idx = base + lane;
+        int k = 0;  // first leaf whose inclusive count exceeds idx
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int32_t v = __shfl_sync(0xffffffffu, incl, k + step - 1);
+          if (v <= idx) k += step;
+        }
+        const int32_t fk = __shfl_sync(0xffffffffu, f, k), ek = __shfl_sync(0xffffffffu, excl, k);
+        const T ox = __shfl_sync(0xffffffffu, sx, k), oy = __shfl_sync(0xffffffffu, sy, k),
+                oz = __shfl_sync(0xffffffffu, sz, k);
+        if (idx < total) {
+          const typename V4<T>::type sp = src[fk + (idx - ek)];
+          const T q = sp.w;
+          irregular_stream<T>(PT, (sp.x + ox) * inva, (sp.y + oy) * inva, (sp.z + oz) * inva,
+                              [&](int n, int m, T re, T im) {
+                                racc[cidx(n, m)] += q * re;
+                                if (m > 0) racc[cidx(n, -m)] -= q * im;
+                              });
+        }
       }
     }
-    add_warp_sums<T, NC>(racc, lane, L + (int64_t)C * ld);
+    transpose_sums<true, T, NC>(racc, lane, buf, L + (int64_t)C * ld, ld, nullptr);
     return;
   }
   T acc[kAccSlots];
@@ -647,7 +674,7 @@ void launch_p2m(int p, int64_t nleaves, const int32_t *leaves, const int32_t *fi
     constexpr int P = decltype(PC)::value;
     auto kern = k_p2m<T, P>;
     const int wk = reg_accumulate<T, P>() ? 4 : w;
-    const size_t sm = reg_accumulate<T, P>() ? 0 : per * w;
+    const size_t sm = per * wk;  // per warp: the (NC x 33) sum buffer
     allow_smem(kern, sm);
     kern<<<ceil_div(nleaves, wk), 32 * wk, sm, s>>>(p, nleaves, leaves, first, count, geo, src, side,
                                                     M, M64, coarse);
@@ -666,7 +693,7 @@ void launch_p2l(int p, int64_t nx, const int32_t *xboxes, const int32_t *xoff, c
     constexpr int P = decltype(PC)::value;
     auto kern = k_p2l<T, P>;
     const int wk = reg_accumulate<T, P>() ? 4 : w;
-    const size_t sm = reg_accumulate<T, P>() ? 0 : per * w;
+    const size_t sm = per * wk;  // per warp: the (NC x 33) sum buffer
     allow_smem(kern, sm);
     kern<<<ceil_div(nx, wk), 32 * wk, sm, s>>>(p, nx, xboxes, xoff, xidx, first, count, geo, src,
                                                side, L);
