@@ -40,6 +40,12 @@ PASSES = ["keys+sort", "boxes", "lists", "P2M", "M2M", "M2L", "P2L", "L2L", "L2P
           "reduce"]
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel, taken from one ncu capture of the same kernel and workload
+# (profiles/p2p_packed_plummer4m_p8_leaf192.md); keyed by
+# (pass, N, order, leaf size, precision).  Any other configuration reports null.
+TRAFFIC_BYTES = {("P2P", 4194304, 8, 192, "mixed"): 173.2e6}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -427,7 +433,8 @@ def run_ours(args):
         bound, unit, peak = "hbm", "GB/s", peaks.get("hbm_gbs", 6800.0)
         achieved = None
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": TRAFFIC_BYTES.get((dom, n, p, S, args.precision)),
             "peak_source": ("FP32: %d SMs x %d lanes x 2 flop x %.0f MHz" % (sms, FP32_LANES_PER_SM, max_mhz)
                             if bound == "alu" else
                             "TF32 = measured sustained bf16 x 1.1/2.25 (of measured)" if bound == "tensor"

@@ -95,6 +95,43 @@ __device__ __forceinline__ void irregular_stream(int p, T x, T y, T z, F &&f) {
   }
 }
 
+// The irregular stream for two points at once (the .x and .y halves), on the
+// paired FP32 instructions: the same recurrence as irregular_stream, two
+// evaluations per instruction.  The reciprocal and reciprocal square root of
+// r^2 stay scalar (IEEE division and square root).
+template <typename F>
+__device__ __forceinline__ void irregular_stream2(int p, float2 x, float2 y, float2 z, F &&f) {
+  const float2 r2 = __ffma2_rn(z, z, __ffma2_rn(y, y, __fmul2_rn(x, x)));
+  const float2 inv = make_float2(1.f / r2.x, 1.f / r2.y);
+  float2 dre = make_float2(1.f / sqrtf(r2.x), 1.f / sqrtf(r2.y)), dim = make_float2(0.f, 0.f);
+  const float2 ny = make_float2(-y.x, -y.y);
+#pragma unroll
+  for (int m = 0; m <= p; ++m) {
+    if (m > 0) {
+      const float cm = -(float)(2 * m - 1);
+      const float2 c = __fmul2_rn(make_float2(cm, cm), inv);
+      const float2 t1 = __ffma2_rn(ny, dim, __fmul2_rn(x, dre));  // x dre - y dim
+      const float2 t2 = __ffma2_rn(y, dre, __fmul2_rn(x, dim));   // x dim + y dre
+      dre = __fmul2_rn(c, t1);
+      dim = __fmul2_rn(c, t2);
+    }
+    f(m, m, dre, dim);
+    float2 pre = make_float2(0.f, 0.f), pim = make_float2(0.f, 0.f), cre = dre, cim = dim;
+#pragma unroll
+    for (int n = m + 1; n <= p; ++n) {
+      const float an = (float)(2 * n - 1), nb = -(float)((n - 1) * (n - 1) - m * m);
+      const float2 a = __fmul2_rn(make_float2(an, an), z), b = make_float2(nb, nb);
+      const float2 nre = __fmul2_rn(__ffma2_rn(b, pre, __fmul2_rn(a, cre)), inv);
+      const float2 nim = __fmul2_rn(__ffma2_rn(b, pim, __fmul2_rn(a, cim)), inv);
+      pre = cre;
+      pim = cim;
+      cre = nre;
+      cim = nim;
+      f(n, m, cre, cim);
+    }
+  }
+}
+
 // complex coefficient X_n^m of a real-basis vector v (any -n <= m <= n;
 // zero outside), using X_n^{-m} = (-1)^m conj(X_n^m)
 template <typename T>

@@ -480,9 +480,11 @@ __global__ void k_m2p_prep(int p, int64_t nx, const int32_t *__restrict__ xboxes
   kz = -(im_part ? ai : ar);
   kx = T(0.5) * (im_part ? (bi - ci) : (br - cr));
   ky = im_part ? T(-0.5) * (br + cr) : T(0.5) * (bi + ci);
-  // a real expansion sums Re(X_n^0 I_n^0) + 2 sum_{m>0} Re(X_n^m I_n^m):
-  // the factor 2 of the m > 0 terms is applied here, once per coefficient
-  const T w = m > 0 ? T(2) : T(1);
+  // a real expansion sums Re(X_n^0 I_n^0) + 2 sum_{m>0} Re(X_n^m I_n^m) and
+  // Re(X I) = Re X Re I - Im X Im I: the factor 2 of the m > 0 terms and the
+  // sign of the imaginary slots are applied here, once per coefficient, so
+  // every term of the evaluation is a plain multiply-add
+  const T w = m > 0 ? (im_part ? T(-2) : T(2)) : T(1);
   typename V4<T>::type v;
   v.x = w * k0;
   v.y = w * kx;
@@ -566,10 +568,10 @@ __global__ void __launch_bounds__(kM2PThreads)
                                 fz += kp.w * re;
                                 if (m > 0) {
                                   const V kn = kb[cidx(nn, -m)];
-                                  fp -= kn.x * im;
-                                  fx -= kn.y * im;
-                                  fy -= kn.z * im;
-                                  fz -= kn.w * im;
+                                  fp += kn.x * im;
+                                  fx += kn.y * im;
+                                  fy += kn.z * im;
+                                  fz += kn.w * im;
                                 }
                               });
           const double ia = s_ia[b];
@@ -599,6 +601,142 @@ __global__ void __launch_bounds__(kM2PThreads)
       far[n + i] += a1;
       far[2 * n + i] += a2;
       far[3 * n + i] += a3;
+    }
+    __syncthreads();  // red is rewritten by the next chunk
+  }
+}
+
+// FP32 M2P with two targets per lane: the degree p+1 irregular stream runs
+// on paired FP32 instructions for both targets, and each staged coefficient
+// 4-vector (one 16-byte broadcast load) serves both targets, which halves
+// the shared-memory traffic per evaluation (the scalar kernel is bound by
+// it).  Up to 256 targets per chunk; the 4 warps form 1, 2 or 4 replicas
+// that split the W list, as in the FP64 kernel.
+template <int PT>
+__global__ void __launch_bounds__(kM2PThreads)
+    k_m2p_f32x2(int p_rt, int nstage, const int32_t *__restrict__ wleaves,
+                const int32_t *__restrict__ woff, const int32_t *__restrict__ widx,
+                const int32_t *__restrict__ xslot, const int32_t *__restrict__ first,
+                const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
+                const float4 *__restrict__ src, const double *__restrict__ side,
+                const float4 *__restrict__ K, int64_t n, double *__restrict__ far) {
+  const int p = PT > 0 ? PT : p_rt;
+  extern __shared__ __align__(16) unsigned char m2p_smem[];
+  float4 *ks = reinterpret_cast<float4 *>(m2p_smem);  // [nstage][ld1]
+  __shared__ float s_off[kM2PStage][3], s_inva[kM2PStage];
+  __shared__ double s_ia[kM2PStage];
+  __shared__ int32_t s_slot[kM2PStage];
+  __shared__ double red[4][2][kM2PThreads];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ld1 = coef_pitch(p + 1), nc1 = ncoef(p + 1);
+  const int32_t B = wleaves[blockIdx.x];
+  const BoxGeo gb = geo[B];
+  const double sb = side[B];
+  const int32_t f = first[B], c = count[B], e0 = woff[B], e1 = woff[B + 1];
+  for (int32_t tc = 0; tc < c; tc += 2 * kM2PThreads) {
+    const int tcount = min(2 * kM2PThreads, c - tc);
+    const int wpr = (tcount + 63) / 64;  // warps per replica
+    const int k = 4 / wpr;               // replicas
+    const int rep = warp / wpr, j = (warp - rep * wpr) * 32 + lane, ti = 2 * j;
+    const bool act = rep < k && ti < tcount;
+    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+    if (act) {
+      s0 = src[f + tc + ti];
+      s1 = ti + 1 < tcount ? src[f + tc + ti + 1] : s0;  // a duplicate is evaluated, not stored
+    }
+    double phi[2] = {0, 0}, gx[2] = {0, 0}, gy[2] = {0, 0}, gz[2] = {0, 0};
+    for (int32_t e = e0; e < e1; e += nstage) {
+      const int nb = min(nstage, e1 - e);
+      __syncthreads();  // the previous batch has been consumed
+      if (tid < nb) {
+        const int32_t A = widx[e + tid];
+        const BoxGeo ga = geo[A];
+        const double aa = side[A];
+        s_slot[tid] = xslot[A];
+        s_off[tid][0] = (float)center_delta(gb.ix, sb, ga.ix, aa);
+        s_off[tid][1] = (float)center_delta(gb.iy, sb, ga.iy, aa);
+        s_off[tid][2] = (float)center_delta(gb.iz, sb, ga.iz, aa);
+        s_inva[tid] = (float)(1.0 / aa);
+        s_ia[tid] = 1.0 / aa;
+      }
+      __syncthreads();
+      for (int q = tid; q < nb * nc1; q += kM2PThreads) {
+        const int b = q / nc1, r = q - b * nc1;
+        ks[b * ld1 + r] = K[(int64_t)s_slot[b] * ld1 + r];
+      }
+      __syncthreads();
+      if (act) {
+        for (int b = rep; b < nb; b += k) {
+          const float4 *kb = ks + b * ld1;
+          const float inva = s_inva[b];
+          const float ox = s_off[b][0], oy = s_off[b][1], oz = s_off[b][2];
+          float2 fp = make_float2(0.f, 0.f), fx = fp, fy = fp, fz = fp;
+          irregular_stream2(p + 1, make_float2((s0.x + ox) * inva, (s1.x + ox) * inva),
+                            make_float2((s0.y + oy) * inva, (s1.y + oy) * inva),
+                            make_float2((s0.z + oz) * inva, (s1.z + oz) * inva),
+                            [&](int nn, int m, float2 re, float2 im) {
+                              const float4 kp = kb[cidx(nn, m)];
+                              fp.x = fmaf(kp.x, re.x, fp.x);
+                              fp.y = fmaf(kp.x, re.y, fp.y);
+                              fx.x = fmaf(kp.y, re.x, fx.x);
+                              fx.y = fmaf(kp.y, re.y, fx.y);
+                              fy.x = fmaf(kp.z, re.x, fy.x);
+                              fy.y = fmaf(kp.z, re.y, fy.y);
+                              fz.x = fmaf(kp.w, re.x, fz.x);
+                              fz.y = fmaf(kp.w, re.y, fz.y);
+                              if (m > 0) {
+                                const float4 kn = kb[cidx(nn, -m)];
+                                fp.x = fmaf(kn.x, im.x, fp.x);
+                                fp.y = fmaf(kn.x, im.y, fp.y);
+                                fx.x = fmaf(kn.y, im.x, fx.x);
+                                fx.y = fmaf(kn.y, im.y, fx.y);
+                                fy.x = fmaf(kn.z, im.x, fy.x);
+                                fy.y = fmaf(kn.z, im.y, fy.y);
+                                fz.x = fmaf(kn.w, im.x, fz.x);
+                                fz.y = fmaf(kn.w, im.y, fz.y);
+                              }
+                            });
+          const double ia = s_ia[b], ia2 = ia * ia;
+          phi[0] += (double)fp.x * ia;
+          phi[1] += (double)fp.y * ia;
+          gx[0] += (double)fx.x * ia2;
+          gx[1] += (double)fx.y * ia2;
+          gy[0] += (double)fy.x * ia2;
+          gy[1] += (double)fy.y * ia2;
+          gz[0] += (double)fz.x * ia2;
+          gz[1] += (double)fz.y * ia2;
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      red[0][h][tid] = phi[h];
+      red[1][h][tid] = gx[h];
+      red[2][h][tid] = gy[h];
+      red[3][h][tid] = gz[h];
+    }
+    __syncthreads();
+    // target pair jj (targets 2 jj, 2 jj + 1): replica r holds it at thread r * 32 * wpr + jj
+    if (tid < (tcount + 1) / 2) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int u = 2 * tid + h;
+        if (u < tcount) {
+          double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+          for (int r = 0; r < k; ++r) {
+            const int o = r * 32 * wpr + tid;
+            a0 += red[0][h][o];
+            a1 += red[1][h][o];
+            a2 += red[2][h][o];
+            a3 += red[3][h][o];
+          }
+          const int64_t i = f + tc + u;
+          far[i] += a0;
+          far[n + i] += a1;
+          far[2 * n + i] += a2;
+          far[3 * n + i] += a3;
+        }
+      }
     }
     __syncthreads();  // red is rewritten by the next chunk
   }
@@ -774,16 +912,29 @@ void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, 
   const int64_t tot = nx * ncoef(p + 1);
   k_m2p_prep<T><<<ceil_div(tot, 256), 256, 0, s>>>(p, nx, xboxes, M, K4);
   FMM_LAUNCH_CHECK();
-  // stage as many W boxes as fit in 64 KB (at most kM2PStage)
-  const size_t per_box = (size_t)coef_pitch(p + 1) * sizeof(V);
-  const int nstage = (int)std::max<size_t>(1, std::min<size_t>(kM2PStage, (64 << 10) / per_box));
-  const size_t sm = nstage * per_box;
-  with_order(p, [&](auto PC) {
-    auto kern = k_m2p<T, decltype(PC)::value>;
-    FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    kern<<<(unsigned)nw, kM2PThreads, sm, s>>>(p, nstage, wleaves, woff, widx, xslot, first, count,
-                                               geo, src, side, K4, n, far);
-  });
+  if constexpr (sizeof(T) == 4) {
+    // stage as many W boxes as fit in 32 KB (at most kM2PStage)
+    const size_t per_box = (size_t)coef_pitch(p + 1) * sizeof(float4);
+    const int nstage = (int)std::max<size_t>(1, std::min<size_t>(kM2PStage, (32 << 10) / per_box));
+    const size_t sm = nstage * per_box;
+    with_order(p, [&](auto PC) {
+      auto kern = k_m2p_f32x2<decltype(PC)::value>;
+      FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      kern<<<(unsigned)nw, kM2PThreads, sm, s>>>(p, nstage, wleaves, woff, widx, xslot, first, count,
+                                                 geo, src, side, K4, n, far);
+    });
+  } else {
+    // stage as many W boxes as fit in 64 KB (at most kM2PStage)
+    const size_t per_box = (size_t)coef_pitch(p + 1) * sizeof(V);
+    const int nstage = (int)std::max<size_t>(1, std::min<size_t>(kM2PStage, (64 << 10) / per_box));
+    const size_t sm = nstage * per_box;
+    with_order(p, [&](auto PC) {
+      auto kern = k_m2p<T, decltype(PC)::value>;
+      FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      kern<<<(unsigned)nw, kM2PThreads, sm, s>>>(p, nstage, wleaves, woff, widx, xslot, first, count,
+                                                 geo, src, side, K4, n, far);
+    });
+  }
   FMM_LAUNCH_CHECK();
 }
 
