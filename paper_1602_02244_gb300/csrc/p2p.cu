@@ -25,7 +25,8 @@ namespace {
 // done, so uneven leaf costs leave no idle warps holding an SM slot.
 constexpr int kP2PWarps = 1;
 constexpr int kP2PThreads = 32 * kP2PWarps;
-constexpr int kP2PMinCtas = 16;  // resident CTAs per SM: caps registers at 128
+constexpr int kP2PMinCtas = 16;     // resident CTAs per SM: caps registers at 128
+constexpr int kP2PMinCtasF32 = 20;  // FP32 kernel (totals in shared memory): <= 102 registers
 constexpr int kMaxTPL = 4;  // targets per lane
 
 template <typename T>
@@ -243,7 +244,7 @@ __device__ __forceinline__ void sweep2(const float4 *sa, const float4 *sb, int k
 }
 
 template <int CAP>
-__global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
+__global__ void __launch_bounds__(kP2PThreads, kP2PMinCtasF32)
     k_p2p_f32(int64_t nleaves, const int32_t *__restrict__ leaves, const int32_t *__restrict__ uoff,
               const int32_t *__restrict__ uidx, const int32_t *__restrict__ first,
               const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
@@ -252,6 +253,10 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
   static_assert(CAP % 2 == 0, "pairs");
   __shared__ float4 sa_all[kP2PWarps][CAP / 2], sb_all[kP2PWarps][CAP / 2];
   __shared__ int32_t s_incl_all[kP2PWarps][32];
+  // FP64 running totals of the lane's targets, [target][component][lane]:
+  // touched once per staged batch, so they live in shared memory and leave
+  // the registers to the inner loop (more resident warps)
+  __shared__ double tot_all[kP2PWarps][kMaxTPL * 4][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t li = (int64_t)blockIdx.x * kP2PWarps + warp;
   if (li >= nleaves) return;  // whole warp: there are no block-wide barriers below
@@ -276,7 +281,9 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
       ty[t] = make_float2(v.y, v.y);
       tz[t] = make_float2(v.z, v.z);
     }
-    double tot[kMaxTPL][4] = {};
+    double(*tot)[32] = tot_all[warp];
+#pragma unroll
+    for (int q = 0; q < kMaxTPL * 4; ++q) tot[q][lane] = 0.0;
     int32_t e = e0, off = 0;  // next source: leaf uidx[e], point `off` within it
     while (e < e1) {
       // ---- metadata of up to 32 source leaves, one per lane
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
 #pragma unroll
       for (int t = 0; t < kMaxTPL; ++t)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) tot[t][a] += (double)acc[t][a].x + (double)acc[t][a].y;
+        for (int a = 0; a < 4; ++a) tot[t * 4 + a][lane] += (double)acc[t][a].x + (double)acc[t][a].y;
       if (m == 0) {
         off += CAP;
       } else {
@@ -363,10 +370,10 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
       const int i = lane + 32 * t;
       if (i < tcount) {
         const int64_t g = fb + tc + i;
-        near[g] = tot[t][0];
-        near[n + g] = -tot[t][1];
-        near[2 * n + g] = -tot[t][2];
-        near[3 * n + g] = -tot[t][3];
+        near[g] = tot[t * 4][lane];
+        near[n + g] = -tot[t * 4 + 1][lane];
+        near[2 * n + g] = -tot[t * 4 + 2][lane];
+        near[3 * n + g] = -tot[t * 4 + 3][lane];
       }
     }
   }
@@ -380,8 +387,9 @@ void launch_p2p(int64_t nleaves, const int32_t *leaves, const int32_t *uoff, con
                 const typename V4<T>::type *src, const double *side, int64_t n, double *near,
                 cudaStream_t s) {
   if (nleaves == 0) return;
-  constexpr int CAP = sizeof(T) == 4 ? 640 : 320;  // 10 KB of staged sources per warp
+  constexpr int CAP = sizeof(T) == 4 ? 448 : 320;  // 7 KB (FP32) / 10 KB of staged sources per warp
   if constexpr (sizeof(T) == 4) {
+    // 7 KB of sources + 4 KB of FP64 totals per one-warp CTA: 20 CTAs per SM
     k_p2p_f32<CAP><<<ceil_div(nleaves, kP2PWarps), kP2PThreads, 0, s>>>(
         nleaves, leaves, uoff, uidx, first, count, geo, src, side, n, near);
   } else {
