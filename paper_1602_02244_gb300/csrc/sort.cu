@@ -80,6 +80,38 @@ __global__ void k_scan_sums(int32_t *sums, int nblocks, int32_t *d_total) {
   if (threadIdx.x == 0 && d_total) *d_total = carry;
 }
 
+// Small inputs: one CTA walks the array in tiles of kScanTile with a running
+// carry -- one launch instead of three (in place is allowed).
+constexpr int64_t kScanSingleMax = 16384;
+
+__global__ void k_scan_single(const int32_t *in, int32_t *out, int64_t n, int32_t *d_total) {
+  __shared__ int32_t ws[32];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t t0 = 0; t0 < n; t0 += kScanTile) {
+    const int64_t base = t0 + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = base + k < n ? in[base + k] : 0;
+      sum += v[k];
+    }
+    int32_t tot;
+    int32_t ex = block_exclusive_scan(sum, ws, &tot) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (base + k < n) out[base + k] = ex;
+      ex += v[k];
+    }
+    __syncthreads();  // everyone has read carry
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
 __global__ void k_scan_apply(const int32_t *in, int32_t *out, int64_t n, const int32_t *sums) {
   // each thread owns kScanItems consecutive elements of the tile
   __shared__ int32_t ws[32];
@@ -212,6 +244,11 @@ void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *d_total
                     DBuf<int32_t> &tmp, cudaStream_t s) {
   if (n <= 0) {
     if (d_total) FMM_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int32_t), s));
+    return;
+  }
+  if (n <= kScanSingleMax) {
+    k_scan_single<<<1, kScanThreads, 0, s>>>(in, out, n, d_total);
+    FMM_LAUNCH_CHECK();
     return;
   }
   int nb = ceil_div(n, kScanTile);
