@@ -121,7 +121,8 @@ void release_plan(fmm_plan_impl &P) {
   P.m2l_nslots.release(); P.ops.m2l32p.release(); P.ops.m2l_tc.release(); P.Mhi.release();
   P.Mlo.release(); P.dev_err.release();
   P.xslot.release(); P.K64.release(); P.K32.release(); P.box_prob.release();
-  P.box_side.release(); P.prob_off.release(); P.prob_geom.release();
+  P.box_side.release(); P.prob_off.release(); P.prob_geom.release(); P.iperm.release();
+  P.ops.m2m32t.release(); P.ops.l2l32t.release();
 }
 
 }  // namespace fmm

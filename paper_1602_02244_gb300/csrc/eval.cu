@@ -84,7 +84,7 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   }
   {
     PassScope ps_(P, kPassReduce);
-    launch_combine(n, P.perm.p, P.far_acc.p, P.near_acc.p, d_phi, d_grad, s);
+    launch_combine(n, P.iperm.p, P.far_acc.p, P.near_acc.p, d_phi, d_grad, s);
   }
 }
 
@@ -175,7 +175,7 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   }
   {
     PassScope ps_(P, kPassReduce);
-    launch_combine(n, P.perm.p, P.far_acc.p, P.near_acc.p, d_phi, d_grad, s);
+    launch_combine(n, P.iperm.p, P.far_acc.p, P.near_acc.p, d_phi, d_grad, s);
   }
 }
 

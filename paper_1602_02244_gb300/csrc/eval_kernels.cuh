@@ -51,7 +51,7 @@ void launch_m2m_f32q(int p, int32_t b0, int32_t nbl, const int32_t *child, const
                      cudaStream_t s);
 void launch_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *parent, const BoxGeo *geo,
                      const float *opT, float *L, cudaStream_t s);
-void launch_combine(int64_t n, const int32_t *perm, const double *far, const double *near,
+void launch_combine(int64_t n, const int32_t *iperm, const double *far, const double *near,
                     double *phi, double *grad, cudaStream_t s);
 void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double *gq,
                        const double *gw, double *dx, cudaStream_t s);

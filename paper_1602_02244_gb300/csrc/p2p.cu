@@ -178,10 +178,7 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
       const int i = lane + 32 * t;
       if (i < tcount) {
         const int64_t g = fb + tc + i;
-        near[g] = tot[t][0];
-        near[n + g] = tot[t][1];
-        near[2 * n + g] = tot[t][2];
-        near[3 * n + g] = tot[t][3];
+        reinterpret_cast<double4 *>(near)[g] = make_double4(tot[t][0], tot[t][1], tot[t][2], tot[t][3]);
       }
     }
   }
@@ -370,10 +367,8 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtasF32)
       const int i = lane + 32 * t;
       if (i < tcount) {
         const int64_t g = fb + tc + i;
-        near[g] = tot[t * 4][lane];
-        near[n + g] = -tot[t * 4 + 1][lane];
-        near[2 * n + g] = -tot[t * 4 + 2][lane];
-        near[3 * n + g] = -tot[t * 4 + 3][lane];
+        reinterpret_cast<double4 *>(near)[g] = make_double4(
+            tot[t * 4][lane], -tot[t * 4 + 1][lane], -tot[t * 4 + 2][lane], -tot[t * 4 + 3][lane]);
       }
     }
   }

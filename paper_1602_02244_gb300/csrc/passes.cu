@@ -408,7 +408,7 @@ __global__ void k_l2p(int p_rt, const int32_t *__restrict__ leaves, const int32_
   const int32_t f = first[b], c = count[b];
   if (g.level < 2) {  // no far field reaches levels 0 and 1
     for (int32_t i = f + threadIdx.x; i < f + c; i += blockDim.x)
-      for (int a = 0; a < 4; ++a) far[a * n + i] = 0.0;
+      reinterpret_cast<double4 *>(far)[i] = make_double4(0.0, 0.0, 0.0, 0.0);
     return;
   }
   for (int k = threadIdx.x; k < nc; k += blockDim.x) Ls[k] = L[(int64_t)b * coef_pitch(p) + k];
@@ -436,10 +436,9 @@ __global__ void k_l2p(int p_rt, const int32_t *__restrict__ leaves, const int32_
       }
     });
     const double ia = 1.0 / a;
-    far[i] = (double)phi * ia;
-    far[n + i] = (double)gx * ia * ia;
-    far[2 * n + i] = (double)gy * ia * ia;
-    far[3 * n + i] = (double)gz * ia * ia;
+    reinterpret_cast<double4 *>(far)[i] =
+        make_double4((double)phi * ia, (double)gx * ia * ia, (double)gy * ia * ia,
+                     (double)gz * ia * ia);
   }
 }
 
@@ -597,10 +596,13 @@ __global__ void __launch_bounds__(kM2PThreads)
         a3 += red[3][o];
       }
       const int64_t i = f + tc + tid;
-      far[i] += a0;
-      far[n + i] += a1;
-      far[2 * n + i] += a2;
-      far[3 * n + i] += a3;
+      double4 *fi = reinterpret_cast<double4 *>(far) + i;
+      double4 v = *fi;
+      v.x += a0;
+      v.y += a1;
+      v.z += a2;
+      v.w += a3;
+      *fi = v;
     }
     __syncthreads();  // red is rewritten by the next chunk
   }
@@ -731,10 +733,13 @@ __global__ void __launch_bounds__(kM2PThreads)
             a3 += red[3][h][o];
           }
           const int64_t i = f + tc + u;
-          far[i] += a0;
-          far[n + i] += a1;
-          far[2 * n + i] += a2;
-          far[3 * n + i] += a3;
+          double4 *fi = reinterpret_cast<double4 *>(far) + i;
+          double4 v = *fi;
+          v.x += a0;
+          v.y += a1;
+          v.z += a2;
+          v.w += a3;
+          *fi = v;
         }
       }
     }
@@ -743,17 +748,21 @@ __global__ void __launch_bounds__(kM2PThreads)
 }
 
 // final per-target reduction in FP64 and scatter to the caller's order
-__global__ void k_combine(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ far,
-                          const double *__restrict__ near, double *__restrict__ phi,
-                          double *__restrict__ grad) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t o = perm[i];
-  phi[o] = far[i] + near[i];
+// far + near per target, gathered into the caller's order: thread o reads the
+// two 32-byte records of its sorted position and writes phi[o], grad[o][:]
+// with consecutive threads on consecutive addresses
+__global__ void k_combine(int64_t n, const int32_t *__restrict__ iperm,
+                          const double4 *__restrict__ far, const double4 *__restrict__ near,
+                          double *__restrict__ phi, double *__restrict__ grad) {
+  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  const int64_t i = iperm[o];
+  const double4 f = far[i], g = near[i];
+  phi[o] = f.x + g.x;
   if (grad) {
-    grad[3 * o] = far[n + i] + near[n + i];
-    grad[3 * o + 1] = far[2 * n + i] + near[2 * n + i];
-    grad[3 * o + 2] = far[3 * n + i] + near[3 * n + i];
+    grad[3 * o] = f.y + g.y;
+    grad[3 * o + 1] = f.z + g.z;
+    grad[3 * o + 2] = f.w + g.w;
   }
 }
 
@@ -938,10 +947,11 @@ void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, 
   FMM_LAUNCH_CHECK();
 }
 
-void launch_combine(int64_t n, const int32_t *perm, const double *far, const double *near,
+void launch_combine(int64_t n, const int32_t *iperm, const double *far, const double *near,
                     double *phi, double *grad, cudaStream_t s) {
   if (n == 0) return;
-  k_combine<<<ceil_div(n, 256), 256, 0, s>>>(n, perm, far, near, phi, grad);
+  k_combine<<<ceil_div(n, 256), 256, 0, s>>>(n, iperm, reinterpret_cast<const double4 *>(far),
+                                             reinterpret_cast<const double4 *>(near), phi, grad);
   FMM_LAUNCH_CHECK();
 }
 

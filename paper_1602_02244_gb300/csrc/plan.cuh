@@ -57,6 +57,7 @@ struct fmm_plan_impl {
   DBuf<double> partial;             // bbox partials
   DBuf<uint64_t> keys, keys_tmp;    // sorted Morton keys
   DBuf<int32_t> perm, perm_tmp;     // sorted position -> input index
+  DBuf<int32_t> iperm;              // input index -> sorted position
   DBuf<double> xyz_sorted;          // n x 3 (sorted order)
   DBuf<double4> pl64;               // per sorted point: position - leaf centre (w unused)
   DBuf<float4> pl32;                // FP32 copy of pl64

@@ -100,6 +100,7 @@ __global__ void k_bbox_final(const double *partial, int nb, double *geom) {
   for (int a = 0; a < 3; ++a) geom[a] = smin[a][0];
   geom[3] = D;
   geom[4] = sbad[0];
+  geom[5] = ldexp(1.0, kMaxDepth) / D;  // quantisation scale, a power of two
 }
 
 // one CTA per problem of a batch: root cube of its points (same rule as above)
@@ -139,6 +140,7 @@ __global__ void k_bbox_problems(const double *__restrict__ xyz, const int64_t *_
     g[0] = g[1] = g[2] = 0.0;
     g[3] = 1.0;
     g[4] = 0.0;
+    g[5] = ldexp(1.0, kMaxDepth);
     return;
   }
   double ext = 0.0;
@@ -152,6 +154,7 @@ __global__ void k_bbox_problems(const double *__restrict__ xyz, const int64_t *_
   for (int a = 0; a < 3; ++a) g[a] = smin[a][0];
   g[3] = D;
   g[4] = sbad[0];
+  g[5] = ldexp(1.0, kMaxDepth) / D;  // quantisation scale, a power of two
 }
 
 __device__ __forceinline__ int problem_of(int64_t i, const int64_t *__restrict__ off, int nprob) {
@@ -172,8 +175,7 @@ __global__ void k_morton(const double *__restrict__ xyz, int64_t n, const double
   int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
   if (i >= n) return;
   const double *g = geom + (off ? 8 * problem_of(i, off, nprob) : 0);
-  const double D = g[3];
-  const double s = ldexp(1.0, kMaxDepth) / D;  // power of two: the product below is exact
+  const double s = g[5];  // 2^21 / D, a power of two: the product below is exact
   const double top = (double)((1u << kMaxDepth) - 1u);
   uint32_t q[3];
   for (int a = 0; a < 3; ++a) {
@@ -203,14 +205,17 @@ __global__ void k_apply_perm(int64_t n, const int32_t *__restrict__ sigma,
   pout[i] = pin[sigma[i]];
 }
 
+// sorted coordinates, and the inverse permutation (input index -> sorted
+// position) that the final reduction gathers through
 __global__ void k_gather_xyz(const double *__restrict__ xyz, const int32_t *__restrict__ perm,
-                             int64_t n, double *__restrict__ out) {
+                             int64_t n, double *__restrict__ out, int32_t *__restrict__ iperm) {
   int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
   if (i >= n) return;
   int64_t j = perm[i];
   out[3 * i] = xyz[3 * j];
   out[3 * i + 1] = xyz[3 * j + 1];
   out[3 * i + 2] = xyz[3 * j + 2];
+  iperm[j] = (int32_t)i;
 }
 
 // --------------------------------------------------------------- octree
@@ -332,19 +337,26 @@ __global__ void k_compact(int64_t n, const int32_t *__restrict__ flag, const int
   if (flag[i]) out[pos[i]] = (int32_t)i;
 }
 
-__global__ void k_leaf_points(const int32_t *__restrict__ leaves, const BoxGeo *__restrict__ geo,
-                              const int32_t *__restrict__ first, const int32_t *__restrict__ count,
-                              const double *__restrict__ xyz, const int32_t *__restrict__ bprob,
-                              const double *__restrict__ pgeom, const double *__restrict__ side,
-                              double4 *__restrict__ pl64, float4 *__restrict__ pl32) {
-  int32_t b = leaves[blockIdx.x];
+// one warp per leaf (8 leaves per CTA): leaf-local coordinates x - c_leaf in
+// FP64 and FP32
+constexpr int kLeafWarps = 8;
+__global__ void k_leaf_points(int64_t nleaves, const int32_t *__restrict__ leaves,
+                              const BoxGeo *__restrict__ geo, const int32_t *__restrict__ first,
+                              const int32_t *__restrict__ count, const double *__restrict__ xyz,
+                              const int32_t *__restrict__ bprob, const double *__restrict__ pgeom,
+                              const double *__restrict__ side, double4 *__restrict__ pl64,
+                              float4 *__restrict__ pl32) {
+  const int64_t w = (int64_t)blockIdx.x * kLeafWarps + (threadIdx.x >> 5);
+  if (w >= nleaves) return;
+  const int lane = threadIdx.x & 31;
+  int32_t b = leaves[w];
   BoxGeo g = geo[b];
   const double *lo = pgeom + 8 * bprob[b];
   double a = side[b];
   double cx = lo[0] + ((double)g.ix + 0.5) * a, cy = lo[1] + ((double)g.iy + 0.5) * a,
          cz = lo[2] + ((double)g.iz + 0.5) * a;
   int32_t f = first[b], c = count[b];
-  for (int32_t i = f + threadIdx.x; i < f + c; i += blockDim.x) {
+  for (int32_t i = f + lane; i < f + c; i += 32) {
     double x = xyz[3 * (int64_t)i] - cx, y = xyz[3 * (int64_t)i + 1] - cy,
            z = xyz[3 * (int64_t)i + 2] - cz;
     pl64[i] = make_double4(x, y, z, 0.0);
@@ -619,11 +631,13 @@ void set_points(fmm_plan_impl &P, const double *d_xyz) {
   cudaStream_t s = P.stream;
   int64_t n = P.n;
   if (n == 0) return;
-  k_gather_xyz<<<grid(n), kT, 0, s>>>(d_xyz, P.perm.p, n, P.xyz_sorted.p);
+  P.iperm.resize(n, s);
+  k_gather_xyz<<<grid(n), kT, 0, s>>>(d_xyz, P.perm.p, n, P.xyz_sorted.p, P.iperm.p);
   FMM_LAUNCH_CHECK();
-  k_leaf_points<<<(int)P.nleaves, 128, 0, s>>>(P.leaves.p, P.box_geo.p, P.box_first.p,
-                                                P.box_count.p, P.xyz_sorted.p, P.box_prob.p,
-                                                P.prob_geom.p, P.box_side.p, P.pl64.p, P.pl32.p);
+  if (P.nleaves > 0)
+    k_leaf_points<<<(unsigned)ceil_div(P.nleaves, (int64_t)kLeafWarps), 32 * kLeafWarps, 0, s>>>(
+        P.nleaves, P.leaves.p, P.box_geo.p, P.box_first.p, P.box_count.p, P.xyz_sorted.p,
+        P.box_prob.p, P.prob_geom.p, P.box_side.p, P.pl64.p, P.pl32.p);
   FMM_LAUNCH_CHECK();
 }
 
@@ -691,7 +705,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
     std::swap(P.perm, P.perm_tmp);
   }
   P.xyz_sorted.resize(3 * n, s);
-  k_gather_xyz<<<grid(n), kT, 0, s>>>(d_xyz, P.perm.p, n, P.xyz_sorted.p);
+  P.iperm.resize(n, s);
+  k_gather_xyz<<<grid(n), kT, 0, s>>>(d_xyz, P.perm.p, n, P.xyz_sorted.p, P.iperm.p);
   FMM_LAUNCH_CHECK();
 
   // ---- boxes, level by level; level 0 holds one root per non-empty problem
@@ -768,9 +783,9 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   P.nleaves = compact(P, nb, P.s_i32a.p, P.leaves);
   P.pl64.resize(n, s);
   P.pl32.resize(n, s);
-  k_leaf_points<<<(int)P.nleaves, 128, 0, s>>>(P.leaves.p, P.box_geo.p, P.box_first.p,
-                                                P.box_count.p, P.xyz_sorted.p, P.box_prob.p,
-                                                P.prob_geom.p, P.box_side.p, P.pl64.p, P.pl32.p);
+  k_leaf_points<<<(unsigned)ceil_div(P.nleaves, (int64_t)kLeafWarps), 32 * kLeafWarps, 0, s>>>(
+      P.nleaves, P.leaves.p, P.box_geo.p, P.box_first.p, P.box_count.p, P.xyz_sorted.p,
+      P.box_prob.p, P.prob_geom.p, P.box_side.p, P.pl64.p, P.pl32.p);
   FMM_LAUNCH_CHECK();
 
   // ---- colleagues

@@ -33,11 +33,14 @@ int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) return it->second;
   }
-  static const int ladder[] = {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+  // finer steps where the optimum usually sits (64..256 for p = 6..10)
+  static const int ladder[] = {16,  24,  32,  48,  64,  80,  96,  112, 128,
+                               144, 160, 176, 192, 224, 256, 320, 384, 512};
   cudaStream_t s = P.stream;
-  DBuf<double> q, phi;
+  DBuf<double> q, phi, grad;
   q.resize(n, s);
   phi.resize(n, s);
+  grad.resize((size_t)3 * n, s);
   k_fill<<<ceil_div(n, 256), 256, 0, s>>>(n, 1.0 / (double)n, q.p);
   FMM_LAUNCH_CHECK();
   cudaEvent_t a, b;
@@ -56,7 +59,7 @@ int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
       for (int rep = 0; rep < 2; ++rep) {
         FMM_CUDA(cudaEventRecord(a, s));
         build_tree(P, d_xyz, n);
-        eval_fmm(P, q.p, phi.p, nullptr);
+        eval_fmm(P, q.p, phi.p, grad.p);  // the same work as a mat-vec with gradients
         FMM_CUDA(cudaEventRecord(b, s));
         FMM_CUDA(cudaEventSynchronize(b));
         float t = 0.f;
@@ -74,6 +77,7 @@ int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
     cudaEventDestroy(b);
     q.release();
     phi.release();
+    grad.release();
     throw;
   }
   P.prof_on = prof;
@@ -81,6 +85,7 @@ int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   cudaEventDestroy(b);
   q.release();
   phi.release();
+  grad.release();
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = best;
   return best;
