@@ -42,15 +42,20 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel, taken from one ncu capture of the same kernel and workload
-# (profiles/p2p_packed_plummer4m_p8_leaf192.md); keyed by
+# at the leaf sizes the autotuner chooses between
+# (profiles/p2p_traffic_plummer4m_p8.md); keyed by
 # (pass, N, order, leaf size, precision).  Any other configuration reports null.
-TRAFFIC_BYTES = {("P2P", 4194304, 8, 192, "mixed"): 173.2e6}
+TRAFFIC_BYTES = {("P2P", 4194304, 8, 128, "mixed"): 180.0e6,
+                 ("P2P", 4194304, 8, 144, "mixed"): 176.4e6,
+                 ("P2P", 4194304, 8, 160, "mixed"): 175.8e6,
+                 ("P2P", 4194304, 8, 176, "mixed"): 172.1e6,
+                 ("P2P", 4194304, 8, 192, "mixed"): 170.2e6}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4194304)
@@ -95,7 +100,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None

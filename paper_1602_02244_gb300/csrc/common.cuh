@@ -124,6 +124,19 @@ __host__ __device__ constexpr int coef_pitch(int p) {
 }
 
 // Box geometry record: integer anchor at its level and the level.
+// four doubles on a 32-byte boundary (one point or one per-target record)
+struct __align__(32) Dbl4 {
+  double x, y, z, w;
+};
+__host__ __device__ __forceinline__ Dbl4 make_dbl4(double x, double y, double z, double w) {
+  Dbl4 v;
+  v.x = x;
+  v.y = y;
+  v.z = z;
+  v.w = w;
+  return v;
+}
+
 struct __align__(16) BoxGeo {
   int32_t ix, iy, iz, level;
 };

@@ -8,7 +8,7 @@ template <typename T>
 struct V4;
 template <>
 struct V4<double> {
-  using type = double4;
+  using type = Dbl4;
 };
 template <>
 struct V4<float> {

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtas)
       const int i = lane + 32 * t;
       if (i < tcount) {
         const int64_t g = fb + tc + i;
-        reinterpret_cast<double4 *>(near)[g] = make_double4(tot[t][0], tot[t][1], tot[t][2], tot[t][3]);
+        reinterpret_cast<Dbl4 *>(near)[g] = make_dbl4(tot[t][0], tot[t][1], tot[t][2], tot[t][3]);
       }
     }
   }
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtasF32)
       const int i = lane + 32 * t;
       if (i < tcount) {
         const int64_t g = fb + tc + i;
-        reinterpret_cast<double4 *>(near)[g] = make_double4(
+        reinterpret_cast<Dbl4 *>(near)[g] = make_dbl4(
             tot[t * 4][lane], -tot[t * 4 + 1][lane], -tot[t * 4 + 2][lane], -tot[t * 4 + 3][lane]);
       }
     }
@@ -398,7 +398,7 @@ template void launch_p2p<float>(int64_t, const int32_t *, const int32_t *, const
                                 const int32_t *, const int32_t *, const BoxGeo *, const float4 *,
                                 const double *, int64_t, double *, cudaStream_t);
 template void launch_p2p<double>(int64_t, const int32_t *, const int32_t *, const int32_t *,
-                                 const int32_t *, const int32_t *, const BoxGeo *, const double4 *,
+                                 const int32_t *, const int32_t *, const BoxGeo *, const Dbl4 *,
                                  const double *, int64_t, double *, cudaStream_t);
 
 }  // namespace fmm

@@ -107,42 +107,42 @@ __global__ void k_p2m(int p_rt, int64_t nleaves, const int32_t *__restrict__ lea
     }
     transpose_sums<false, T, NC>(racc, lane, buf, M + (int64_t)b * ld, ld,
                                  (M64 && g.level <= coarse) ? M64 + (int64_t)b * ld : nullptr);
-    return;
-  }
-  T acc[kAccSlots];
+  } else {  // run-time order: per-point columns summed in shared memory
+    T acc[kAccSlots];
 #pragma unroll
-  for (int t = 0; t < kAccSlots; ++t) acc[t] = T(0);
-  const int32_t f = first[b], c = count[b];
-  for (int32_t j0 = 0; j0 < c; j0 += 32) {
-    const int32_t j = j0 + lane;
-    if (j < c) {
-      const typename V4<T>::type s = src[f + j];
-      const T q = s.w;
-      regular_stream<T>(p, s.x * inva, s.y * inva, s.z * inva, [&](int n, int m, T re, T im) {
-        buf[cidx(n, m) * pitch + lane] = q * re;
-        if (m > 0) buf[cidx(n, -m) * pitch + lane] = -q * im;
-      });
-    } else {
-      for (int k = 0; k < nc; ++k) buf[k * pitch + lane] = T(0);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < kAccSlots; ++t) {
-      const int k = lane + 32 * t;
-      if (k < nc) {
-        T s = T(0);
-        for (int jj = 0; jj < 32; ++jj) s += buf[k * pitch + jj];
-        acc[t] += s;
+    for (int t = 0; t < kAccSlots; ++t) acc[t] = T(0);
+    const int32_t f = first[b], c = count[b];
+    for (int32_t j0 = 0; j0 < c; j0 += 32) {
+      const int32_t j = j0 + lane;
+      if (j < c) {
+        const typename V4<T>::type s = src[f + j];
+        const T q = s.w;
+        regular_stream<T>(p, s.x * inva, s.y * inva, s.z * inva, [&](int n, int m, T re, T im) {
+          buf[cidx(n, m) * pitch + lane] = q * re;
+          if (m > 0) buf[cidx(n, -m) * pitch + lane] = -q * im;
+        });
+      } else {
+        for (int k = 0; k < nc; ++k) buf[k * pitch + lane] = T(0);
       }
-    }
-    __syncwarp();
-  }
+      __syncwarp();
 #pragma unroll
-  for (int t = 0; t < kAccSlots; ++t) {  // the row padding is written as zero
-    const int k = lane + 32 * t;
-    if (k < ld) {
-      M[(int64_t)b * ld + k] = acc[t];
-      if (M64 && g.level <= coarse) M64[(int64_t)b * ld + k] = (double)acc[t];
+      for (int t = 0; t < kAccSlots; ++t) {
+        const int k = lane + 32 * t;
+        if (k < nc) {
+          T s = T(0);
+          for (int jj = 0; jj < 32; ++jj) s += buf[k * pitch + jj];
+          acc[t] += s;
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int t = 0; t < kAccSlots; ++t) {  // the row padding is written as zero
+      const int k = lane + 32 * t;
+      if (k < ld) {
+        M[(int64_t)b * ld + k] = acc[t];
+        if (M64 && g.level <= coarse) M64[(int64_t)b * ld + k] = (double)acc[t];
+      }
     }
   }
 }
@@ -217,48 +217,48 @@ __global__ void k_p2l(int p_rt, int64_t nboxes_x, const int32_t *__restrict__ xb
       }
     }
     transpose_sums<true, T, NC>(racc, lane, buf, L + (int64_t)C * ld, ld, nullptr);
-    return;
-  }
-  T acc[kAccSlots];
+  } else {  // run-time order: per-point columns summed in shared memory
+    T acc[kAccSlots];
 #pragma unroll
-  for (int t = 0; t < kAccSlots; ++t) acc[t] = T(0);
-  for (int32_t e = xoff[C]; e < xoff[C + 1]; ++e) {
-    const int32_t A = xidx[e];
-    const BoxGeo ga = geo[A];
-    const T sx = (T)center_delta(ga.ix, side[A], gc.ix, ac);
-    const T sy = (T)center_delta(ga.iy, side[A], gc.iy, ac);
-    const T sz = (T)center_delta(ga.iz, side[A], gc.iz, ac);
-    const int32_t f = first[A], c = count[A];
-    for (int32_t j0 = 0; j0 < c; j0 += 32) {
-      const int32_t j = j0 + lane;
-      if (j < c) {
-        const typename V4<T>::type s = src[f + j];
-        const T q = s.w;
-        irregular_stream<T>(p, (s.x + sx) * inva, (s.y + sy) * inva, (s.z + sz) * inva,
-                            [&](int n, int m, T re, T im) {
-                              buf[cidx(n, m) * pitch + lane] = q * re;
-                              if (m > 0) buf[cidx(n, -m) * pitch + lane] = -q * im;
-                            });
-      } else {
-        for (int k = 0; k < nc; ++k) buf[k * pitch + lane] = T(0);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int t = 0; t < kAccSlots; ++t) {
-        const int k = lane + 32 * t;
-        if (k < nc) {
-          T s = T(0);
-          for (int jj = 0; jj < 32; ++jj) s += buf[k * pitch + jj];
-          acc[t] += s;
+    for (int t = 0; t < kAccSlots; ++t) acc[t] = T(0);
+    for (int32_t e = xoff[C]; e < xoff[C + 1]; ++e) {
+      const int32_t A = xidx[e];
+      const BoxGeo ga = geo[A];
+      const T sx = (T)center_delta(ga.ix, side[A], gc.ix, ac);
+      const T sy = (T)center_delta(ga.iy, side[A], gc.iy, ac);
+      const T sz = (T)center_delta(ga.iz, side[A], gc.iz, ac);
+      const int32_t f = first[A], c = count[A];
+      for (int32_t j0 = 0; j0 < c; j0 += 32) {
+        const int32_t j = j0 + lane;
+        if (j < c) {
+          const typename V4<T>::type s = src[f + j];
+          const T q = s.w;
+          irregular_stream<T>(p, (s.x + sx) * inva, (s.y + sy) * inva, (s.z + sz) * inva,
+                              [&](int n, int m, T re, T im) {
+                                buf[cidx(n, m) * pitch + lane] = q * re;
+                                if (m > 0) buf[cidx(n, -m) * pitch + lane] = -q * im;
+                              });
+        } else {
+          for (int k = 0; k < nc; ++k) buf[k * pitch + lane] = T(0);
         }
-      }
-      __syncwarp();
-    }
-  }
+        __syncwarp();
 #pragma unroll
-  for (int t = 0; t < kAccSlots; ++t) {
-    const int k = lane + 32 * t;
-    if (k < nc) L[(int64_t)C * ld + k] += acc[t];
+        for (int t = 0; t < kAccSlots; ++t) {
+          const int k = lane + 32 * t;
+          if (k < nc) {
+            T s = T(0);
+            for (int jj = 0; jj < 32; ++jj) s += buf[k * pitch + jj];
+            acc[t] += s;
+          }
+        }
+        __syncwarp();
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kAccSlots; ++t) {
+      const int k = lane + 32 * t;
+      if (k < nc) L[(int64_t)C * ld + k] += acc[t];
+    }
   }
 }
 
@@ -408,7 +408,7 @@ __global__ void k_l2p(int p_rt, const int32_t *__restrict__ leaves, const int32_
   const int32_t f = first[b], c = count[b];
   if (g.level < 2) {  // no far field reaches levels 0 and 1
     for (int32_t i = f + threadIdx.x; i < f + c; i += blockDim.x)
-      reinterpret_cast<double4 *>(far)[i] = make_double4(0.0, 0.0, 0.0, 0.0);
+      reinterpret_cast<Dbl4 *>(far)[i] = make_dbl4(0.0, 0.0, 0.0, 0.0);
     return;
   }
   for (int k = threadIdx.x; k < nc; k += blockDim.x) Ls[k] = L[(int64_t)b * coef_pitch(p) + k];
@@ -436,8 +436,8 @@ __global__ void k_l2p(int p_rt, const int32_t *__restrict__ leaves, const int32_
       }
     });
     const double ia = 1.0 / a;
-    reinterpret_cast<double4 *>(far)[i] =
-        make_double4((double)phi * ia, (double)gx * ia * ia, (double)gy * ia * ia,
+    reinterpret_cast<Dbl4 *>(far)[i] =
+        make_dbl4((double)phi * ia, (double)gx * ia * ia, (double)gy * ia * ia,
                      (double)gz * ia * ia);
   }
 }
@@ -596,8 +596,8 @@ __global__ void __launch_bounds__(kM2PThreads)
         a3 += red[3][o];
       }
       const int64_t i = f + tc + tid;
-      double4 *fi = reinterpret_cast<double4 *>(far) + i;
-      double4 v = *fi;
+      Dbl4 *fi = reinterpret_cast<Dbl4 *>(far) + i;
+      Dbl4 v = *fi;
       v.x += a0;
       v.y += a1;
       v.z += a2;
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kM2PThreads)
                 const float4 *__restrict__ src, const double *__restrict__ side,
                 const float4 *__restrict__ K, int64_t n, double *__restrict__ far) {
   const int p = PT > 0 ? PT : p_rt;
-  extern __shared__ __align__(16) unsigned char m2p_smem[];
+  extern __shared__ __align__(32) unsigned char m2p_smem[];
   float4 *ks = reinterpret_cast<float4 *>(m2p_smem);  // [nstage][ld1]
   __shared__ float s_off[kM2PStage][3], s_inva[kM2PStage];
   __shared__ double s_ia[kM2PStage];
@@ -733,8 +733,8 @@ __global__ void __launch_bounds__(kM2PThreads)
             a3 += red[3][h][o];
           }
           const int64_t i = f + tc + u;
-          double4 *fi = reinterpret_cast<double4 *>(far) + i;
-          double4 v = *fi;
+          Dbl4 *fi = reinterpret_cast<Dbl4 *>(far) + i;
+          Dbl4 v = *fi;
           v.x += a0;
           v.y += a1;
           v.z += a2;
@@ -752,12 +752,12 @@ __global__ void __launch_bounds__(kM2PThreads)
 // two 32-byte records of its sorted position and writes phi[o], grad[o][:]
 // with consecutive threads on consecutive addresses
 __global__ void k_combine(int64_t n, const int32_t *__restrict__ iperm,
-                          const double4 *__restrict__ far, const double4 *__restrict__ near,
+                          const Dbl4 *__restrict__ far, const Dbl4 *__restrict__ near,
                           double *__restrict__ phi, double *__restrict__ grad) {
   int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n) return;
   const int64_t i = iperm[o];
-  const double4 f = far[i], g = near[i];
+  const Dbl4 f = far[i], g = near[i];
   phi[o] = f.x + g.x;
   if (grad) {
     grad[3 * o] = f.y + g.y;
@@ -950,8 +950,8 @@ void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, 
 void launch_combine(int64_t n, const int32_t *iperm, const double *far, const double *near,
                     double *phi, double *grad, cudaStream_t s) {
   if (n == 0) return;
-  k_combine<<<ceil_div(n, 256), 256, 0, s>>>(n, iperm, reinterpret_cast<const double4 *>(far),
-                                             reinterpret_cast<const double4 *>(near), phi, grad);
+  k_combine<<<ceil_div(n, 256), 256, 0, s>>>(n, iperm, reinterpret_cast<const Dbl4 *>(far),
+                                             reinterpret_cast<const Dbl4 *>(near), phi, grad);
   FMM_LAUNCH_CHECK();
 }
 

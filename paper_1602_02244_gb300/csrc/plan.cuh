@@ -59,7 +59,7 @@ struct fmm_plan_impl {
   DBuf<int32_t> perm, perm_tmp;     // sorted position -> input index
   DBuf<int32_t> iperm;              // input index -> sorted position
   DBuf<double> xyz_sorted;          // n x 3 (sorted order)
-  DBuf<double4> pl64;               // per sorted point: position - leaf centre (w unused)
+  DBuf<Dbl4> pl64;               // per sorted point: position - leaf centre (w unused)
   DBuf<float4> pl32;                // FP32 copy of pl64
 
   // boxes, numbered by (level, key)
@@ -100,7 +100,7 @@ struct fmm_plan_impl {
   Operators ops;
 
   // evaluation workspace
-  DBuf<double4> src64;              // per sorted point: (local x, y, z, q)
+  DBuf<Dbl4> src64;              // per sorted point: (local x, y, z, q)
   DBuf<float4> src32;
   DBuf<double> M64, L64;            // nboxes x NC
   DBuf<float> M32, L32;

@@ -344,7 +344,7 @@ __global__ void k_leaf_points(int64_t nleaves, const int32_t *__restrict__ leave
                               const BoxGeo *__restrict__ geo, const int32_t *__restrict__ first,
                               const int32_t *__restrict__ count, const double *__restrict__ xyz,
                               const int32_t *__restrict__ bprob, const double *__restrict__ pgeom,
-                              const double *__restrict__ side, double4 *__restrict__ pl64,
+                              const double *__restrict__ side, Dbl4 *__restrict__ pl64,
                               float4 *__restrict__ pl32) {
   const int64_t w = (int64_t)blockIdx.x * kLeafWarps + (threadIdx.x >> 5);
   if (w >= nleaves) return;
@@ -359,7 +359,7 @@ __global__ void k_leaf_points(int64_t nleaves, const int32_t *__restrict__ leave
   for (int32_t i = f + lane; i < f + c; i += 32) {
     double x = xyz[3 * (int64_t)i] - cx, y = xyz[3 * (int64_t)i + 1] - cy,
            z = xyz[3 * (int64_t)i + 2] - cz;
-    pl64[i] = make_double4(x, y, z, 0.0);
+    pl64[i] = make_dbl4(x, y, z, 0.0);
     pl32[i] = make_float4((float)x, (float)y, (float)z, 0.f);
   }
 }
