@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-problem leg")
+    ap.add_argument("--precond", action="store_true",
+                    help="add the FMM-preconditioned CG solve of the 7-point Laplace problem")
     ap.add_argument("--lattice", action="store_true",
                     help="add plan/eval time and peak device memory vs N on uniform lattices")
     return ap.parse_args()
@@ -315,6 +317,44 @@ def lattice_leg(dev, order=8):
     return rows
 
 
+def precond_leg(dev, h=2.0 ** -5, tol=1e-8):
+    """The paper's preconditioning experiment (§4.2), Laplace part: -Laplace u = 1
+    on [-1, 1]^3, u = 0 on the boundary, 7-point stencil at spacing h; CG
+    iterations and solve time without a preconditioner and with the FMM
+    (free-space Green's function, mixed precision) at low orders."""
+    import torch
+    from paper_1602_02244_gb300 import binding, precond
+    m = int(round(2.0 / h)) - 1
+    b = torch.ones(m ** 3, dtype=torch.float64, device=dev)
+    A = lambda v: binding.laplace7(v, h)
+    rows = []
+    for order in (None, 2, 3, 4):
+        pre = precond.GreenPreconditioner(h, order=order, leaf_size=64, device=dev) if order else None
+        if pre is not None:
+            pre(b)  # operators and workspace
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, it, hist = precond.fpcg(A, b, pre, tol=tol, maxiter=2000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        row = {"preconditioner": "FMM p=%d" % order if order else "none", "iterations": it,
+               "rel_residual": hist[-1], "solve_ms": 1e3 * dt}
+        if pre is not None:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                pre(b)
+            e1.record()
+            e1.synchronize()
+            row["apply_ms"] = e0.elapsed_time(e1) / 5
+            pre.close()
+        rows.append(row)
+    return {"problem": "-Laplace u = 1 on [-1,1]^3, u = 0 on the boundary, 7-point stencil, "
+                       "h = 2^-5 (%d unknowns), CG to relative residual %.0e" % (m ** 3, tol),
+            "runs": rows}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -549,6 +589,8 @@ def run_ours(args):
         line["batched"] = batched_leg(dev, args.steps, args.warmup)
     if args.lattice:
         line["lattice"] = lattice_leg(dev)
+    if args.precond:
+        line["precond"] = precond_leg(dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample, p, S)

@@ -211,6 +211,16 @@ fmm_status fmm_memory_usage(uint64_t *current, uint64_t *peak, int reset_peak);
 fmm_status fmm_direct(const double *d_src, const double *d_q, int64_t n, const double *d_tgt,
                       int64_t m, double *d_phi, double *d_grad, void *stream);
 
+/* The 7-point discrete Laplacian with zero Dirichlet boundary values on an
+ * m x m x m interior grid of spacing h (the PDE operator of the paper's
+ * preconditioning experiment, §4.2):
+ *   out_ijk = (6 u_ijk - sum of the 6 neighbours) / h^2, neighbours outside
+ *   the grid taken as 0; index (k m + j) m + i.
+ * d_u, d_out: device, m^3 FP64, not overlapping.  Stream-ordered, asynchronous.
+ * FMM_ERR_INVALID_ARG for m < 0, h <= 0, m^3 beyond int64 range or NULL
+ * pointers with m > 0. */
+fmm_status fmm_laplace7_apply(const double *d_u, double *d_out, int64_t m, double h, void *stream);
+
 /* Number of kernels this library has launched in this process so far. */
 uint64_t fmm_kernel_launches(void);
 

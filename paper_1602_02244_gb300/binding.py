@@ -20,8 +20,8 @@ _STATUS = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_CUDA", 3: "FMM_ERR
 
 EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_plan_set_points",
            "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_sync", "fmm_plan_sizes",
-           "fmm_plan_export", "fmm_plan_destroy", "fmm_direct", "fmm_status_string",
-           "fmm_last_error_message")
+           "fmm_plan_export", "fmm_plan_destroy", "fmm_direct", "fmm_laplace7_apply",
+           "fmm_status_string", "fmm_last_error_message")
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
                  "box_parent", "box_child", "box_nchild", "u_off", "u_idx", "v_off", "v_idx",
@@ -69,6 +69,7 @@ def library():
         L.fmm_plan_export.argtypes = [_vp, _int, _vp, ctypes.c_size_t]
         L.fmm_plan_destroy.argtypes = [_vp]
         L.fmm_direct.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _vp]
+        L.fmm_laplace7_apply.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp]
         L.fmm_status_string.argtypes = [_int]
         L.fmm_status_string.restype = ctypes.c_char_p
         L.fmm_last_error_message.restype = ctypes.c_char_p
@@ -298,3 +299,19 @@ def direct(points, q, targets, grad=True, stream=None):
         _check(library().fmm_direct(_ptr(pts), _ptr(qq), n, _ptr(tgt), m, _ptr(phi), _ptr(g),
                                     _stream(stream)))
     return phi, g
+
+
+def laplace7(u, h, out=None, stream=None):
+    """The 7-point Laplacian with zero Dirichlet boundary values applied to the
+    interior grid function ``u`` (CUDA float64, shape (m, m, m) indexed [k, j, i]
+    or flat m^3) with spacing ``h`` (``fmm_laplace7_apply``)."""
+    if not isinstance(u, torch.Tensor) or not u.is_cuda or u.dtype != torch.float64:
+        raise TypeError("u must be a CUDA float64 tensor")
+    m = round(u.numel() ** (1.0 / 3.0))
+    if m ** 3 != u.numel():
+        raise ValueError("u must hold m^3 values")
+    u = u.contiguous()
+    out = torch.empty_like(u) if out is None else out
+    with torch.cuda.device(u.device):
+        _check(library().fmm_laplace7_apply(_ptr(u), _ptr(out), m, float(h), _stream(stream)))
+    return out
