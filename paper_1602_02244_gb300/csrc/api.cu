@@ -115,7 +115,8 @@ void release_plan(fmm_plan_impl &P) {
   P.ops.l2l32.release(); P.src64.release(); P.src32.release(); P.M64.release(); P.L64.release();
   P.M32.release(); P.L32.release(); P.far_acc.release(); P.near_acc.release();
   P.adj_grad_w.release(); P.adj_grad_q.release(); P.adj_phi.release(); P.host_io.release();
-  P.s_i32a.release(); P.s_i32b.release(); P.s_i32c.release(); P.s_hist.release();
+  P.s_i32a.release(); P.s_i32b.release(); P.s_i32c.release(); P.s_i32d.release();
+  P.s_hist.release();
   P.s_scan.release(); P.s_u64a.release(); P.s_u64b.release(); P.s_total.release();
   P.ca_off.release(); P.ca_idx.release(); P.m2l_src.release(); P.m2l_slots.release();
   P.m2l_nslots.release(); P.ops.m2l32p.release(); P.ops.m2l_tc.release(); P.Mhi.release();

@@ -137,7 +137,7 @@ struct fmm_plan_impl {
   const void *graph_key[8] = {};
 
   // scratch
-  DBuf<int32_t> s_i32a, s_i32b, s_i32c, s_hist, s_scan;
+  DBuf<int32_t> s_i32a, s_i32b, s_i32c, s_i32d, s_hist, s_scan;
   DBuf<uint64_t> s_u64a, s_u64b;
   DBuf<int32_t> s_total;            // device scalars for scan totals
   DBuf<int32_t> ca_off, ca_idx;     // coarser-or-equal adjacent leaves per box

@@ -482,30 +482,6 @@ __global__ void k_calist(int64_t nb, const BoxGeo *__restrict__ geo, const int32
 
 // U pairs of leaf B: (B,B), (B,A) for A in CA(B), and (A,B) for the coarser
 // A in CA(B) (finer adjacent leaves find B in their own CA lists).
-template <bool kFill>
-__global__ void k_upairs(int64_t nleaves, const int32_t *__restrict__ leaves,
-                         const BoxGeo *__restrict__ geo, const int32_t *__restrict__ caoff,
-                         const int32_t *__restrict__ caidx, int32_t *__restrict__ cnt,
-                         const int32_t *__restrict__ off, uint64_t *__restrict__ pairs) {
-  int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
-  if (t >= nleaves) return;
-  int32_t B = leaves[t];
-  int lb = geo[B].level;
-  int32_t k = 0;
-  int64_t o = kFill ? off[t] : 0;
-  if (kFill) pairs[o] = ((uint64_t)B << 32) | (uint32_t)B;
-  ++k;
-  for (int32_t e = caoff[B]; e < caoff[B + 1]; ++e) {
-    int32_t A = caidx[e];
-    if (kFill) pairs[o + k] = ((uint64_t)B << 32) | (uint32_t)A;
-    ++k;
-    if (geo[A].level < lb) {
-      if (kFill) pairs[o + k] = ((uint64_t)A << 32) | (uint32_t)B;
-      ++k;
-    }
-  }
-  if (!kFill) cnt[t] = k;
-}
 
 // X(C) = { A in CA(parent(C)) : A not adjacent to C }
 template <bool kFill>
@@ -532,24 +508,112 @@ __global__ void k_xlist(int64_t nb, const BoxGeo *__restrict__ geo, const int32_
 }
 
 // W pairs from X: (A, C) for every A in X(C)
-__global__ void k_wpairs(int64_t nb, const int32_t *__restrict__ xoff, const int32_t *__restrict__ xidx,
-                         uint64_t *__restrict__ pairs) {
-  int64_t C = (int64_t)blockIdx.x * kT + threadIdx.x;
-  if (C >= nb) return;
-  for (int32_t e = xoff[C]; e < xoff[C + 1]; ++e)
-    pairs[e] = ((uint64_t)(uint32_t)xidx[e] << 32) | (uint32_t)C;
+// Sort a short run of box numbers in place (Shell sort with Ciura's gaps;
+// plain insertion for runs up to 32).
+__device__ void sort_run(int32_t *a, int n) {
+  const int gaps[] = {301, 132, 57, 23, 10, 4, 1};
+  for (int gi = 0; gi < 7; ++gi) {
+    const int gap = gaps[gi];
+    if (gap >= n) continue;
+    for (int i = gap; i < n; ++i) {
+      const int32_t v = a[i];
+      int j = i;
+      while (j >= gap && a[j - gap] > v) {
+        a[j] = a[j - gap];
+        j -= gap;
+      }
+      a[j] = v;
+    }
+  }
 }
 
-// CSR rows from (row << 32 | col) keys sorted ascending
-__global__ void k_pairs_csr(int64_t np, int64_t nb, const uint64_t *__restrict__ keys,
-                            int32_t *__restrict__ off, int32_t *__restrict__ idx) {
-  int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
-  if (i > np) return;
-  int64_t prev = i > 0 ? (int64_t)(keys[i - 1] >> 32) : -1;
-  int64_t cur = i < np ? (int64_t)(keys[i] >> 32) : nb;
-  for (int64_t r = prev + 1; r <= cur; ++r) off[r] = (int32_t)i;
-  if (i < np) idx[i] = (int32_t)(keys[i] & 0xffffffffu);
+// pending boxes of the descent: at most the 26 colleagues plus 8 children per
+// level of depth (194), so the overflow check below never fires
+constexpr int kUWStack = 256;
+
+// U and W of one leaf B, without a global sort.  U(B) is the leaf itself,
+// its coarser-or-equal adjacent leaves CA(B) (already in box order), and the
+// finer leaves adjacent to it.  Those lie inside B's colleagues, and so do
+// the boxes of W(B) (not adjacent to B, parent adjacent).  One descent from
+// the colleagues finds both: a child of a box adjacent to B goes to U if it
+// is an adjacent leaf, to W if it is not adjacent, and is descended into if
+// it is adjacent with children.  Box numbers are level-major, so the finer U
+// entries all follow the coarser-or-equal ones; each finer run and each W
+// run is sorted in place.  Count pass (kFill = false) and fill pass.
+template <bool kFill>
+__global__ void k_uwlist(int64_t nl, const int32_t *__restrict__ leaves,
+                         const BoxGeo *__restrict__ geo, const int32_t *__restrict__ child,
+                         const int32_t *__restrict__ nchild, const int32_t *__restrict__ col,
+                         const int32_t *__restrict__ ncol, const int32_t *__restrict__ caoff,
+                         const int32_t *__restrict__ caidx, int32_t *__restrict__ ucnt,
+                         int32_t *__restrict__ wcnt, const int32_t *__restrict__ uoff,
+                         int32_t *__restrict__ uidx, const int32_t *__restrict__ woff,
+                         int32_t *__restrict__ widx, int *__restrict__ err) {
+  const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (t >= nl) return;
+  const int32_t B = leaves[t];
+  const BoxGeo gB = geo[B];
+  const int32_t c0 = caoff[B], c1 = caoff[B + 1];
+  int64_t ou = 0, ow = 0;
+  if (kFill) {
+    ou = uoff[B];
+    ow = woff[B];
+    int64_t k = ou;  // CA(B) with B merged in at its place
+    bool placed = false;
+    for (int32_t e = c0; e < c1; ++e) {
+      const int32_t A = caidx[e];
+      if (!placed && A > B) {
+        uidx[k++] = B;
+        placed = true;
+      }
+      uidx[k++] = A;
+    }
+    if (!placed) uidx[k++] = B;
+  }
+  int32_t ku = (c1 - c0) + 1, kw = 0;
+  const int32_t kfine = ku;
+  int32_t stack[kUWStack];
+  int sp = 0;
+  bool overflow = false;
+  for (int j = 0; j < ncol[B]; ++j) {
+    const int32_t C = col[26 * (int64_t)B + j];
+    if (nchild[C] > 0) stack[sp++] = C;  // 26 <= kUWStack
+  }
+  while (sp > 0 && !overflow) {
+    const int32_t D = stack[--sp];
+    const int32_t e0 = child[D], e1 = e0 + nchild[D];
+    for (int32_t E = e0; E < e1; ++E) {
+      const BoxGeo gE = geo[E];
+      if (adjacent(gE, gB)) {
+        if (nchild[E] == 0) {
+          if (kFill) uidx[ou + ku] = E;
+          ++ku;
+        } else if (sp < kUWStack) {
+          stack[sp++] = E;
+        } else {
+          overflow = true;
+        }
+      } else {
+        if (kFill) widx[ow + kw] = E;
+        ++kw;
+      }
+    }
+  }
+  if (overflow) {
+    atomicExch(err, 1);
+    return;
+  }
+  if (!kFill) {
+    ucnt[B] = ku;
+    wcnt[B] = kw;
+  } else {
+    sort_run(uidx + ou + kfine, ku - kfine);
+    sort_run(widx + ow, kw);
+  }
 }
+
+
+// CSR rows from (row << 32 | col) keys sorted ascending
 
 // M2L ordering key: (level, parity) class of every box of level >= 2
 __global__ void k_m2l_class(int64_t b0, int64_t nb, const BoxGeo *__restrict__ geo,
@@ -578,21 +642,6 @@ int64_t counts_to_offsets(fmm_plan_impl &P, const int32_t *cnt, DBuf<int32_t> &o
   off.resize(nrows + 1, P.stream);
   scan_exclusive(cnt, off.p, nrows, off.p + nrows, P.s_scan, P.stream);
   return read_scalar(off.p + nrows, P.stream);
-}
-
-// sort (row<<32|col) pairs and convert to CSR over nb rows
-void pairs_to_csr(fmm_plan_impl &P, DBuf<uint64_t> &pairs, int64_t np, int64_t nb,
-                  DBuf<int32_t> &off, DBuf<int32_t> &idx) {
-  cudaStream_t s = P.stream;
-  int b = bits_for(nb);
-  std::vector<int> sh = digit_shifts(0, b);
-  for (int x : digit_shifts(32, 32 + b)) sh.push_back(x);
-  DBuf<int32_t> novals;
-  radix_sort(pairs, novals, P.s_u64b, novals, np, sh, P.s_hist, P.s_scan, s);
-  off.resize(nb + 1, s);
-  idx.resize(np > 0 ? np : 1, s);
-  k_pairs_csr<<<grid(np + 1), kT, 0, s>>>(np, nb, pairs.p, off.p, idx.p);
-  FMM_LAUNCH_CHECK();
 }
 
 int64_t compact(fmm_plan_impl &P, int64_t n, const int32_t *flag, DBuf<int32_t> &out) {
@@ -826,26 +875,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
                                           P.ca_idx.p);
   FMM_LAUNCH_CHECK();
 
-  // ---- U lists (pairs -> sort -> CSR)
-  {
-    int64_t nl = P.nleaves;
-    P.s_i32a.resize(nl + 1, s);
-    k_upairs<false><<<grid(nl), kT, 0, s>>>(nl, P.leaves.p, P.box_geo.p, P.ca_off.p, P.ca_idx.p,
-                                             P.s_i32a.p, nullptr, nullptr);
-    FMM_LAUNCH_CHECK();
-    DBuf<int32_t> &uoffs = P.s_i32b;
-    uoffs.resize(nl + 1, s);
-    scan_exclusive(P.s_i32a.p, uoffs.p, nl, uoffs.p + nl, P.s_scan, s);
-    int64_t np = read_scalar(uoffs.p + nl, s);
-    P.s_u64a.resize(np, s);
-    k_upairs<true><<<grid(nl), kT, 0, s>>>(nl, P.leaves.p, P.box_geo.p, P.ca_off.p, P.ca_idx.p,
-                                            nullptr, uoffs.p, P.s_u64a.p);
-    FMM_LAUNCH_CHECK();
-    pairs_to_csr(P, P.s_u64a, np, nb, P.u_off, P.u_idx);
-    P.nu = np;
-  }
-
-  // ---- X lists, then W as their transpose
+  // ---- X lists (box C: the adjacent leaves of its parent's level or coarser
+  // that are not adjacent to C)
   k_xlist<false><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.ca_off.p, P.ca_idx.p,
                                           P.s_i32a.p, nullptr, nullptr);
   FMM_LAUNCH_CHECK();
@@ -854,11 +885,34 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   k_xlist<true><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.ca_off.p, P.ca_idx.p,
                                          nullptr, P.x_off.p, P.x_idx.p);
   FMM_LAUNCH_CHECK();
-  P.s_u64a.resize(P.nx > 0 ? P.nx : 1, s);
-  k_wpairs<<<grid(nb), kT, 0, s>>>(nb, P.x_off.p, P.x_idx.p, P.s_u64a.p);
-  FMM_LAUNCH_CHECK();
-  pairs_to_csr(P, P.s_u64a, P.nx, nb, P.w_off, P.w_idx);
-  P.nw = P.nx;
+
+  // ---- U and W lists of the leaves (one descent per leaf, rows sorted in place)
+  {
+    const int64_t nl = P.nleaves;
+    DBuf<int32_t> &ucnt = P.s_i32a, &wcnt = P.s_i32d;
+    ucnt.resize(nb, s);
+    wcnt.resize(nb, s);
+    FMM_CUDA(cudaMemsetAsync(ucnt.p, 0, sizeof(int32_t) * nb, s));
+    FMM_CUDA(cudaMemsetAsync(wcnt.p, 0, sizeof(int32_t) * nb, s));
+    if (!P.dev_err.p) {
+      P.dev_err.resize(1, s);
+      FMM_CUDA(cudaMemsetAsync(P.dev_err.p, 0, sizeof(int), s));
+    }
+    k_uwlist<false><<<grid(nl), kT, 0, s>>>(nl, P.leaves.p, P.box_geo.p, P.box_child.p,
+                                             P.box_nchild.p, P.colleagues.p, P.ncolleagues.p,
+                                             P.ca_off.p, P.ca_idx.p, ucnt.p, wcnt.p, nullptr,
+                                             nullptr, nullptr, nullptr, P.dev_err.p);
+    FMM_LAUNCH_CHECK();
+    P.nu = counts_to_offsets(P, ucnt.p, P.u_off, nb);
+    P.nw = counts_to_offsets(P, wcnt.p, P.w_off, nb);
+    P.u_idx.resize(P.nu > 0 ? P.nu : 1, s);
+    P.w_idx.resize(P.nw > 0 ? P.nw : 1, s);
+    k_uwlist<true><<<grid(nl), kT, 0, s>>>(nl, P.leaves.p, P.box_geo.p, P.box_child.p,
+                                            P.box_nchild.p, P.colleagues.p, P.ncolleagues.p,
+                                            P.ca_off.p, P.ca_idx.p, nullptr, nullptr, P.u_off.p,
+                                            P.u_idx.p, P.w_off.p, P.w_idx.p, P.dev_err.p);
+    FMM_LAUNCH_CHECK();
+  }
 
   // ---- work lists for P2L and M2P
   P.s_i32a.resize(nb, s);
