@@ -53,6 +53,12 @@ def _declare(L):
     L.oracle_tree_export.argtypes = [ctypes.c_void_p, _U64, _I32, _I32, _U64] + [_I32] * 14
     L.oracle_fmm_eval.argtypes = [ctypes.c_void_p, _int, _D, _D, _D]
     L.oracle_num_threads.restype = _int
+    L.oracle_dual_build.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    L.oracle_dual_build.restype = ctypes.c_void_p
+    L.oracle_dual_free.argtypes = [ctypes.c_void_p]
+    L.oracle_dual_sizes.argtypes = [ctypes.c_void_p, _I64]
+    L.oracle_dual_export.argtypes = [ctypes.c_void_p, _I32, _I32, _I32, _I32, _D]
+    L.oracle_dual_eval.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _int, _D, _D, _D]
 
 
 def _p(a, t=_D):
@@ -232,4 +238,44 @@ class Tree:
         h = getattr(self, "_h", None)
         if h and _lib is not None:
             _lib.oracle_tree_free(h)
+            self._h = None
+
+
+class Dual:
+    """Dual-tree traversal lists on an oracle ``Tree``: per target box its M2L
+    sources (accepted by r_T + r_S < theta |c_T - c_S|) and its P2P source
+    leaves, plus the cell radii."""
+
+    def __init__(self, tree, theta):
+        self.tree = tree
+        self.theta = float(theta)
+        h = lib().oracle_dual_build(tree._h, self.theta)
+        self._h = h
+        s = np.zeros(2, np.int64)
+        lib().oracle_dual_sizes(h, _p(s, _I64))
+        nb = tree.nboxes
+        self.m2l_off = np.zeros(nb + 1, np.int32)
+        self.m2l_idx = np.zeros(int(s[0]), np.int32)
+        self.p2p_off = np.zeros(nb + 1, np.int32)
+        self.p2p_idx = np.zeros(int(s[1]), np.int32)
+        self.radius = np.zeros(nb)
+        lib().oracle_dual_export(h, _p(self.m2l_off, _I32), _p(self.m2l_idx, _I32),
+                                 _p(self.p2p_off, _I32), _p(self.p2p_idx, _I32),
+                                 _p(self.radius))
+
+    def lst(self, name, b):
+        off = getattr(self, name + "_off")
+        return getattr(self, name + "_idx")[off[b]:off[b + 1]]
+
+    def eval(self, p, q, grad=True):
+        q = _f64(q)
+        phi = np.zeros(self.tree.n)
+        g = np.zeros((self.tree.n, 3)) if grad else None
+        lib().oracle_dual_eval(self.tree._h, self._h, p, _p(q), _p(phi), _p(g))
+        return (phi, g) if grad else phi
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.oracle_dual_free(h)
             self._h = None

@@ -753,3 +753,207 @@ void oracle_fmm_eval(const oracle_tree *t, int p, const double *q_in, double *ph
   free(phi);
   free(grad);
 }
+
+/* ------------------------------------------------------------------------
+ * Dual-tree traversal with a multipole acceptance criterion (§2.1: Dehnen's
+ * dual tree walk as the alternative to fixed interaction lists).
+ *
+ * Expansion centres are the geometric box centres.  Cell radius:
+ *   r_B = max over the points j of B of |x_j - c_B|.
+ * A pair (T, S) of distinct cells is accepted for one M2L from S into T iff
+ *   r_T + r_S < theta |c_T - c_S|,
+ * with c_T - c_S taken from the integer anchors (exact in FP64) and every
+ * operation a single IEEE-rounded add, multiply or square root in the order
+ * written, so that another implementation that follows the same steps takes
+ * the same decisions.
+ * A rejected pair splits by a rule that does not depend on the order of T
+ * and S, so (T, S) ends in M2L (or P2P) exactly when (S, T) does and the
+ * truncated operator stays symmetric:
+ *   both leaves       -> P2P (T == S included: the leaf with itself)
+ *   one leaf          -> split the other cell
+ *   different levels  -> split the coarser cell
+ *   same level        -> split both.
+ * Starting from (root, root) every ordered pair (target point, source point)
+ * lands in exactly one M2L pair (T, S) with the target in T and the source in
+ * S, or in one P2P pair of leaves.
+ * ---------------------------------------------------------------------- */
+struct oracle_dual {
+  int64_t nb;
+  double theta;
+  double *radius;
+  ivec *M, *P; /* per target box: M2L sources, P2P source leaves */
+};
+
+static int dual_accept(const oracle_tree *t, const double *r, double theta, int32_t T,
+                       int32_t S) {
+  double aT = t->side[t->box_level[T]], aS = t->side[t->box_level[S]];
+  double d[3];
+  for (int k = 0; k < 3; ++k)
+    d[k] = ((double)t->anchor[T][k] + 0.5) * aT - ((double)t->anchor[S][k] + 0.5) * aS;
+  double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  return r[T] + r[S] < theta * dist;
+}
+
+static void dual_walk(const oracle_tree *t, oracle_dual *D, int32_t T, int32_t S) {
+  if (T != S && dual_accept(t, D->radius, D->theta, T, S)) {
+    ivec_push(&D->M[T], S);
+    return;
+  }
+  int lt = t->box_nchild[T] == 0, ls = t->box_nchild[S] == 0;
+  if (lt && ls) {
+    ivec_push(&D->P[T], S);
+    return;
+  }
+  int splitT, splitS;
+  if (lt) {
+    splitT = 0;
+    splitS = 1;
+  } else if (ls) {
+    splitT = 1;
+    splitS = 0;
+  } else if (t->box_level[T] != t->box_level[S]) {
+    splitT = t->box_level[T] < t->box_level[S];
+    splitS = !splitT;
+  } else {
+    splitT = splitS = 1;
+  }
+  int nt = splitT ? t->box_nchild[T] : 1, ns = splitS ? t->box_nchild[S] : 1;
+  for (int i = 0; i < nt; ++i)
+    for (int j = 0; j < ns; ++j)
+      dual_walk(t, D, splitT ? t->box_child[T] + i : T, splitS ? t->box_child[S] + j : S);
+}
+
+oracle_dual *oracle_dual_build(const oracle_tree *t, double theta) {
+  oracle_dual *D = calloc(1, sizeof(oracle_dual));
+  int64_t nb = t->nboxes, nba = nb ? nb : 1;
+  D->nb = nb;
+  D->theta = theta;
+  D->radius = calloc(nba, sizeof(double));
+  D->M = calloc(nba, sizeof(ivec));
+  D->P = calloc(nba, sizeof(ivec));
+  for (int64_t b = 0; b < nb; ++b) {
+    double m = 0.0;
+    for (int64_t j = t->box_first[b]; j < t->box_first[b] + t->box_count[b]; ++j) {
+      double dx = t->xyz[3 * j] - t->center[b][0];
+      double dy = t->xyz[3 * j + 1] - t->center[b][1];
+      double dz = t->xyz[3 * j + 2] - t->center[b][2];
+      double s = dx * dx + dy * dy + dz * dz;
+      if (s > m) m = s;
+    }
+    D->radius[b] = sqrt(m);
+  }
+  if (nb > 0) dual_walk(t, D, 0, 0);
+  for (int64_t b = 0; b < nb; ++b) {
+    qsort(D->M[b].a, D->M[b].n, sizeof(int32_t), cmp_i32);
+    qsort(D->P[b].a, D->P[b].n, sizeof(int32_t), cmp_i32);
+  }
+  return D;
+}
+
+void oracle_dual_free(oracle_dual *D) {
+  if (!D) return;
+  for (int64_t b = 0; b < D->nb; ++b) {
+    free(D->M[b].a);
+    free(D->P[b].a);
+  }
+  free(D->M);
+  free(D->P);
+  free(D->radius);
+  free(D);
+}
+
+void oracle_dual_sizes(const oracle_dual *D, int64_t s[2]) {
+  s[0] = list_total(D->M, D->nb);
+  s[1] = list_total(D->P, D->nb);
+}
+
+void oracle_dual_export(const oracle_dual *D, int32_t *m_off, int32_t *m_idx, int32_t *p_off,
+                        int32_t *p_idx, double *radius) {
+  export_list(D->M, D->nb, m_off, m_idx);
+  export_list(D->P, D->nb, p_off, p_idx);
+  if (radius) memcpy(radius, D->radius, sizeof(double) * D->nb);
+}
+
+/* FMM mat-vec on the dual-tree lists: P2M at leaves; M2M up to the root;
+ * M2L over every accepted pair (any level, cells of different sizes
+ * included); L2L from the root down; at leaf targets L2P + P2P over the
+ * leaf pairs.  There are no W/X corrections: the traversal covers every
+ * point pair by M2L or P2P. */
+void oracle_dual_eval(const oracle_tree *t, const oracle_dual *D, int p, const double *q_in,
+                      double *phi_out, double *grad_out) {
+  int64_t n = t->n, nb = t->nboxes;
+  int nc = ncoef(p);
+  if (n == 0) return;
+  double *q = malloc(sizeof(double) * n);
+  for (int64_t i = 0; i < n; ++i) q[i] = q_in[t->perm[i]];
+  cplx *M = calloc((size_t)nb * nc, sizeof(cplx));
+  cplx *L = calloc((size_t)nb * nc, sizeof(cplx));
+  double *phi = calloc(n, sizeof(double));
+  double *grad = calloc(3 * n, sizeof(double));
+
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t b = 0; b < nb; ++b)
+    if (t->box_nchild[b] == 0)
+      oracle_p2m(p, t->center[b], t->box_count[b], t->xyz + 3 * (int64_t)t->box_first[b],
+                 q + t->box_first[b], (double *)(M + (size_t)b * nc));
+  for (int l = t->nlevels - 2; l >= 0; --l) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = t->level_offset[l]; b < t->level_offset[l + 1]; ++b)
+      for (int c = 0; c < t->box_nchild[b]; ++c) {
+        int32_t C = t->box_child[b] + c;
+        oracle_m2m(p, t->center[C], (double *)(M + (size_t)C * nc), t->center[b],
+                   (double *)(M + (size_t)b * nc));
+      }
+  }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t b = 0; b < nb; ++b)
+    for (int64_t k = 0; k < D->M[b].n; ++k) {
+      int32_t A = D->M[b].a[k];
+      oracle_m2l(p, t->center[A], (double *)(M + (size_t)A * nc), t->center[b],
+                 (double *)(L + (size_t)b * nc));
+    }
+  for (int l = 1; l < t->nlevels; ++l) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = t->level_offset[l]; b < t->level_offset[l + 1]; ++b) {
+      int32_t P = t->box_parent[b];
+      oracle_l2l(p, t->center[P], (double *)(L + (size_t)P * nc), t->center[b],
+                 (double *)(L + (size_t)b * nc));
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t b = 0; b < nb; ++b) {
+    if (t->box_nchild[b] != 0) continue;
+    int64_t f = t->box_first[b], cnt = t->box_count[b];
+    const double *tx = t->xyz + 3 * f;
+    oracle_l2p(p, t->center[b], (double *)(L + (size_t)b * nc), cnt, tx, phi + f, grad + 3 * f);
+    for (int64_t k = 0; k < D->P[b].n; ++k) {
+      int32_t A = D->P[b].a[k];
+      int64_t fa = t->box_first[A], ca = t->box_count[A];
+      for (int64_t i = 0; i < cnt; ++i)
+        for (int64_t j = fa; j < fa + ca; ++j) {
+          double dx = tx[3 * i] - t->xyz[3 * j];
+          double dy = tx[3 * i + 1] - t->xyz[3 * j + 1];
+          double dz = tx[3 * i + 2] - t->xyz[3 * j + 2];
+          double r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 == 0.0) continue;
+          double r = sqrt(r2);
+          phi[f + i] += q[j] / r;
+          double s = q[j] / (r2 * r);
+          grad[3 * (f + i)] -= s * dx;
+          grad[3 * (f + i) + 1] -= s * dy;
+          grad[3 * (f + i) + 2] -= s * dz;
+        }
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t o = t->perm[i];
+    phi_out[o] = phi[i];
+    if (grad_out)
+      for (int a = 0; a < 3; ++a) grad_out[3 * (int64_t)o + a] = grad[3 * i + a];
+  }
+  free(q);
+  free(M);
+  free(L);
+  free(phi);
+  free(grad);
+}

@@ -106,6 +106,24 @@ void oracle_tree_export(const oracle_tree *t, uint64_t *keys, int32_t *perm,
 void oracle_fmm_eval(const oracle_tree *t, int p, const double *q,
                      double *phi, double *grad);
 
+/* ---- dual-tree traversal with a multipole acceptance criterion (§2.1):
+ * cell radius r_B = max |x_j - c_B| over B's points; (T, S) accepted for M2L
+ * iff r_T + r_S < theta |c_T - c_S|; rejected pairs split symmetrically
+ * (both leaves -> P2P; one leaf -> the other; coarser cell; same level ->
+ * both).  Lists per target box, sources ascending. */
+typedef struct oracle_dual oracle_dual;
+oracle_dual *oracle_dual_build(const oracle_tree *t, double theta);
+void oracle_dual_free(oracle_dual *d);
+/* sizes: [0] = M2L pairs, [1] = P2P leaf pairs */
+void oracle_dual_sizes(const oracle_dual *d, int64_t sizes[2]);
+/* offsets nboxes+1, sources, radius nboxes; any pointer may be NULL */
+void oracle_dual_export(const oracle_dual *d, int32_t *m2l_off, int32_t *m2l_idx,
+                        int32_t *p2p_off, int32_t *p2p_idx, double *radius);
+/* FMM mat-vec over the dual-tree lists (M2M to the root, M2L over the
+ * accepted pairs, L2L from the root, L2P + P2P at the leaves) */
+void oracle_dual_eval(const oracle_tree *t, const oracle_dual *d, int p, const double *q,
+                      double *phi, double *grad);
+
 /* number of OpenMP threads the oracle runs with (1 without OpenMP) */
 int oracle_num_threads(void);
 
