@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-problem leg")
+    ap.add_argument("--dual-theta", type=float, default=0.75,
+                    help="also time the dual-tree walk (acceptance theta) on the same points; 0 skips")
     ap.add_argument("--precond", action="store_true",
                     help="add the FMM-preconditioned CG solve of the 7-point Laplace problem")
     ap.add_argument("--lattice", action="store_true",
@@ -355,6 +357,53 @@ def precond_leg(dev, h=2.0 ** -5, tol=1e-8):
             "runs": rows}
 
 
+def dual_leg(X, Q, S, p, precision, theta, rel_err, steps, stream, ms_lists, ms_eval_lists):
+    """The same points and order with the dual-tree walk (§2.1: Dehnen's walk
+    with acceptance r_T + r_S < theta |c_T - c_S|) instead of the U/V/W/X
+    lists: plan + eval and eval-only time, error on the same sampled targets,
+    pair counts and per-pass times."""
+    import torch
+    from paper_1602_02244_gb300 import binding
+    L = binding.library()
+    plan = binding.Plan(X, leaf_size=S, order=p, precision=precision, interaction="dual",
+                        theta=theta)
+    phi, g = plan.eval(Q)
+    err = rel_err(phi, g)
+    plan.rebuild(X)
+    plan.eval(Q, out=(phi, g))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        plan.rebuild(X)
+        plan.eval(Q, out=(phi, g))
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    e0.record(stream)
+    for _ in range(steps):
+        plan.eval(Q, out=(phi, g))
+    e1.record(stream)
+    e1.synchronize()
+    ms_eval = e0.elapsed_time(e1) / steps
+    ms_arr = (ctypes.c_double * 12)()
+    la_arr = (ctypes.c_int64 * 12)()
+    L.fmm_profile(plan._h, 1)
+    plan.rebuild(X)
+    plan.eval(Q, out=(phi, g))
+    L.fmm_profile_read(plan._h, ms_arr, la_arr)
+    sz = plan.sizes()
+    plan.close()
+    n = Q.shape[0]
+    return {"theta": theta, "value": n / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "eval_only": {"value": n / (ms_eval / 1e3), "ms": ms_eval},
+            "rel_error_vs_direct": err, "m2l_pairs": sz["nv"], "p2p_leaf_pairs": sz["nu"],
+            "pass_ms": {PASSES[i]: ms_arr[i] for i in range(12)},
+            "lists_over_dual_speedup": ms / ms_lists,
+            "lists_over_dual_speedup_eval_only": ms_eval / ms_eval_lists}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -585,6 +634,9 @@ def run_ours(args):
                                     "mixed_speedup_eval_only": ms64_eval / ms_eval}
         plan64.close()
 
+    if args.dual_theta > 0:
+        line["dual_tree"] = dual_leg(X, Q, S, p, args.precision, args.dual_theta, rel_err,
+                                     min(args.steps, 5), stream, ms, ms_eval)
     if not args.no_batch:
         line["batched"] = batched_leg(dev, args.steps, args.warmup)
     if args.lattice:

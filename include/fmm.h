@@ -69,7 +69,16 @@ typedef struct {
   int m2l_path;           /* MIXED, order <= 10: 0 = default (tensor cores),
                              1 = FP32 CUDA cores, 2 = tensor cores (tcgen05,
                              three-product TF32 split)                        */
-  int reserved[4];        /* must be zero                                     */
+  int interaction;        /* how boxes are paired (§2.1):
+                             0 = U/V/W/X lists of the adaptive octree (default);
+                             1 = dual-tree walk with the multipole acceptance
+                                 criterion r_T + r_S < mac_theta |c_T - c_S|,
+                                 r_B = max |x_j - c_B| over the box's points
+                                 (Dehnen): M2L between cells of any sizes,
+                                 P2P between the remaining leaf pairs          */
+  int reserved;           /* must be zero                                     */
+  double mac_theta;       /* interaction 1: 0 < theta < 1 (0 = default, 0.5);
+                             smaller is more accurate and slower              */
 } fmm_opts;
 
 /* Build a plan for n points (d_xyz: device, n x 3 FP64).
@@ -145,7 +154,8 @@ fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_
                           double *h_phi, double *h_grad, void *stream);
 
 /* Plan layout, for tests and inspection.  sizes[0..9] =
- *   n, nboxes, nlevels, |U|, |V|, |W|, |X|, order, leaf_size, precision. */
+ *   n, nboxes, nlevels, |U|, |V|, |W|, |X|, order, leaf_size, precision.
+ * For a dual-tree plan |U| counts P2P leaf pairs and |V| M2L pairs. */
 fmm_status fmm_plan_sizes(fmm_plan_t plan, int64_t sizes[10]);
 
 /* Copy one plan array to host memory (synchronous).  Arrays (element type,
@@ -164,6 +174,10 @@ fmm_status fmm_plan_sizes(fmm_plan_t plan, int64_t sizes[10]);
  *  12/13 V, 14/15 W, 16/17 X likewise.
  *  18 root cubes (double, 4 per problem): lo_x, lo_y, lo_z, D.
  *  19 problem offsets (int64, nproblems + 1).
+ *  20 cell radii (double, nboxes; dual-tree plans only, else 0 bytes).
+ * A dual-tree plan (opts.interaction 1) keeps its P2P source leaves in U (per
+ * leaf) and its M2L sources in V (per box of any level, sources of any
+ * level); W and X are empty.
  * Boxes are numbered by (level, key); list sources ascend by box number.
  * `bytes` must equal the array's size in bytes (INVALID_ARG otherwise). */
 fmm_status fmm_plan_export(fmm_plan_t plan, int which, void *h_dst, size_t bytes);

@@ -25,7 +25,7 @@ EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
                  "box_parent", "box_child", "box_nchild", "u_off", "u_idx", "v_off", "v_idx",
-                 "w_off", "w_idx", "x_off", "x_idx", "root", "offsets")
+                 "w_off", "w_idx", "x_off", "x_idx", "root", "offsets", "radius")
 
 
 class FMMError(RuntimeError):
@@ -37,7 +37,8 @@ class FMMError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("coarse_fp64_levels", ctypes.c_int),
                 ("max_depth", ctypes.c_int), ("m2l_path", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("interaction", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("mac_theta", ctypes.c_double)]
 
 
 _lib = None
@@ -109,11 +110,14 @@ class Plan:
     ``points``: (N, 3) float64 CUDA tensor.  ``order`` is the largest harmonic
     degree p; ``precision`` is "fp64" or "mixed"; ``leaf_size`` 0 autotunes.
     ``offsets`` (sequence of B+1 ints) makes a batch of B independent problems
-    over the concatenated points (fmm_plan_create_batch).
+    over the concatenated points (fmm_plan_create_batch).  ``interaction`` is
+    "lists" (U/V/W/X) or "dual" (dual-tree walk with acceptance criterion
+    r_T + r_S < theta |c_T - c_S|; ``theta`` 0 = default 0.5).
     """
 
     def __init__(self, points, leaf_size=64, order=8, precision="fp64", coarse_fp64_levels=0,
-                 max_depth=0, stream=None, offsets=None, m2l_path="auto"):
+                 max_depth=0, stream=None, offsets=None, m2l_path="auto", interaction="lists",
+                 theta=0.0):
         L = library()
         self.device = points.device
         self.n = int(points.shape[0])
@@ -123,6 +127,9 @@ class Plan:
         opts.coarse_fp64_levels = coarse_fp64_levels
         opts.max_depth = max_depth
         opts.m2l_path = {"auto": 0, "simt": 1, "tensor": 2}[m2l_path]
+        opts.interaction = {"lists": 0, "dual": 1}[interaction]
+        opts.mac_theta = float(theta)
+        self.interaction = interaction
         self.precision, self.order, self.leaf_size = precision, order, leaf_size
         h = _vp()
         self.nproblems = 1 if offsets is None else len(offsets) - 1
@@ -242,7 +249,8 @@ class Plan:
                [(np.int32, nb)] * 6 + \
                [(np.int32, nb1), (np.int32, sz["nu"]), (np.int32, nb1), (np.int32, sz["nv"]),
                 (np.int32, nb1), (np.int32, sz["nw"]), (np.int32, nb1), (np.int32, sz["nx"]),
-                (np.float64, 4 * self.nproblems), (np.int64, self.nproblems + 1)]
+                (np.float64, 4 * self.nproblems), (np.int64, self.nproblems + 1),
+                (np.float64, nb if self.interaction == "dual" else 0)]
         out = {}
         for i, (name, (dt, cnt)) in enumerate(zip(EXPORT_FIELDS, spec)):
             a = np.zeros(cnt, dtype=dt)

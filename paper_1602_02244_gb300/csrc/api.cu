@@ -67,8 +67,21 @@ void check_opts(const fmm_opts *o) {
     throw Error(FMM_ERR_INVALID_ARG, "opts.max_depth must be in 0..21");
   if (o->m2l_path < 0 || o->m2l_path > 2)
     throw Error(FMM_ERR_INVALID_ARG, "opts.m2l_path must be 0, 1 or 2");
-  for (int r : o->reserved)
-    if (r != 0) throw Error(FMM_ERR_INVALID_ARG, "opts.reserved must be zero");
+  if (o->interaction < 0 || o->interaction > 1)
+    throw Error(FMM_ERR_INVALID_ARG, "opts.interaction must be 0 or 1");
+  if (!(o->mac_theta >= 0.0 && o->mac_theta < 1.0))
+    throw Error(FMM_ERR_INVALID_ARG, "opts.mac_theta must be in [0, 1)");
+  if (o->reserved != 0) throw Error(FMM_ERR_INVALID_ARG, "opts.reserved must be zero");
+}
+
+void apply_opts(fmm_plan_impl &P, const fmm_opts *o) {
+  if (!o) return;
+  P.m2l_path = o->m2l_path;
+  P.precision = o->precision;
+  P.coarse_fp64_levels = o->coarse_fp64_levels == 0 ? 3 : o->coarse_fp64_levels;
+  P.max_depth = o->max_depth == 0 ? kMaxDepth : o->max_depth;
+  P.dual = o->interaction == 1;
+  P.theta = o->mac_theta > 0.0 ? o->mac_theta : 0.5;
 }
 
 }  // namespace
@@ -124,6 +137,8 @@ void release_plan(fmm_plan_impl &P) {
   P.xslot.release(); P.K64.release(); P.K32.release(); P.box_prob.release();
   P.box_side.release(); P.prob_off.release(); P.prob_geom.release(); P.iperm.release();
   P.ops.m2m32t.release(); P.ops.l2l32t.release();
+  P.radius.release(); P.dt_a.release(); P.dt_b.release(); P.dt_m2l.release();
+  P.dt_p2p.release(); P.dt_cnt.release();
 }
 
 }  // namespace fmm
@@ -148,12 +163,7 @@ fmm_status fmm_plan_create(const double *d_xyz, int64_t n, int leaf_size, int or
     P->leaf_size = leaf_size > 0 ? leaf_size : 64;
     P->autotune = leaf_size == 0;
     P->stream = (cudaStream_t)stream;
-    if (opts) {
-      P->m2l_path = opts->m2l_path;
-      P->precision = opts->precision;
-      P->coarse_fp64_levels = opts->coarse_fp64_levels == 0 ? 3 : opts->coarse_fp64_levels;
-      P->max_depth = opts->max_depth == 0 ? kMaxDepth : opts->max_depth;
-    }
+    apply_opts(*P, opts);
     if (P->autotune && n > 0) P->leaf_size = tuned_leaf_size(*P, d_xyz, n);
     build_tree(*P, d_xyz, n);
   });
@@ -193,12 +203,7 @@ fmm_status fmm_plan_create_batch(const double *d_xyz, const int64_t *h_offsets, 
     P->stream = (cudaStream_t)stream;
     P->nproblems = nproblems;
     P->prob_off_h.assign(h_offsets, h_offsets + nproblems + 1);
-    if (opts) {
-      P->m2l_path = opts->m2l_path;
-      P->precision = opts->precision;
-      P->coarse_fp64_levels = opts->coarse_fp64_levels == 0 ? 3 : opts->coarse_fp64_levels;
-      P->max_depth = opts->max_depth == 0 ? kMaxDepth : opts->max_depth;
-    }
+    apply_opts(*P, opts);
     if (P->autotune && n > 0) P->leaf_size = tuned_leaf_size(*P, d_xyz, n);
     build_tree(*P, d_xyz, n);
   });
@@ -380,6 +385,7 @@ fmm_status fmm_plan_export(fmm_plan_t plan, int which, void *h_dst, size_t bytes
     case 17: src = P.x_idx.p; want = (size_t)P.nx * 4; break;
     case 18: src = nullptr; want = geo4.size() * sizeof(double); break;
     case 19: src = nullptr; want = (P.prob_off_h.empty() ? 2 : P.prob_off_h.size()) * sizeof(int64_t); break;
+    case 20: src = P.radius.p; want = P.dual ? nb * 8 : 0; break;
     default: return fail(FMM_ERR_INVALID_ARG, "unknown export array");
   }
   if (bytes != want)

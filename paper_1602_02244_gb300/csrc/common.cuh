@@ -137,6 +137,25 @@ __host__ __device__ __forceinline__ Dbl4 make_dbl4(double x, double y, double z,
   return v;
 }
 
+// Sort a short run of box numbers in place (Shell sort with Ciura's gaps;
+// plain insertion for runs up to 32).
+__device__ inline void sort_run(int32_t *a, int n) {
+  const int gaps[] = {301, 132, 57, 23, 10, 4, 1};
+  for (int gi = 0; gi < 7; ++gi) {
+    const int gap = gaps[gi];
+    if (gap >= n) continue;
+    for (int i = gap; i < n; ++i) {
+      const int32_t v = a[i];
+      int j = i;
+      while (j >= gap && a[j - gap] > v) {
+        a[j] = a[j - gap];
+        j -= gap;
+      }
+      a[j] = v;
+    }
+  }
+}
+
 struct __align__(16) BoxGeo {
   int32_t ix, iy, iz, level;
 };

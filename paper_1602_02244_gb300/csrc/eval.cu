@@ -6,6 +6,9 @@
 // FP64 mode runs every pass in FP64.  Mixed mode runs P2M/M2L/P2L/L2P/M2P/P2P
 // in FP32 and keeps FP64 only for M2M/L2L into the coarsest levels
 // (<= coarse_fp64_levels) and for the per-target totals.
+// A dual-tree plan runs the same sequence with M2M up to level 1, one M2L
+// launch over its accepted pairs (any level, writes every box's local), L2L
+// from level 1 down, no P2L/M2P, and P2P over its leaf pairs.
 #include "eval_kernels.cuh"
 #include <algorithm>
 
@@ -43,7 +46,8 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
     launch_p2m<double>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p,
                        P.src64.p, P.box_side.p, P.M64.p, nullptr, -1, s);
   }
-  for (int l = P.nlevels - 2; l >= 2; --l) {
+  const int ltop = P.dual ? 1 : 2;  // coarsest level whose boxes take part in M2L
+  for (int l = P.nlevels - 2; l >= ltop; --l) {
     PassScope ps_(P, kPassM2M);
     launch_m2m<double, double, double, double>(p, P.level_off[l], P.level_off[l + 1] - P.level_off[l],
                                                P.box_child.p, P.box_nchild.p, P.box_geo.p, P.M64.p,
@@ -51,15 +55,18 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   }
   {
     PassScope ps_(P, kPassM2L);
-    launch_m2l<double>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_order.p, P.v_off.p,
-                       P.v_idx.p, P.box_geo.p, P.M64.p, P.ops.m2l64.p, P.L64.p, s);
+    if (P.dual)
+      launch_m2l_dual<double>(p, P.nboxes, P.v_off.p, P.v_idx.p, P.box_geo.p, P.M64.p, P.L64.p, s);
+    else
+      launch_m2l<double>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_order.p, P.v_off.p,
+                         P.v_idx.p, P.box_geo.p, P.M64.p, P.ops.m2l64.p, P.L64.p, s);
   }
   {
     PassScope ps_(P, kPassP2L);
     launch_p2l<double>(p, P.nxboxes, P.xboxes.p, P.x_off.p, P.x_idx.p, P.box_first.p, P.box_count.p,
                        P.box_geo.p, P.src64.p, P.box_side.p, P.L64.p, s);
   }
-  for (int l = 3; l < P.nlevels; ++l) {
+  for (int l = ltop + 1; l < P.nlevels; ++l) {
     PassScope ps_(P, kPassL2L);
     launch_l2l<double, double, double, double, double>(
         p, P.level_off[l], P.level_off[l + 1] - P.level_off[l], P.box_parent.p, P.box_geo.p, P.L64.p,
@@ -68,9 +75,9 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   {
     PassScope ps_(P, kPassL2P);
     launch_l2p<double>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src64.p,
-                       P.box_side.p, P.L64.p, n, P.far_acc.p, s);
+                       P.box_side.p, P.L64.p, n, P.far_acc.p, ltop, s);
   }
-  {
+  if (P.nwleaves > 0) {
     PassScope ps_(P, kPassM2P);
     P.K64.resize(std::max<size_t>(1, (size_t)P.nxboxes * 4 * coef_pitch(p + 1)), s);
     launch_m2p<double>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.nxboxes, P.xboxes.p,
@@ -102,7 +109,8 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
     launch_p2m<float>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p,
                       P.box_side.p, P.M32.p, coarse ? P.M64.p : nullptr, lc, s);
   }
-  for (int l = P.nlevels - 2; l >= 2; --l) {
+  const int ltop = P.dual ? 1 : 2;  // coarsest level whose boxes take part in M2L
+  for (int l = P.nlevels - 2; l >= ltop; --l) {
     const int32_t b0 = P.level_off[l], nbl = P.level_off[l + 1] - b0;
     PassScope ps_(P, kPassM2M);
     if (l <= lc) {
@@ -121,7 +129,9 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   }
   {
     PassScope ps_(P, kPassM2L);
-    if (P.m2l_tc) {
+    if (P.dual) {
+      launch_m2l_dual<float>(p, P.nboxes, P.v_off.p, P.v_idx.p, P.box_geo.p, P.M32.p, P.L32.p, s);
+    } else if (P.m2l_tc) {
       const size_t kt = m2l_tc_pitch(p);
       P.Mhi.resize((size_t)P.nboxes * kt, s);
       P.Mlo.resize((size_t)P.nboxes * kt, s);
@@ -141,12 +151,12 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
                       P.box_geo.p, P.src32.p, P.box_side.p, P.L32.p, s);
   }
   const size_t nc = (size_t)coef_pitch(p);
-  if (coarse && P.nlevels > 2) {
-    const size_t b0 = (size_t)P.level_off[2], b1 = (size_t)P.level_off[3];
+  if (coarse && P.nlevels > ltop) {
+    const size_t b0 = (size_t)P.level_off[ltop], b1 = (size_t)P.level_off[ltop + 1];
     PassScope ps_(P, kPassL2L);
     launch_to_f64<float>((int64_t)((b1 - b0) * nc), P.L32.p + b0 * nc, P.L64.p + b0 * nc, s);
   }
-  for (int l = 3; l < P.nlevels; ++l) {
+  for (int l = ltop + 1; l < P.nlevels; ++l) {
     const int32_t b0 = P.level_off[l], nbl = P.level_off[l + 1] - b0;
     PassScope ps_(P, kPassL2L);
     if (l <= lc)
@@ -159,9 +169,9 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   {
     PassScope ps_(P, kPassL2P);
     launch_l2p<float>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p,
-                      P.box_side.p, P.L32.p, n, P.far_acc.p, s);
+                      P.box_side.p, P.L32.p, n, P.far_acc.p, ltop, s);
   }
-  {
+  if (P.nwleaves > 0) {
     PassScope ps_(P, kPassM2P);
     P.K32.resize(std::max<size_t>(1, (size_t)P.nxboxes * 4 * coef_pitch(p + 1)), s);
     launch_m2p<float>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.nxboxes, P.xboxes.p,

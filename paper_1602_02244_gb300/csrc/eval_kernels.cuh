@@ -36,10 +36,12 @@ void launch_l2l(int p, int32_t b0, int32_t nbl, const int32_t *parent, const Box
                 cudaStream_t s);
 template <typename Tin>
 void launch_to_f64(int64_t count, const Tin *in, double *out, cudaStream_t s);
+// lfar: leaves above this level get no far field (2 for U/V/W/X lists, 1
+// for the dual tree)
 template <typename T>
 void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
-                const T *L, int64_t n, double *far, cudaStream_t s);
+                const T *L, int64_t n, double *far, int lfar, cudaStream_t s);
 // M2P over W lists; K is scratch of 4 * coef_pitch(p+1) per X box (the W sources)
 template <typename T>
 void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, const int32_t *widx,
@@ -72,6 +74,12 @@ void launch_m2l_tc(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *t
                    const int16_t *slots, const int32_t *nslots, const int32_t *order, int64_t nb,
                    const float *M, float *Mhi, float *Mlo, const float *opt, float *L, int *err,
                    cudaStream_t s);
+
+// dual.cu: M2L over the dual-tree pairs (cells of any two sizes); writes
+// L of every box (zero where its list is empty)
+template <typename T>
+void launch_m2l_dual(int p, int64_t nb, const int32_t *off, const int32_t *idx, const BoxGeo *geo,
+                     const T *M, T *L, cudaStream_t s);
 
 // p2p.cu
 template <typename T>

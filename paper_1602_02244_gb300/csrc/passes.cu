@@ -398,7 +398,7 @@ __global__ void k_l2p(int p_rt, const int32_t *__restrict__ leaves, const int32_
                       const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
                       const typename V4<T>::type *__restrict__ src,
                       const double *__restrict__ side, const T *__restrict__ L, int64_t n,
-                      double *__restrict__ far) {
+                      double *__restrict__ far, int lfar) {
   const int p = PT > 0 ? PT : p_rt;  // compile-time order unrolls the harmonic streams
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Ls = reinterpret_cast<T *>(smem_raw);
@@ -406,7 +406,7 @@ __global__ void k_l2p(int p_rt, const int32_t *__restrict__ leaves, const int32_
   const int32_t b = leaves[blockIdx.x];
   const BoxGeo g = geo[b];
   const int32_t f = first[b], c = count[b];
-  if (g.level < 2) {  // no far field reaches levels 0 and 1
+  if (g.level < lfar) {  // no far field reaches the levels above lfar
     for (int32_t i = f + threadIdx.x; i < f + c; i += blockDim.x)
       reinterpret_cast<Dbl4 *>(far)[i] = make_dbl4(0.0, 0.0, 0.0, 0.0);
     return;
@@ -900,12 +900,12 @@ void launch_to_f64(int64_t count, const Tin *in, double *out, cudaStream_t s) {
 template <typename T>
 void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
-                const T *L, int64_t n, double *far, cudaStream_t s) {
+                const T *L, int64_t n, double *far, int lfar, cudaStream_t s) {
   if (nleaves == 0) return;
   size_t sm = (size_t)ncoef(p) * sizeof(T);
   with_order(p, [&](auto PC) {
     k_l2p<T, decltype(PC)::value><<<(unsigned)nleaves, 64, sm, s>>>(p, leaves, first, count, geo, src,
-                                                                    side, L, n, far);
+                                                                    side, L, n, far, lfar);
   });
   FMM_LAUNCH_CHECK();
 }
@@ -974,7 +974,7 @@ void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double
                               const V4<T>::type *, const double *, T *, cudaStream_t);                     \
   template void launch_l2p<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
                               const BoxGeo *, const V4<T>::type *, const double *, const T *, int64_t,     \
-                              double *, cudaStream_t);                                             \
+                              double *, int, cudaStream_t);                                        \
   template void launch_m2p<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
                               int64_t, const int32_t *, const int32_t *, const int32_t *,          \
                               const int32_t *, const BoxGeo *, const V4<T>::type *, const double *, \

@@ -37,6 +37,8 @@ uint64_t launch_count();
 struct fmm_plan_impl {
   // configuration
   int m2l_path = 0;                  // 0 auto, 1 CUDA cores, 2 tensor cores
+  bool dual = false;                 // lists from the dual-tree walk (else U/V/W/X)
+  double theta = 0.5;                // dual tree: acceptance r_T + r_S < theta |c_T - c_S|
   bool m2l_tc = false;               // this plan's M2L runs on the tensor cores
   int order = 0, leaf_size = 1, autotune = 0, precision = FMM_FP64, coarse_fp64_levels = 3, max_depth = kMaxDepth;
   cudaStream_t stream = nullptr;
@@ -74,8 +76,12 @@ struct fmm_plan_impl {
   DBuf<int32_t> colleagues;         // nboxes x 26, sorted, -1 padded
   DBuf<int32_t> ncolleagues;
 
-  // lists (CSR over all boxes)
+  // lists (CSR over all boxes); a dual-tree plan keeps its P2P leaf pairs in
+  // U and its M2L pairs (sources of any level) in V, with W and X empty
   DBuf<int32_t> u_off, u_idx, v_off, v_idx, w_off, w_idx, x_off, x_idx;
+  DBuf<double> radius;              // dual tree: max |x_j - c_B| over the box's points
+  DBuf<int2> dt_a, dt_b, dt_m2l, dt_p2p;  // dual-tree walk: frontiers and pairs
+  DBuf<unsigned long long> dt_cnt;
   int64_t nu = 0, nv = 0, nw = 0, nx = 0;
 
   // work lists
@@ -176,6 +182,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n);
 void morton_keys_raw(const double *d_xyz, int64_t n, double *partial, double *geom, uint64_t *keys,
                      int32_t *perm, cudaStream_t s);
 void set_points(fmm_plan_impl &P, const double *d_xyz);
+// dual.cu: cell radii, the dual-tree walk, and its M2L / P2P lists
+void build_dual_lists(fmm_plan_impl &P);
 // operators.cu
 void build_operators(fmm_plan_impl &P);
 // m2l.cu

@@ -508,25 +508,6 @@ __global__ void k_xlist(int64_t nb, const BoxGeo *__restrict__ geo, const int32_
 }
 
 // W pairs from X: (A, C) for every A in X(C)
-// Sort a short run of box numbers in place (Shell sort with Ciura's gaps;
-// plain insertion for runs up to 32).
-__device__ void sort_run(int32_t *a, int n) {
-  const int gaps[] = {301, 132, 57, 23, 10, 4, 1};
-  for (int gi = 0; gi < 7; ++gi) {
-    const int gap = gaps[gi];
-    if (gap >= n) continue;
-    for (int i = gap; i < n; ++i) {
-      const int32_t v = a[i];
-      int j = i;
-      while (j >= gap && a[j - gap] > v) {
-        a[j] = a[j - gap];
-        j -= gap;
-      }
-      a[j] = v;
-    }
-  }
-}
-
 // pending boxes of the descent: at most the 26 colleagues plus 8 children per
 // level of depth (194), so the overflow check below never fires
 constexpr int kUWStack = 256;
@@ -837,8 +818,13 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
       P.box_prob.p, P.prob_geom.p, P.box_side.p, P.pl64.p, P.pl32.p);
   FMM_LAUNCH_CHECK();
 
-  // ---- colleagues
   scope.reset(new PassScope(P, kPassLists));
+  if (P.dual) {
+    build_dual_lists(P);
+    return;
+  }
+
+  // ---- colleagues
   DBuf<int32_t> &loff = P.s_i32b;
   loff.resize(P.level_off.size(), s);
   FMM_CUDA(cudaMemcpyAsync(loff.p, P.level_off.data(), sizeof(int32_t) * P.level_off.size(),

@@ -3,7 +3,7 @@
 // and keeps the fastest.  The balance it settles is the paper's compute-memory
 // trade-off inside the FMM (§1): larger leaves move work from the
 // translations (M2L) to the dense near field (P2P).  Results are cached per
-// (size bucket, order, precision) for the life of the process.
+// (size bucket, order, precision, list builder) for the life of the process.
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -21,13 +21,13 @@ __global__ void k_fill(int64_t n, double v, double *out) {
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int, double>, int> g_tune_cache;
 
 }  // namespace
 
 int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   const int bucket = n > 0 ? (int)std::floor(std::log2((double)n)) : 0;
-  const auto key = std::make_tuple(bucket, P.order, P.precision);
+  const auto key = std::make_tuple(bucket, P.order, P.precision, (int)P.dual, P.dual ? P.theta : 0.0);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
