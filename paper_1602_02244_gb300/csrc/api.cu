@@ -339,6 +339,10 @@ fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_
 
 fmm_status fmm_plan_sizes(fmm_plan_t plan, int64_t sizes[10]) {
   if (!plan || !sizes) return fail(FMM_ERR_INVALID_ARG, "plan or sizes is NULL");
+  if (!plan->v_built) {
+    fmm_status st = guarded([&] { build_vlists(*plan); });
+    if (st != FMM_OK) return st;
+  }
   sizes[0] = plan->n;
   sizes[1] = plan->nboxes;
   sizes[2] = plan->nlevels;
@@ -354,6 +358,10 @@ fmm_status fmm_plan_sizes(fmm_plan_t plan, int64_t sizes[10]) {
 
 fmm_status fmm_plan_export(fmm_plan_t plan, int which, void *h_dst, size_t bytes) {
   if (!plan) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
+  if (!plan->v_built && (which == 12 || which == 13)) {
+    fmm_status st = guarded([&] { build_vlists(*plan); });
+    if (st != FMM_OK) return st;
+  }
   const fmm_plan_impl &P = *plan;
   const void *src = nullptr;
   size_t want = 0;

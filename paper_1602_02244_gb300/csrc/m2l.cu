@@ -124,12 +124,17 @@ void run(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *order, cons
 
 // ------------------------------------------------------ plan-time tables
 // One CTA per tile: src[tile][slot][t] = source box of target t in that slot
-// (-1 if none) and the ascending list of occupied slots.
+// (-1 if none) and the ascending list of occupied slots.  The sources of
+// target B are its V list, taken straight from its definition: the children
+// of the colleagues of parent(B) that are not adjacent to B (same level, so
+// adjacency is a Chebyshev distance of at most 1).  The V-list CSR itself is
+// not needed on this path.
 __global__ void k_m2l_table(int tile_size, const M2LTile *__restrict__ tiles,
-                            const int32_t *__restrict__ order, const int32_t *__restrict__ voff,
-                            const int32_t *__restrict__ vidx, const BoxGeo *__restrict__ geo,
-                            int32_t *__restrict__ table, int16_t *__restrict__ slots,
-                            int32_t *__restrict__ nslots) {
+                            const int32_t *__restrict__ order, const int32_t *__restrict__ parent,
+                            const int32_t *__restrict__ child, const int32_t *__restrict__ nchild,
+                            const int32_t *__restrict__ col, const int32_t *__restrict__ ncol,
+                            const BoxGeo *__restrict__ geo, int32_t *__restrict__ table,
+                            int16_t *__restrict__ slots, int32_t *__restrict__ nslots) {
   __shared__ int32_t used[216];
   const M2LTile tile = tiles[blockIdx.x];
   int32_t *tab = table + (size_t)blockIdx.x * 216 * tile_size;
@@ -140,10 +145,16 @@ __global__ void k_m2l_table(int tile_size, const M2LTile *__restrict__ tiles,
   for (int t = threadIdx.x >> 5; t < tile.count; t += blockDim.x >> 5) {
     const int32_t B = order[tile.start + t];
     const BoxGeo gb = geo[B];
-    for (int32_t e = voff[B] + (threadIdx.x & 31); e < voff[B + 1]; e += 32) {
-      const int32_t A = vidx[e];
+    const int32_t P = parent[B];
+    const int nco = ncol[P];
+    for (int e = threadIdx.x & 31; e < 8 * nco; e += 32) {
+      const int32_t C = col[26 * (int64_t)P + (e >> 3)];
+      if ((e & 7) >= nchild[C]) continue;
+      const int32_t A = child[C] + (e & 7);
       const BoxGeo ga = geo[A];
-      const int sx = ga.ix - gb.ix + 2 + px, sy = ga.iy - gb.iy + 2 + py, sz = ga.iz - gb.iz + 2 + pz;
+      const int dx = ga.ix - gb.ix, dy = ga.iy - gb.iy, dz = ga.iz - gb.iz;
+      if (max(abs(dx), max(abs(dy), abs(dz))) <= 1) continue;  // adjacent: near field
+      const int sx = dx + 2 + px, sy = dy + 2 + py, sz = dz + 2 + pz;
       if ((unsigned)sx < 6u && (unsigned)sy < 6u && (unsigned)sz < 6u) {  // always, by construction
         const int slot = (sx * 6 + sy) * 6 + sz;
         tab[slot * tile_size + t] = A;
@@ -329,9 +340,10 @@ void build_m2l_tables(fmm_plan_impl &P) {
   P.m2l_src.resize((size_t)nt * 216 * P.m2l_tile_size, s);
   P.m2l_slots.resize((size_t)nt * 216, s);
   P.m2l_nslots.resize((size_t)nt, s);
-  k_m2l_table<<<(unsigned)nt, 256, 0, s>>>(P.m2l_tile_size, P.m2l_tiles.p, P.m2l_order.p, P.v_off.p,
-                                            P.v_idx.p, P.box_geo.p, P.m2l_src.p, P.m2l_slots.p,
-                                            P.m2l_nslots.p);
+  k_m2l_table<<<(unsigned)nt, 256, 0, s>>>(P.m2l_tile_size, P.m2l_tiles.p, P.m2l_order.p,
+                                            P.box_parent.p, P.box_child.p, P.box_nchild.p,
+                                            P.colleagues.p, P.ncolleagues.p, P.box_geo.p, P.m2l_src.p,
+                                            P.m2l_slots.p, P.m2l_nslots.p);
   FMM_LAUNCH_CHECK();
 }
 

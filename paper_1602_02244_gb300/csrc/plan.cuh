@@ -83,6 +83,7 @@ struct fmm_plan_impl {
   DBuf<int2> dt_a, dt_b, dt_m2l, dt_p2p;  // dual-tree walk: frontiers and pairs
   DBuf<unsigned long long> dt_cnt;
   int64_t nu = 0, nv = 0, nw = 0, nx = 0;
+  bool v_built = true;              // false: V is built on request (build_vlists)
 
   // work lists
   DBuf<int32_t> leaves;             // leaf boxes
@@ -182,6 +183,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n);
 void morton_keys_raw(const double *d_xyz, int64_t n, double *partial, double *geom, uint64_t *keys,
                      int32_t *perm, cudaStream_t s);
 void set_points(fmm_plan_impl &P, const double *d_xyz);
+// the V-list CSR of a plan whose M2L does not need it (on request; synchronous)
+void build_vlists(fmm_plan_impl &P);
 // dual.cu: cell radii, the dual-tree walk, and its M2L / P2P lists
 void build_dual_lists(fmm_plan_impl &P);
 // operators.cu

@@ -638,6 +638,26 @@ int64_t compact(fmm_plan_impl &P, int64_t n, const int32_t *flag, DBuf<int32_t> 
 
 }  // namespace
 
+void build_vlists(fmm_plan_impl &P) {
+  cudaStream_t s = P.stream;
+  const int64_t nb = P.nboxes;
+  P.v_built = true;
+  P.nv = 0;
+  if (nb == 0) return;
+  if (P.dual) return;  // a dual-tree plan keeps its M2L pairs in V
+  P.s_i32a.resize(nb, s);
+  k_vlist<false><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_child.p,
+                                          P.box_nchild.p, P.colleagues.p, P.ncolleagues.p,
+                                          P.s_i32a.p, nullptr, nullptr);
+  FMM_LAUNCH_CHECK();
+  P.nv = counts_to_offsets(P, P.s_i32a.p, P.v_off, nb);
+  P.v_idx.resize(P.nv > 0 ? P.nv : 1, s);
+  k_vlist<true><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_child.p,
+                                         P.box_nchild.p, P.colleagues.p, P.ncolleagues.p, nullptr,
+                                         P.v_off.p, P.v_idx.p);
+  FMM_LAUNCH_CHECK();
+}
+
 int32_t read_scalar(const int32_t *d, cudaStream_t s) {
   int32_t h = 0;
   FMM_CUDA(cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -679,6 +699,7 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   P.nlevels = 0;
   P.level_off.assign(1, 0);
   P.nu = P.nv = P.nw = P.nx = 0;
+  P.v_built = true;
   P.nleaves = P.nxboxes = P.nwleaves = P.nm2l_tiles = 0;
   if (n == 0) return;
   std::unique_ptr<PassScope> scope(new PassScope(P, kPassSort));
@@ -836,18 +857,11 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   FMM_LAUNCH_CHECK();
   FMM_CUDA(cudaStreamSynchronize(s));  // level_off host vector must outlive the copy
 
-  // ---- V lists
-  P.s_i32a.resize(nb, s);
-  k_vlist<false><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_child.p,
-                                          P.box_nchild.p, P.colleagues.p, P.ncolleagues.p,
-                                          P.s_i32a.p, nullptr, nullptr);
-  FMM_LAUNCH_CHECK();
-  P.nv = counts_to_offsets(P, P.s_i32a.p, P.v_off, nb);
-  P.v_idx.resize(P.nv > 0 ? P.nv : 1, s);
-  k_vlist<true><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_child.p,
-                                         P.box_nchild.p, P.colleagues.p, P.ncolleagues.p, nullptr,
-                                         P.v_off.p, P.v_idx.p);
-  FMM_LAUNCH_CHECK();
+  // ---- V lists: the mixed-precision M2L of orders <= kM2LStagedMaxOrder reads
+  // its per-tile source table, built from the colleagues; the CSR is then
+  // built only on request (fmm_plan_sizes / fmm_plan_export)
+  P.v_built = false;
+  if (!(P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder)) build_vlists(P);
 
   // ---- coarser-or-equal adjacent leaves (CA)
   k_calist<false><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_nchild.p,

@@ -81,3 +81,13 @@ def test_full_size_plummer_4m_bit_exact(cuda):
     plan = gpu_plan(cuda, xyz, 64, order=8)
     compare(plan, oracle.Tree(xyz, 64))
     plan.close()
+
+
+def test_lists_of_a_mixed_plan_built_on_request(cuda):
+    """A mixed-precision plan of order <= 10 builds its M2L source table from
+    the colleagues and its V lists only when asked; both must equal the
+    oracle's."""
+    xyz = points("plummer", 30000)
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=24, order=8, precision="mixed")
+    compare(plan, oracle.Tree(xyz, 24))
+    plan.close()
