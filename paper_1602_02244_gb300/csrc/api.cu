@@ -138,7 +138,8 @@ void release_plan(fmm_plan_impl &P) {
   P.box_side.release(); P.prob_off.release(); P.prob_geom.release(); P.iperm.release();
   P.ops.m2m32t.release(); P.ops.l2l32t.release();
   P.radius.release(); P.dt_a.release(); P.dt_b.release(); P.dt_m2l.release();
-  P.dt_p2p.release(); P.dt_cnt.release();
+  P.dt_p2p.release(); P.dt_cnt.release(); P.dt_toff.release(); P.dt_tidx.release();
+  P.dt_goff.release(); P.dt_gidx.release();
 }
 
 }  // namespace fmm

@@ -21,6 +21,7 @@
 // a depth-first walk.  M2L rows go to v_off/v_idx (sources of any level, for
 // every box) and P2P rows to u_off/u_idx; W and X are empty.
 #include "eval_kernels.cuh"
+#include "m2l_config.cuh"
 #include "sort.cuh"
 
 namespace fmm {
@@ -169,6 +170,43 @@ __global__ void k_row_sort(int64_t nb, const int32_t *__restrict__ off, int32_t 
   if (b < nb) sort_run(idx + off[b], off[b + 1] - off[b]);
 }
 
+// Split each M2L row into the pairs the fixed-offset operators of the M2L
+// tiles cover (same level, 2 <= max|d| <= 3, inside the 6x6x6 slot window of
+// the target's octant parity; the tensor-core path) and the rest, keeping
+// the ascending order of both.
+template <bool kFill>
+__global__ void k_dual_split(int64_t nb, const int32_t *__restrict__ off, const int32_t *__restrict__ idx,
+                             const BoxGeo *__restrict__ geo, int32_t *__restrict__ tcnt,
+                             int32_t *__restrict__ gcnt, const int32_t *__restrict__ toff,
+                             int32_t *__restrict__ tidx, const int32_t *__restrict__ goff,
+                             int32_t *__restrict__ gidx) {
+  const int64_t b = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (b >= nb) return;
+  const BoxGeo gt = geo[b];
+  const int px = gt.ix & 1, py = gt.iy & 1, pz = gt.iz & 1;
+  int32_t kt = 0, kg = 0;
+  for (int32_t e = off[b]; e < off[b + 1]; ++e) {
+    const int32_t S = idx[e];
+    const BoxGeo gs = geo[S];
+    const int dx = gs.ix - gt.ix, dy = gs.iy - gt.iy, dz = gs.iz - gt.iz;
+    const int cheb = max(abs(dx), max(abs(dy), abs(dz)));
+    const bool tc = gs.level == gt.level && gt.level >= 2 && cheb >= 2 && cheb <= 3 &&
+                    (unsigned)(dx + 2 + px) < 6u && (unsigned)(dy + 2 + py) < 6u &&
+                    (unsigned)(dz + 2 + pz) < 6u;
+    if (tc) {
+      if (kFill) tidx[toff[b] + kt] = S;
+      ++kt;
+    } else {
+      if (kFill) gidx[goff[b] + kg] = S;
+      ++kg;
+    }
+  }
+  if (!kFill) {
+    tcnt[b] = kt;
+    gcnt[b] = kg;
+  }
+}
+
 // CSR rows (nb + 1 offsets, sources ascending) from unordered (target,
 // source) pairs; returns the number of pairs
 int64_t pairs_to_rows(fmm_plan_impl &P, const int2 *pairs, int64_t np, DBuf<int32_t> &off,
@@ -232,7 +270,7 @@ __host__ __device__ constexpr int dual_pitch(int p) {
 template <typename T, int PT>
 __global__ void k_m2l_dual(int p_rt, const int32_t *__restrict__ off, const int32_t *__restrict__ idx,
                            const BoxGeo *__restrict__ geo, const T *__restrict__ M,
-                           T *__restrict__ L, int ld) {
+                           T *__restrict__ L, int ld, int accumulate) {
   extern __shared__ __align__(16) unsigned char dual_smem[];
   const int p = PT > 0 ? PT : p_rt;
   const int P2 = 2 * p, R = dual_pitch(p);  // I_j^i at (i + 2p) R + j
@@ -326,6 +364,10 @@ __global__ void k_m2l_dual(int p_rt, const int32_t *__restrict__ off, const int3
   }
   T *out = L + (int64_t)B * ld;
   if (act) {
+    if (accumulate) {
+      accr += out[cidx(on, om)];
+      if (om > 0) acci += out[cidx(on, -om)];
+    }
     out[cidx(on, om)] = accr;
     if (om > 0) out[cidx(on, -om)] = acci;
   }
@@ -406,12 +448,36 @@ void build_dual_lists(fmm_plan_impl &P) {
   }
   P.w_idx.resize(1, s);
   P.x_idx.resize(1, s);
+
+  // mixed precision, orders with fixed-offset M2L tiles: the pairs those
+  // tiles cover run there (tensor cores), the rest in the per-pair kernel
+  P.ndt_t = P.ndt_g = 0;
+  if (P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder) {
+    P.s_i32a.resize(nb, s);
+    P.s_i32b.resize(nb, s);
+    k_dual_split<false><<<grid(nb), kT, 0, s>>>(nb, P.v_off.p, P.v_idx.p, P.box_geo.p, P.s_i32a.p,
+                                                P.s_i32b.p, nullptr, nullptr, nullptr, nullptr);
+    FMM_LAUNCH_CHECK();
+    P.dt_toff.resize(nb + 1, s);
+    P.dt_goff.resize(nb + 1, s);
+    scan_exclusive(P.s_i32a.p, P.dt_toff.p, nb, P.dt_toff.p + nb, P.s_scan, s);
+    scan_exclusive(P.s_i32b.p, P.dt_goff.p, nb, P.dt_goff.p + nb, P.s_scan, s);
+    P.ndt_t = read_scalar(P.dt_toff.p + nb, s);
+    P.ndt_g = read_scalar(P.dt_goff.p + nb, s);
+    P.dt_tidx.resize(P.ndt_t > 0 ? P.ndt_t : 1, s);
+    P.dt_gidx.resize(P.ndt_g > 0 ? P.ndt_g : 1, s);
+    k_dual_split<true><<<grid(nb), kT, 0, s>>>(nb, P.v_off.p, P.v_idx.p, P.box_geo.p, nullptr,
+                                               nullptr, P.dt_toff.p, P.dt_tidx.p, P.dt_goff.p,
+                                               P.dt_gidx.p);
+    FMM_LAUNCH_CHECK();
+    build_m2l_tiles(P);
+  }
   FMM_CUDA(cudaStreamSynchronize(s));  // `roots` is a host temporary
 }
 
 template <typename T>
 void launch_m2l_dual(int p, int64_t nb, const int32_t *off, const int32_t *idx, const BoxGeo *geo,
-                     const T *M, T *L, cudaStream_t s) {
+                     const T *M, T *L, bool accumulate, cudaStream_t s) {
   if (nb <= 0) return;
   const int nout = (p + 1) * (p + 2) / 2;
   const int threads = std::max(64, (nout + 31) / 32 * 32);
@@ -419,7 +485,7 @@ void launch_m2l_dual(int p, int64_t nb, const int32_t *off, const int32_t *idx, 
   const size_t smem = sizeof(T) * (2 * nI + (size_t)(p + 1) * (p + 1));
   auto go = [&](auto kern) {
     if (smem > 48 * 1024) FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)nb, threads, smem, s>>>(p, off, idx, geo, M, L, coef_pitch(p));
+    kern<<<(unsigned)nb, threads, smem, s>>>(p, off, idx, geo, M, L, coef_pitch(p), accumulate ? 1 : 0);
   };
   switch (p) {
     case 4: go(k_m2l_dual<T, 4>); break;
@@ -432,8 +498,8 @@ void launch_m2l_dual(int p, int64_t nb, const int32_t *off, const int32_t *idx, 
 }
 
 template void launch_m2l_dual<double>(int, int64_t, const int32_t *, const int32_t *, const BoxGeo *,
-                                      const double *, double *, cudaStream_t);
+                                      const double *, double *, bool, cudaStream_t);
 template void launch_m2l_dual<float>(int, int64_t, const int32_t *, const int32_t *, const BoxGeo *,
-                                     const float *, float *, cudaStream_t);
+                                     const float *, float *, bool, cudaStream_t);
 
 }  // namespace fmm

@@ -56,7 +56,8 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   {
     PassScope ps_(P, kPassM2L);
     if (P.dual)
-      launch_m2l_dual<double>(p, P.nboxes, P.v_off.p, P.v_idx.p, P.box_geo.p, P.M64.p, P.L64.p, s);
+      launch_m2l_dual<double>(p, P.nboxes, P.v_off.p, P.v_idx.p, P.box_geo.p, P.M64.p, P.L64.p,
+                              false, s);
     else
       launch_m2l<double>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_order.p, P.v_off.p,
                          P.v_idx.p, P.box_geo.p, P.M64.p, P.ops.m2l64.p, P.L64.p, s);
@@ -129,8 +130,28 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   }
   {
     PassScope ps_(P, kPassM2L);
-    if (P.dual) {
-      launch_m2l_dual<float>(p, P.nboxes, P.v_off.p, P.v_idx.p, P.box_geo.p, P.M32.p, P.L32.p, s);
+    if (P.dual && p > kM2LStagedMaxOrder) {
+      launch_m2l_dual<float>(p, P.nboxes, P.v_off.p, P.v_idx.p, P.box_geo.p, P.M32.p, P.L32.p,
+                             false, s);
+    } else if (P.dual) {
+      // the pairs of the fixed-offset tiles on the tensor cores (they write L
+      // of every box of level >= 2), levels 0 and 1 cleared, then the rest
+      const size_t ldc = (size_t)coef_pitch(p);
+      const size_t b2 = (size_t)(P.nlevels > 2 ? P.level_off[2] : P.nboxes);
+      FMM_CUDA(cudaMemsetAsync(P.L32.p, 0, sizeof(float) * b2 * ldc, s));
+      if (P.m2l_tc) {
+        const size_t kt = m2l_tc_pitch(p);
+        P.Mhi.resize((size_t)P.nboxes * kt, s);
+        P.Mlo.resize((size_t)P.nboxes * kt, s);
+        launch_m2l_tc(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_src.p, P.m2l_slots.p, P.m2l_nslots.p,
+                      P.m2l_order.p, P.nboxes, P.M32.p, P.Mhi.p, P.Mlo.p, P.ops.m2l_tc.p, P.L32.p,
+                      P.dev_err.p, s);
+      } else {
+        launch_m2l_staged(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_src.p, P.m2l_slots.p,
+                          P.m2l_nslots.p, P.m2l_order.p, P.M32.p, P.ops.m2l32p.p, P.L32.p, s);
+      }
+      launch_m2l_dual<float>(p, P.nboxes, P.dt_goff.p, P.dt_gidx.p, P.box_geo.p, P.M32.p, P.L32.p,
+                             true, s);
     } else if (P.m2l_tc) {
       const size_t kt = m2l_tc_pitch(p);
       P.Mhi.resize((size_t)P.nboxes * kt, s);

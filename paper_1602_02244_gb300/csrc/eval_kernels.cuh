@@ -76,10 +76,10 @@ void launch_m2l_tc(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *t
                    cudaStream_t s);
 
 // dual.cu: M2L over the dual-tree pairs (cells of any two sizes); writes
-// L of every box (zero where its list is empty)
+// (or, with accumulate, adds to) L of every box
 template <typename T>
 void launch_m2l_dual(int p, int64_t nb, const int32_t *off, const int32_t *idx, const BoxGeo *geo,
-                     const T *M, T *L, cudaStream_t s);
+                     const T *M, T *L, bool accumulate, cudaStream_t s);
 
 // p2p.cu
 template <typename T>

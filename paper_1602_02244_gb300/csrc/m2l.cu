@@ -176,6 +176,48 @@ __global__ void k_m2l_table(int tile_size, const M2LTile *__restrict__ tiles,
   }
 }
 
+// The same table from explicit per-target source rows (CSR): the dual-tree
+// pairs that fall into the tile's offset window.
+__global__ void k_m2l_table_csr(int tile_size, const M2LTile *__restrict__ tiles,
+                                const int32_t *__restrict__ order, const int32_t *__restrict__ off,
+                                const int32_t *__restrict__ idx, const BoxGeo *__restrict__ geo,
+                                int32_t *__restrict__ table, int16_t *__restrict__ slots,
+                                int32_t *__restrict__ nslots) {
+  __shared__ int32_t used[216];
+  const M2LTile tile = tiles[blockIdx.x];
+  int32_t *tab = table + (size_t)blockIdx.x * 216 * tile_size;
+  for (int i = threadIdx.x; i < 216 * tile_size; i += blockDim.x) tab[i] = -1;
+  for (int i = threadIdx.x; i < 216; i += blockDim.x) used[i] = 0;
+  __syncthreads();
+  const int px = tile.parity & 1, py = (tile.parity >> 1) & 1, pz = (tile.parity >> 2) & 1;
+  for (int t = threadIdx.x >> 5; t < tile.count; t += blockDim.x >> 5) {
+    const int32_t B = order[tile.start + t];
+    const BoxGeo gb = geo[B];
+    for (int32_t e = off[B] + (threadIdx.x & 31); e < off[B + 1]; e += 32) {
+      const int32_t A = idx[e];
+      const BoxGeo ga = geo[A];
+      const int sx = ga.ix - gb.ix + 2 + px, sy = ga.iy - gb.iy + 2 + py, sz = ga.iz - gb.iz + 2 + pz;
+      if ((unsigned)sx < 6u && (unsigned)sy < 6u && (unsigned)sz < 6u) {  // always, by construction
+        const int slot = (sx * 6 + sy) * 6 + sz;
+        tab[slot * tile_size + t] = A;
+        used[slot] = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int base = 0;
+    for (int s0 = 0; s0 < 216; s0 += 32) {
+      const int sl = s0 + threadIdx.x;
+      const bool u = sl < 216 && used[sl];
+      const unsigned mask = __ballot_sync(0xffffffffu, u);
+      if (u) slots[(size_t)blockIdx.x * 216 + base + __popc(mask & ((1u << threadIdx.x) - 1u))] = (int16_t)sl;
+      base += __popc(mask);
+    }
+    if (threadIdx.x == 0) nslots[blockIdx.x] = base;
+  }
+}
+
 // ------------------------------------------------- staged FP32 M2L kernel
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -340,10 +382,15 @@ void build_m2l_tables(fmm_plan_impl &P) {
   P.m2l_src.resize((size_t)nt * 216 * P.m2l_tile_size, s);
   P.m2l_slots.resize((size_t)nt * 216, s);
   P.m2l_nslots.resize((size_t)nt, s);
-  k_m2l_table<<<(unsigned)nt, 256, 0, s>>>(P.m2l_tile_size, P.m2l_tiles.p, P.m2l_order.p,
-                                            P.box_parent.p, P.box_child.p, P.box_nchild.p,
-                                            P.colleagues.p, P.ncolleagues.p, P.box_geo.p, P.m2l_src.p,
-                                            P.m2l_slots.p, P.m2l_nslots.p);
+  if (P.dual)
+    k_m2l_table_csr<<<(unsigned)nt, 256, 0, s>>>(P.m2l_tile_size, P.m2l_tiles.p, P.m2l_order.p,
+                                                 P.dt_toff.p, P.dt_tidx.p, P.box_geo.p, P.m2l_src.p,
+                                                 P.m2l_slots.p, P.m2l_nslots.p);
+  else
+    k_m2l_table<<<(unsigned)nt, 256, 0, s>>>(P.m2l_tile_size, P.m2l_tiles.p, P.m2l_order.p,
+                                              P.box_parent.p, P.box_child.p, P.box_nchild.p,
+                                              P.colleagues.p, P.ncolleagues.p, P.box_geo.p,
+                                              P.m2l_src.p, P.m2l_slots.p, P.m2l_nslots.p);
   FMM_LAUNCH_CHECK();
 }
 

@@ -82,6 +82,10 @@ struct fmm_plan_impl {
   DBuf<double> radius;              // dual tree: max |x_j - c_B| over the box's points
   DBuf<int2> dt_a, dt_b, dt_m2l, dt_p2p;  // dual-tree walk: frontiers and pairs
   DBuf<unsigned long long> dt_cnt;
+  // dual tree, mixed precision: the M2L pairs split into those of the tensor-core
+  // tiles (same level, offset in the operator table) and the rest
+  DBuf<int32_t> dt_toff, dt_tidx, dt_goff, dt_gidx;
+  int64_t ndt_t = 0, ndt_g = 0;
   int64_t nu = 0, nv = 0, nw = 0, nx = 0;
   bool v_built = true;              // false: V is built on request (build_vlists)
 
@@ -185,6 +189,8 @@ void morton_keys_raw(const double *d_xyz, int64_t n, double *partial, double *ge
 void set_points(fmm_plan_impl &P, const double *d_xyz);
 // the V-list CSR of a plan whose M2L does not need it (on request; synchronous)
 void build_vlists(fmm_plan_impl &P);
+// M2L tiles of the boxes of level >= 2 and, in mixed precision, their source tables
+void build_m2l_tiles(fmm_plan_impl &P);
 // dual.cu: cell radii, the dual-tree walk, and its M2L / P2P lists
 void build_dual_lists(fmm_plan_impl &P);
 // operators.cu

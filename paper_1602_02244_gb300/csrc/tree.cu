@@ -638,6 +638,42 @@ int64_t compact(fmm_plan_impl &P, int64_t n, const int32_t *flag, DBuf<int32_t> 
 
 }  // namespace
 
+// M2L tiles: boxes of level >= 2 grouped by (level, octant parity), and for
+// the mixed-precision paths the per-tile source tables
+void build_m2l_tiles(fmm_plan_impl &P) {
+  cudaStream_t s = P.stream;
+  const int64_t nb = P.nboxes;
+  P.m2l_tc = P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder && P.m2l_path != 1;
+  P.m2l_tile_size = P.m2l_tc ? kM2LTensorTile : m2l_tile_size(P.order, P.precision);
+  int64_t b2 = P.nlevels > 2 ? P.level_off[2] : nb;
+  int64_t n2 = nb - b2;
+  if (n2 > 0) {
+    const int ncls = 8 * (kMaxDepth + 1);
+    P.s_hist.resize(ncls, s);
+    FMM_CUDA(cudaMemsetAsync(P.s_hist.p, 0, sizeof(int32_t) * ncls, s));
+    P.s_u64a.resize(n2, s);
+    P.m2l_order.resize(n2, s);
+    k_m2l_class<<<grid(n2), kT, 0, s>>>(b2, nb, P.box_geo.p, P.s_u64a.p, P.m2l_order.p, P.s_hist.p);
+    FMM_LAUNCH_CHECK();
+    std::vector<int32_t> h(ncls);
+    FMM_CUDA(cudaMemcpyAsync(h.data(), P.s_hist.p, sizeof(int32_t) * ncls, cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
+    radix_sort(P.s_u64a, P.m2l_order, P.s_u64b, P.s_i32a, n2, {0}, P.s_hist, P.s_scan, s);
+    std::vector<M2LTile> tiles;
+    int32_t o = 0, T = P.m2l_tile_size;
+    for (int c = 0; c < ncls; ++c) {
+      for (int32_t t = 0; t < h[c]; t += T) tiles.push_back({o + t, std::min(T, h[c] - t), c & 7, 0});
+      o += h[c];
+    }
+    P.nm2l_tiles = (int64_t)tiles.size();
+    P.m2l_tiles.resize(tiles.size(), s);
+    FMM_CUDA(cudaMemcpyAsync(P.m2l_tiles.p, tiles.data(), sizeof(M2LTile) * tiles.size(),
+                             cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaStreamSynchronize(s));  // `tiles` is a host temporary
+    if (P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder) build_m2l_tables(P);
+  }
+}
+
 void build_vlists(fmm_plan_impl &P) {
   cudaStream_t s = P.stream;
   const int64_t nb = P.nboxes;
@@ -929,36 +965,7 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   FMM_LAUNCH_CHECK();
   P.nwleaves = compact(P, nb, P.s_i32a.p, P.wleaves);
 
-  // ---- M2L tiles: boxes of level >= 2 grouped by (level, octant parity)
-  P.m2l_tc = P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder && P.m2l_path != 1;
-  P.m2l_tile_size = P.m2l_tc ? kM2LTensorTile : m2l_tile_size(P.order, P.precision);
-  int64_t b2 = P.nlevels > 2 ? P.level_off[2] : nb;
-  int64_t n2 = nb - b2;
-  if (n2 > 0) {
-    const int ncls = 8 * (kMaxDepth + 1);
-    P.s_hist.resize(ncls, s);
-    FMM_CUDA(cudaMemsetAsync(P.s_hist.p, 0, sizeof(int32_t) * ncls, s));
-    P.s_u64a.resize(n2, s);
-    P.m2l_order.resize(n2, s);
-    k_m2l_class<<<grid(n2), kT, 0, s>>>(b2, nb, P.box_geo.p, P.s_u64a.p, P.m2l_order.p, P.s_hist.p);
-    FMM_LAUNCH_CHECK();
-    std::vector<int32_t> h(ncls);
-    FMM_CUDA(cudaMemcpyAsync(h.data(), P.s_hist.p, sizeof(int32_t) * ncls, cudaMemcpyDeviceToHost, s));
-    FMM_CUDA(cudaStreamSynchronize(s));
-    radix_sort(P.s_u64a, P.m2l_order, P.s_u64b, P.s_i32a, n2, {0}, P.s_hist, P.s_scan, s);
-    std::vector<M2LTile> tiles;
-    int32_t o = 0, T = P.m2l_tile_size;
-    for (int c = 0; c < ncls; ++c) {
-      for (int32_t t = 0; t < h[c]; t += T) tiles.push_back({o + t, std::min(T, h[c] - t), c & 7, 0});
-      o += h[c];
-    }
-    P.nm2l_tiles = (int64_t)tiles.size();
-    P.m2l_tiles.resize(tiles.size(), s);
-    FMM_CUDA(cudaMemcpyAsync(P.m2l_tiles.p, tiles.data(), sizeof(M2LTile) * tiles.size(),
-                             cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaStreamSynchronize(s));  // `tiles` is a host temporary
-    if (P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder) build_m2l_tables(P);
-  }
+  build_m2l_tiles(P);
 }
 
 }  // namespace fmm

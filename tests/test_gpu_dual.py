@@ -89,8 +89,10 @@ def test_mixed_vs_fp64_oracle(cuda, kind, n, S, p, theta):
     phi, g = phi.cpu().numpy(), g.cpu().numpy()
     plan.close()
     po, go = oracle.Dual(oracle.Tree(xyz, S), theta).eval(p, q)
-    assert rel(phi, po) <= 2e-6
-    assert rel(g, go) <= 2e-5
+    # FP32 arithmetic; the pairs inside the fixed-offset tiles run on the
+    # tensor cores (three-product TF32 split), the rest on the CUDA cores
+    assert rel(phi, po) <= 5e-6
+    assert rel(g, go) <= 5e-5
 
 
 def test_tiny_theta_is_the_direct_sum(cuda):
