@@ -68,7 +68,13 @@ typedef struct {
   int max_depth;          /* deepest level, 1..21; 0 = default (21)           */
   int m2l_path;           /* MIXED, order <= 10: 0 = default (tensor cores),
                              1 = FP32 CUDA cores, 2 = tensor cores (tcgen05,
-                             three-product TF32 split)                        */
+                             three-product TF32 split);
+                             3 = rotated operators, either precision, order
+                             <= 12: rotate each multipole onto the offset
+                             axis, translate along it, rotate back
+                             (O(p^3) per pair instead of O(p^4)).
+                             FP64, order <= 12: the default is 3 (0 and 3
+                             both select it; 1 and 2 the dense operator)      */
   int interaction;        /* how boxes are paired (§2.1):
                              0 = U/V/W/X lists of the adaptive octree (default);
                              1 = dual-tree walk with the multipole acceptance

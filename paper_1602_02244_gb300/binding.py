@@ -126,7 +126,7 @@ class Plan:
         opts.precision = {"fp64": FMM_FP64, "mixed": FMM_MIXED}[precision]
         opts.coarse_fp64_levels = coarse_fp64_levels
         opts.max_depth = max_depth
-        opts.m2l_path = {"auto": 0, "simt": 1, "tensor": 2}[m2l_path]
+        opts.m2l_path = {"auto": 0, "simt": 1, "tensor": 2, "rotation": 3}[m2l_path]
         opts.interaction = {"lists": 0, "dual": 1}[interaction]
         opts.mac_theta = float(theta)
         self.interaction = interaction

@@ -65,8 +65,8 @@ void check_opts(const fmm_opts *o) {
     throw Error(FMM_ERR_INVALID_ARG, "opts.precision must be FMM_FP64 or FMM_MIXED");
   if (o->max_depth < 0 || o->max_depth > kMaxDepth)
     throw Error(FMM_ERR_INVALID_ARG, "opts.max_depth must be in 0..21");
-  if (o->m2l_path < 0 || o->m2l_path > 2)
-    throw Error(FMM_ERR_INVALID_ARG, "opts.m2l_path must be 0, 1 or 2");
+  if (o->m2l_path < 0 || o->m2l_path > 3)
+    throw Error(FMM_ERR_INVALID_ARG, "opts.m2l_path must be 0, 1, 2 or 3");
   if (o->interaction < 0 || o->interaction > 1)
     throw Error(FMM_ERR_INVALID_ARG, "opts.interaction must be 0 or 1");
   if (!(o->mac_theta >= 0.0 && o->mac_theta < 1.0))

@@ -58,6 +58,10 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
     if (P.dual)
       launch_m2l_dual<double>(p, P.nboxes, P.v_off.p, P.v_idx.p, P.box_geo.p, P.M64.p, P.L64.p,
                               false, s);
+    else if (P.m2l_rot)
+      launch_m2l_rot<double>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_src.p,
+                             P.m2l_slots.p, P.m2l_nslots.p, P.m2l_order.p, P.M64.p, P.ops.rot64.p,
+                             P.ops.zt64.p, P.L64.p, s);
     else
       launch_m2l<double>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_order.p, P.v_off.p,
                          P.v_idx.p, P.box_geo.p, P.M64.p, P.ops.m2l64.p, P.L64.p, s);
@@ -152,6 +156,10 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
       }
       launch_m2l_dual<float>(p, P.nboxes, P.dt_goff.p, P.dt_gidx.p, P.box_geo.p, P.M32.p, P.L32.p,
                              true, s);
+    } else if (P.m2l_rot) {
+      launch_m2l_rot<float>(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_tile_size, P.m2l_src.p,
+                            P.m2l_slots.p, P.m2l_nslots.p, P.m2l_order.p, P.M32.p, P.ops.rot32.p,
+                            P.ops.zt32.p, P.L32.p, s);
     } else if (P.m2l_tc) {
       const size_t kt = m2l_tc_pitch(p);
       P.Mhi.resize((size_t)P.nboxes * kt, s);
@@ -215,6 +223,7 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
 void eval_fmm(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad) {
   if (P.n == 0) return;
   build_operators(P);
+  build_rotation(P);
   if (!P.dev_err.p) {
     P.dev_err.resize(1, P.stream);
     FMM_CUDA(cudaMemsetAsync(P.dev_err.p, 0, sizeof(int), P.stream));

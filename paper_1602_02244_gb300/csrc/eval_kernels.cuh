@@ -64,6 +64,12 @@ void launch_m2l(int p, int64_t ntiles, const M2LTile *tiles, int tile, const int
                 const int32_t *voff, const int32_t *vidx, const BoxGeo *geo, const T *M,
                 const T *ops, T *L, cudaStream_t s);
 
+// rotated M2L over the per-tile source tables (any order up to kRotMaxOrder)
+template <typename T>
+void launch_m2l_rot(int p, int64_t ntiles, const M2LTile *tiles, int tile_size, const int32_t *table,
+                    const int16_t *slots, const int32_t *nslots, const int32_t *order, const T *M,
+                    const T *rot, const T *zt, T *L, cudaStream_t s);
+
 void launch_m2l_staged(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *table,
                        const int16_t *slots, const int32_t *nslots, const int32_t *order,
                        const float *M, const float *opsp, float *L, cudaStream_t s);

@@ -218,6 +218,103 @@ __global__ void k_m2l_table_csr(int tile_size, const M2LTile *__restrict__ tiles
   }
 }
 
+// ------------------------------------------------------------ rotated M2L
+// Per tile (targets of one level and octant parity) and occupied slot: the
+// sources' multipoles are staged, rotated so that the slot's offset lies on
+// the z axis (block-diagonal by degree), translated along z (only equal
+// orders couple), rotated back and added to the targets' locals.  The
+// targets go through in groups of TT so that three TT x (p+1)^2 buffers fit
+// in shared memory; every thread keeps up to kRotItems local coefficients of
+// the group in registers across the slots.  2(p+1)(2p+1)(2p+3)/3 + ~(p+1)^3/3
+// multiply-adds per pair against (p+1)^4 for the dense operator.
+constexpr int kRotThreads = 256;
+constexpr int kRotItems = 16;
+
+__device__ __forceinline__ int rot_degree(int k) {
+  int n = (int)sqrtf((float)k);
+  while (n * n > k) --n;
+  while ((n + 1) * (n + 1) <= k) ++n;
+  return n;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRotThreads)
+    k_m2l_rot(int p, int TT, int tile_size, const M2LTile *__restrict__ tiles,
+              const int32_t *__restrict__ table, const int16_t *__restrict__ slots,
+              const int32_t *__restrict__ nslots, const int32_t *__restrict__ order,
+              const T *__restrict__ M, const T *__restrict__ rot, const T *__restrict__ zt,
+              T *__restrict__ L) {
+  extern __shared__ __align__(16) unsigned char rot_smem[];
+  const int nc = (p + 1) * (p + 1), ld = coef_pitch(p), P1 = p + 1;
+  const size_t nrot = (size_t)(p + 1) * (2 * p + 1) * (2 * p + 3) / 3;
+  T *Ms = reinterpret_cast<T *>(rot_smem), *Mb = Ms + TT * nc, *Lb = Mb + TT * nc;
+  const M2LTile tile = tiles[blockIdx.x];
+  const int px = tile.parity & 1, py = (tile.parity >> 1) & 1, pz = (tile.parity >> 2) & 1;
+  const int32_t *tab = table + (size_t)blockIdx.x * 216 * tile_size;
+  const int16_t *sl = slots + (size_t)blockIdx.x * 216;
+  const int ns = nslots[blockIdx.x];
+  const int tid = threadIdx.x, items = TT * nc;
+  for (int t0 = 0; t0 < tile.count; t0 += TT) {
+    const int tc = min(TT, tile.count - t0);
+    T acc[kRotItems];
+#pragma unroll
+    for (int q = 0; q < kRotItems; ++q) acc[q] = T(0);
+    for (int j = 0; j < ns; ++j) {
+      const int slot = sl[j];
+      const int sx = slot / 36, sy = (slot / 6) % 6, sz = slot % 6;
+      const int code = (2 + px - sx + 3) * 49 + (2 + py - sy + 3) * 7 + (2 + pz - sz + 3);
+      const T *Dm = rot + (size_t)code * 2 * nrot, *Dl = Dm + nrot;
+      const T *z = zt + (size_t)code * P1 * P1;
+      __syncthreads();  // the previous slot's buffers are consumed
+      for (int i = tid; i < items; i += kRotThreads) {
+        const int t = i / nc, k = i - t * nc;
+        const int32_t S = t < tc ? tab[(size_t)slot * tile_size + t0 + t] : -1;
+        Ms[i] = S >= 0 ? M[(int64_t)S * ld + k] : T(0);
+      }
+      __syncthreads();
+      for (int i = tid; i < items; i += kRotThreads) {  // M' = A M, degree by degree
+        const int t = i / nc, k = i - t * nc, n = rot_degree(k), w = 2 * n + 1;
+        const T *row = Dm + (size_t)n * (2 * n - 1) * (2 * n + 1) / 3 + (size_t)(k - n * n) * w;
+        const T *x = Ms + t * nc + n * n;
+        T s = T(0);
+        for (int c = 0; c < w; ++c) s += row[c] * x[c];
+        Mb[i] = s;
+      }
+      __syncthreads();
+      for (int i = tid; i < items; i += kRotThreads) {  // translation along z
+        const int t = i / nc, k = i - t * nc, n = rot_degree(k), mm = k - n * n - n;
+        const int am = mm < 0 ? -mm : mm;
+        const T *zr = z + n * P1;
+        const T *x = Mb + t * nc;
+        T s = T(0);
+        for (int kk = am; kk <= p; ++kk) s += zr[kk] * x[kk * kk + kk + mm];
+        Lb[i] = ((n + am) & 1) ? -s : s;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kRotItems; ++q) {  // L += B L', into the owned coefficients
+        const int i = tid + q * kRotThreads;
+        if (i < items) {
+          const int t = i / nc, k = i - t * nc, n = rot_degree(k), w = 2 * n + 1;
+          const T *row = Dl + (size_t)n * (2 * n - 1) * (2 * n + 1) / 3 + (size_t)(k - n * n) * w;
+          const T *x = Lb + t * nc + n * n;
+          T s = T(0);
+          for (int c = 0; c < w; ++c) s += row[c] * x[c];
+          acc[q] += s;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kRotItems; ++q) {
+      const int i = tid + q * kRotThreads;
+      if (i < items) {
+        const int t = i / nc, k = i - t * nc;
+        if (t < tc) L[(int64_t)order[tile.start + t0 + t] * ld + k] = acc[q];
+      }
+    }
+  }
+}
+
 // ------------------------------------------------- staged FP32 M2L kernel
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -393,6 +490,29 @@ void build_m2l_tables(fmm_plan_impl &P) {
                                               P.m2l_src.p, P.m2l_slots.p, P.m2l_nslots.p);
   FMM_LAUNCH_CHECK();
 }
+
+template <typename T>
+void launch_m2l_rot(int p, int64_t ntiles, const M2LTile *tiles, int tile_size, const int32_t *table,
+                    const int16_t *slots, const int32_t *nslots, const int32_t *order, const T *M,
+                    const T *rot, const T *zt, T *L, cudaStream_t s) {
+  if (ntiles == 0) return;
+  const int nc = ncoef(p);
+  const int TT = std::min(32, kRotThreads * kRotItems / nc);
+  const size_t smem = sizeof(T) * 3 * (size_t)TT * nc;
+  if (smem > 48 * 1024)
+    FMM_CUDA(cudaFuncSetAttribute(k_m2l_rot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_m2l_rot<T><<<(unsigned)ntiles, kRotThreads, smem, s>>>(p, TT, tile_size, tiles, table, slots,
+                                                            nslots, order, M, rot, zt, L);
+  FMM_LAUNCH_CHECK();
+}
+
+template void launch_m2l_rot<double>(int, int64_t, const M2LTile *, int, const int32_t *,
+                                     const int16_t *, const int32_t *, const int32_t *,
+                                     const double *, const double *, const double *, double *,
+                                     cudaStream_t);
+template void launch_m2l_rot<float>(int, int64_t, const M2LTile *, int, const int32_t *,
+                                    const int16_t *, const int32_t *, const int32_t *, const float *,
+                                    const float *, const float *, float *, cudaStream_t);
 
 template void launch_m2l<float>(int, int64_t, const M2LTile *, int, const int32_t *, const int32_t *,
                                 const int32_t *, const BoxGeo *, const float *, const float *, float *,

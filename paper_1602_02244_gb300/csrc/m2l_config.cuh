@@ -36,6 +36,8 @@ constexpr int kM2LTensorTile = 128;  // targets per CTA of the tensor-core path 
 // Staged FP32 kernel (orders up to 10): 64 targets x 16*RPT rows per CTA,
 // one whole slot (operator + gathered multipoles) per pipeline stage.
 constexpr int kM2LStagedMaxOrder = 10;
+// rotated M2L: orders whose rotation tables are built at plan time
+constexpr int kRotMaxOrder = 12;
 __host__ __device__ constexpr int m2l_rows(int order) { return (ncoef(order) + 15) / 16 * 16; }
 
 }  // namespace fmm

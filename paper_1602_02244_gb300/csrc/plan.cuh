@@ -26,6 +26,14 @@ struct Operators {
   DBuf<float> m2l32p;
   // tensor-core M2L: TF32 hi/lo halves in the MMA's core-matrix order
   DBuf<float> m2l_tc;
+  // rotated M2L (built when a plan uses it): per offset code, the real
+  // block-diagonal rotation taking the offset to the z axis, applied to the
+  // multipole (rot[code][0]) and back to the local (rot[code][1]), each
+  // sum_n (2n+1)^2 entries, block n at n(2n-1)(2n+1)/3, row-major [out][in];
+  // and the z-axis translation zt[code][n][k] = (n+k)! / |d|^(n+k+1)
+  int rot_order = -1;
+  DBuf<double> rot64, zt64;
+  DBuf<float> rot32, zt32;
 };
 
 // passes timed by the optional profiler (fmm_profile / fmm_profile_read)
@@ -36,7 +44,8 @@ uint64_t launch_count();
 
 struct fmm_plan_impl {
   // configuration
-  int m2l_path = 0;                  // 0 auto, 1 CUDA cores, 2 tensor cores
+  int m2l_path = 0;                  // 0 auto, 1 CUDA cores, 2 tensor cores, 3 rotated
+  bool m2l_rot = false;              // this plan's M2L uses the rotated operators
   bool dual = false;                 // lists from the dual-tree walk (else U/V/W/X)
   double theta = 0.5;                // dual tree: acceptance r_T + r_S < theta |c_T - c_S|
   bool m2l_tc = false;               // this plan's M2L runs on the tensor cores
@@ -195,6 +204,9 @@ void build_m2l_tiles(fmm_plan_impl &P);
 void build_dual_lists(fmm_plan_impl &P);
 // operators.cu
 void build_operators(fmm_plan_impl &P);
+// rotated M2L tables (operators.cu); a no-op unless P.m2l_rot
+void build_rotation(fmm_plan_impl &P);
+size_t rotation_entries(int p);  // sum_n (2n+1)^2 over n <= p
 // m2l.cu
 void build_m2l_tables(fmm_plan_impl &P);
 // m2l_tc.cu

@@ -638,12 +638,23 @@ int64_t compact(fmm_plan_impl &P, int64_t n, const int32_t *flag, DBuf<int32_t> 
 
 }  // namespace
 
+// Rotated M2L: on request (m2l_path 3), and by default in FP64 up to
+// kRotMaxOrder, where it runs 1.7-2x faster than the dense FP64 operator
+// (FP64 multiply-adds are scarce on this GPU); the FP32 paths keep the
+// dense operators (tensor cores up to order 10, CUDA cores above).
+bool uses_rotation(const fmm_plan_impl &P) {
+  if (P.dual || P.order > kRotMaxOrder) return false;
+  return P.m2l_path == 3 || (P.m2l_path == 0 && P.precision == FMM_FP64);
+}
+
 // M2L tiles: boxes of level >= 2 grouped by (level, octant parity), and for
 // the mixed-precision paths the per-tile source tables
 void build_m2l_tiles(fmm_plan_impl &P) {
   cudaStream_t s = P.stream;
   const int64_t nb = P.nboxes;
-  P.m2l_tc = P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder && P.m2l_path != 1;
+  P.m2l_tc = P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder && P.m2l_path != 1 &&
+             P.m2l_path != 3;
+  P.m2l_rot = uses_rotation(P);
   P.m2l_tile_size = P.m2l_tc ? kM2LTensorTile : m2l_tile_size(P.order, P.precision);
   int64_t b2 = P.nlevels > 2 ? P.level_off[2] : nb;
   int64_t n2 = nb - b2;
@@ -670,7 +681,8 @@ void build_m2l_tiles(fmm_plan_impl &P) {
     FMM_CUDA(cudaMemcpyAsync(P.m2l_tiles.p, tiles.data(), sizeof(M2LTile) * tiles.size(),
                              cudaMemcpyHostToDevice, s));
     FMM_CUDA(cudaStreamSynchronize(s));  // `tiles` is a host temporary
-    if (P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder) build_m2l_tables(P);
+    if ((P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder) || P.m2l_rot)
+      build_m2l_tables(P);
   }
 }
 
@@ -897,7 +909,9 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   // its per-tile source table, built from the colleagues; the CSR is then
   // built only on request (fmm_plan_sizes / fmm_plan_export)
   P.v_built = false;
-  if (!(P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder)) build_vlists(P);
+  const bool table_path =
+      (P.precision == FMM_MIXED && P.order <= kM2LStagedMaxOrder) || uses_rotation(P);
+  if (!table_path) build_vlists(P);
 
   // ---- coarser-or-equal adjacent leaves (CA)
   k_calist<false><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_nchild.p,
