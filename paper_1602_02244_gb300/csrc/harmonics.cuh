@@ -95,6 +95,41 @@ __device__ __forceinline__ void irregular_stream(int p, T x, T y, T z, F &&f) {
   }
 }
 
+// The regular stream for two points at once (the .x and .y halves), on the
+// paired FP32 instructions: the same recurrence as regular_stream.
+template <typename F>
+__device__ __forceinline__ void regular_stream2(int p, float2 x, float2 y, float2 z, F &&f) {
+  const float2 r2 = __ffma2_rn(z, z, __ffma2_rn(y, y, __fmul2_rn(x, x)));
+  const float2 nr2 = make_float2(-r2.x, -r2.y);
+  const float2 ny = make_float2(-y.x, -y.y);
+  float2 dre = make_float2(1.f, 1.f), dim = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m <= p; ++m) {
+    if (m > 0) {
+      const float cm = -0.5f / (float)m;
+      const float2 c = make_float2(cm, cm);
+      const float2 t1 = __ffma2_rn(ny, dim, __fmul2_rn(x, dre));  // x dre - y dim
+      const float2 t2 = __ffma2_rn(y, dre, __fmul2_rn(x, dim));   // x dim + y dre
+      dre = __fmul2_rn(c, t1);
+      dim = __fmul2_rn(c, t2);
+    }
+    f(m, m, dre, dim);
+    float2 pre = make_float2(0.f, 0.f), pim = make_float2(0.f, 0.f), cre = dre, cim = dim;
+#pragma unroll
+    for (int n = m + 1; n <= p; ++n) {
+      const float an = (float)(2 * n - 1), sn = recip_nm<float>(n, m);
+      const float2 a = __fmul2_rn(make_float2(an, an), z), s = make_float2(sn, sn);
+      const float2 nre = __fmul2_rn(__ffma2_rn(nr2, pre, __fmul2_rn(a, cre)), s);
+      const float2 nim = __fmul2_rn(__ffma2_rn(nr2, pim, __fmul2_rn(a, cim)), s);
+      pre = cre;
+      pim = cim;
+      cre = nre;
+      cim = nim;
+      f(n, m, cre, cim);
+    }
+  }
+}
+
 // The irregular stream for two points at once (the .x and .y halves), on the
 // paired FP32 instructions: the same recurrence as irregular_stream, two
 // evaluations per instruction.  The reciprocal and reciprocal square root of

@@ -442,6 +442,96 @@ __global__ void k_l2p(int p_rt, const int32_t *__restrict__ leaves, const int32_
   }
 }
 
+// FP32 L2P, two targets per lane on the paired FP32 instructions.  As for
+// M2P below, the gradient is regrouped per regular harmonic: with
+// d/dz R_n^m = R_{n-1}^m, d/dx R_n^m = (R_{n-1}^{m+1} - R_{n-1}^{m-1})/2,
+// d/dy R_n^m = -i (R_{n-1}^{m-1} + R_{n-1}^{m+1})/2, the coefficient of R_n^m is
+//   Gz = L_{n+1}^m,  Gx = (L_{n+1}^{m-1} - L_{n+1}^{m+1})/2,
+//   Gy = -i (L_{n+1}^{m-1} + L_{n+1}^{m+1})/2,
+// so each warp folds its leaf's local into one 4-vector (L, Gx, Gy, Gz) per
+// real slot (the factor 2 of m > 0 and the sign of the imaginary slots
+// included), and the evaluation is four dot products sharing one stream.
+// One warp per leaf, no block-wide barriers.
+constexpr int kL2PWarps = 4;
+
+template <int PT>
+__global__ void __launch_bounds__(32 * kL2PWarps, 4)
+    k_l2p_f32x2(int p_rt, int64_t nleaves, const int32_t *__restrict__ leaves,
+                const int32_t *__restrict__ first, const int32_t *__restrict__ count,
+                const BoxGeo *__restrict__ geo, const float4 *__restrict__ src,
+                const double *__restrict__ side, const float *__restrict__ L,
+                double *__restrict__ far, int lfar) {
+  const int p = PT > 0 ? PT : p_rt;
+  extern __shared__ __align__(16) unsigned char l2p_smem[];
+  const int ld = coef_pitch(p), nc = ncoef(p);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t li = (int64_t)blockIdx.x * kL2PWarps + warp;
+  if (li >= nleaves) return;
+  float4 *K = reinterpret_cast<float4 *>(l2p_smem) + (size_t)warp * ld;
+  const int32_t b = leaves[li];
+  const BoxGeo g = geo[b];
+  const int32_t f = first[b], c = count[b];
+  Dbl4 *out = reinterpret_cast<Dbl4 *>(far);
+  if (g.level < lfar) {  // no far field reaches the levels above lfar
+    for (int32_t i = f + lane; i < f + c; i += 32) out[i] = make_dbl4(0.0, 0.0, 0.0, 0.0);
+    return;
+  }
+  const float *Lb = L + (int64_t)b * ld;
+  for (int r = lane; r < nc; r += 32) {
+    int n = (int)sqrtf((float)r);
+    while (n * n > r) --n;
+    while ((n + 1) * (n + 1) <= r) ++n;
+    const int mm = r - n * n - n, m = mm < 0 ? -mm : mm;
+    const bool im_part = mm < 0;
+    float ar, ai, br, bi, cr, ci;
+    cget(Lb, p, n, m, ar, ai);
+    const float k0 = im_part ? ai : ar;
+    cget(Lb, p, n + 1, m, ar, ai);
+    cget(Lb, p, n + 1, m - 1, br, bi);
+    cget(Lb, p, n + 1, m + 1, cr, ci);
+    const float kz = im_part ? ai : ar;
+    const float kx = 0.5f * (im_part ? (bi - ci) : (br - cr));
+    const float ky = im_part ? -0.5f * (br + cr) : 0.5f * (bi + ci);
+    const float w = m > 0 ? (im_part ? -2.f : 2.f) : 1.f;
+    K[r] = make_float4(w * k0, w * kx, w * ky, w * kz);
+  }
+  __syncwarp();
+  const double a = side[b], ia = 1.0 / a, ia2 = ia * ia;
+  const float inva = (float)ia;
+  for (int32_t tc = 0; tc < c; tc += 64) {
+    const int32_t i0 = f + tc + lane, i1 = i0 + 32;
+    const bool v0 = tc + lane < c, v1 = tc + lane + 32 < c;
+    const float4 s0 = v0 ? src[i0] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 s1 = v1 ? src[i1] : s0;
+    float2 fp = make_float2(0.f, 0.f), fx = fp, fy = fp, fz = fp;
+    regular_stream2(p, make_float2(s0.x * inva, s1.x * inva), make_float2(s0.y * inva, s1.y * inva),
+                    make_float2(s0.z * inva, s1.z * inva), [&](int nn, int m, float2 re, float2 im) {
+                      const float4 kp = K[cidx(nn, m)];
+                      fp.x = fmaf(kp.x, re.x, fp.x);
+                      fp.y = fmaf(kp.x, re.y, fp.y);
+                      fx.x = fmaf(kp.y, re.x, fx.x);
+                      fx.y = fmaf(kp.y, re.y, fx.y);
+                      fy.x = fmaf(kp.z, re.x, fy.x);
+                      fy.y = fmaf(kp.z, re.y, fy.y);
+                      fz.x = fmaf(kp.w, re.x, fz.x);
+                      fz.y = fmaf(kp.w, re.y, fz.y);
+                      if (m > 0) {
+                        const float4 kn = K[cidx(nn, -m)];
+                        fp.x = fmaf(kn.x, im.x, fp.x);
+                        fp.y = fmaf(kn.x, im.y, fp.y);
+                        fx.x = fmaf(kn.y, im.x, fx.x);
+                        fx.y = fmaf(kn.y, im.y, fx.y);
+                        fy.x = fmaf(kn.z, im.x, fy.x);
+                        fy.y = fmaf(kn.z, im.y, fy.y);
+                        fz.x = fmaf(kn.w, im.x, fz.x);
+                        fz.y = fmaf(kn.w, im.y, fz.y);
+                      }
+                    });
+    if (v0) out[i0] = make_dbl4((double)fp.x * ia, (double)fx.x * ia2, (double)fy.x * ia2, (double)fz.x * ia2);
+    if (v1) out[i1] = make_dbl4((double)fp.y * ia, (double)fx.y * ia2, (double)fy.y * ia2, (double)fz.y * ia2);
+  }
+}
+
 // M2P over W lists: phi += (1/a_A) sum M^ I(u), u = (x - c_A)/a_A.  The
 // gradient uses d/dz I_n^m = -I_{n+1}^m, d/dx I_n^m = (I_{n+1}^{m+1} - I_{n+1}^{m-1})/2,
 // d/dy I_n^m = -i (I_{n+1}^{m+1} + I_{n+1}^{m-1})/2; regrouped per I_n^m they are
@@ -902,11 +992,22 @@ void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *fi
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 const T *L, int64_t n, double *far, int lfar, cudaStream_t s) {
   if (nleaves == 0) return;
-  size_t sm = (size_t)ncoef(p) * sizeof(T);
-  with_order(p, [&](auto PC) {
-    k_l2p<T, decltype(PC)::value><<<(unsigned)nleaves, 64, sm, s>>>(p, leaves, first, count, geo, src,
-                                                                    side, L, n, far, lfar);
-  });
+  if constexpr (sizeof(T) == 4) {
+    const size_t sm = (size_t)kL2PWarps * coef_pitch(p) * sizeof(float4);
+    with_order(p, [&](auto PC) {
+      auto kern = k_l2p_f32x2<decltype(PC)::value>;
+      allow_smem(kern, sm);
+      kern<<<ceil_div(nleaves, kL2PWarps), 32 * kL2PWarps, sm, s>>>(
+          p, nleaves, leaves, first, count, geo, reinterpret_cast<const float4 *>(src), side, L,
+          far, lfar);
+    });
+  } else {
+    size_t sm = (size_t)ncoef(p) * sizeof(T);
+    with_order(p, [&](auto PC) {
+      k_l2p<T, decltype(PC)::value><<<(unsigned)nleaves, 64, sm, s>>>(p, leaves, first, count, geo,
+                                                                      src, side, L, n, far, lfar);
+    });
+  }
   FMM_LAUNCH_CHECK();
 }
 
