@@ -27,6 +27,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -96,7 +97,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+        # the raw samples; FMM_BENCH_CLOCKS_DIR keeps them, else a temporary directory
+        self.path = os.path.join(os.environ.get("FMM_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 "fmm_bench_clocks_rank%d.csv" % index)
 
     def start(self):
         try:

@@ -50,7 +50,7 @@ typedef enum {
   FMM_ERR_OOM = 3,             /* device allocation failed                    */
   FMM_ERR_TIMEOUT = 4,         /* a bounded device-side wait gave up          */
   FMM_ERR_NONFINITE_INPUT = 5, /* a coordinate is NaN or infinite             */
-  FMM_ERR_UNSUPPORTED = 6      /* valid request this build does not provide   */
+  FMM_ERR_UNSUPPORTED = 6      /* valid request the library does not provide  */
 } fmm_status;
 
 typedef enum {
