@@ -35,37 +35,65 @@ inline int grid(int64_t n) { return n > 0 ? ceil_div(n, kT) : 1; }
 // r_B^2 of every box: a warp per leaf walks the leaf's ancestors and takes
 // the max of |x_j - c_A|^2 over the leaf's points; every point of a box lies
 // in exactly one of its leaves.  Non-negative doubles order like their bit
-// patterns, so the max is an integer atomicMax.
+// patterns, so the max is an integer atomicMax.  FP64 arithmetic is scarce on
+// this GPU, so an FP32 pass over the leaf-local coordinates first bounds the
+// max; only points within a margin of it (far wider than the FP32 error of
+// |x - c_A|^2, about 1e-6 a_A^2) are evaluated in FP64, in the same operation
+// order as every other evaluation of the criterion.
 __global__ void k_box_radius2(int64_t nleaves, const int32_t *__restrict__ leaves,
                               const BoxGeo *__restrict__ geo, const int32_t *__restrict__ parent,
                               const int32_t *__restrict__ first, const int32_t *__restrict__ count,
-                              const double *__restrict__ xyz, const int32_t *__restrict__ bprob,
-                              const double *__restrict__ pgeom, const double *__restrict__ side,
-                              unsigned long long *__restrict__ r2bits) {
+                              const double *__restrict__ xyz, const float4 *__restrict__ pl32,
+                              const int32_t *__restrict__ bprob, const double *__restrict__ pgeom,
+                              const double *__restrict__ side, unsigned long long *__restrict__ r2bits) {
   const int lane = threadIdx.x & 31;
   const int64_t li = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (li >= nleaves) return;
   const int32_t B = leaves[li];
   const int32_t f = first[B], c = count[B];
   const double *lo = pgeom + 8 * (int64_t)bprob[B];
+  const BoxGeo gb = geo[B];
+  const double ab = side[B];
+  const double lomax = fmax(fabs(lo[0]), fmax(fabs(lo[1]), fabs(lo[2]))) + lo[3];
   for (int32_t A = B; A >= 0; A = parent[A]) {
     const BoxGeo g = geo[A];
     const double a = side[A];
+    // leaf centre - ancestor centre from the anchors (exact), then FP32
+    const float ox = (float)(((double)gb.ix + 0.5) * ab - ((double)g.ix + 0.5) * a);
+    const float oy = (float)(((double)gb.iy + 0.5) * ab - ((double)g.iy + 0.5) * a);
+    const float oz = (float)(((double)gb.iz + 0.5) * ab - ((double)g.iz + 0.5) * a);
+    float mf = 0.f;
+    for (int32_t j = f + lane; j < f + c; j += 32) {
+      const float4 v = pl32[j];
+      const float dx = v.x + ox, dy = v.y + oy, dz = v.z + oz;
+      mf = fmaxf(mf, dx * dx + dy * dy + dz * dz);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+    const double margin = 1e-5 * a * a + 1e-12 * lomax * lomax;
+    // a leaf whose bound cannot raise the box's current value skips it: most
+    // leaves under a coarse box do, so few of them reach the atomic
+    const double cur = __longlong_as_double((long long)__ldcg(&r2bits[A]));
+    if ((double)mf + margin < cur) continue;
+    const float cut = mf - (float)margin;
     // centre = lo + (anchor + 1/2) a: the product is exact, the sum rounds once
     const double cx = __dadd_rn(lo[0], ((double)g.ix + 0.5) * a);
     const double cy = __dadd_rn(lo[1], ((double)g.iy + 0.5) * a);
     const double cz = __dadd_rn(lo[2], ((double)g.iz + 0.5) * a);
     double m = 0.0;
     for (int32_t j = f + lane; j < f + c; j += 32) {
-      const double dx = __dsub_rn(xyz[3 * (int64_t)j], cx);
-      const double dy = __dsub_rn(xyz[3 * (int64_t)j + 1], cy);
-      const double dz = __dsub_rn(xyz[3 * (int64_t)j + 2], cz);
-      const double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      const float4 v = pl32[j];
+      const float dx = v.x + ox, dy = v.y + oy, dz = v.z + oz;
+      if (dx * dx + dy * dy + dz * dz < cut) continue;
+      const double ex = __dsub_rn(xyz[3 * (int64_t)j], cx);
+      const double ey = __dsub_rn(xyz[3 * (int64_t)j + 1], cy);
+      const double ez = __dsub_rn(xyz[3 * (int64_t)j + 2], cz);
+      const double s = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
       m = fmax(m, s);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) atomicMax(&r2bits[A], (unsigned long long)__double_as_longlong(m));
+    if (lane == 0 && m > cur) atomicMax(&r2bits[A], (unsigned long long)__double_as_longlong(m));
   }
 }
 
@@ -165,9 +193,45 @@ __global__ void k_row_fill(int64_t np, const int2 *__restrict__ pairs, const int
   idx[off[pr.x] + atomicAdd(&fill[pr.x], 1)] = pr.y;
 }
 
-__global__ void k_row_sort(int64_t nb, const int32_t *__restrict__ off, int32_t *__restrict__ idx) {
-  const int64_t b = (int64_t)blockIdx.x * kT + threadIdx.x;
-  if (b < nb) sort_run(idx + off[b], off[b + 1] - off[b]);
+// Sort every CSR row ascending: a warp per row, a bitonic network over the
+// row padded to a power of two in shared memory; the rare rows longer than
+// kRowSortMax are sorted in place by one thread.
+constexpr int kRowSortWarps = 4, kRowSortMax = 2048;
+
+__global__ void __launch_bounds__(32 * kRowSortWarps)
+    k_row_sort(int64_t nb, const int32_t *__restrict__ off, int32_t *__restrict__ idx) {
+  __shared__ int32_t buf_all[kRowSortWarps][kRowSortMax];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t *buf = buf_all[warp];
+  for (int64_t b = (int64_t)blockIdx.x * kRowSortWarps + warp; b < nb;
+       b += (int64_t)gridDim.x * kRowSortWarps) {
+    const int32_t o = off[b], n = off[b + 1] - o;
+    if (n < 2) continue;
+    if (n > kRowSortMax) {
+      if (lane == 0) sort_run(idx + o, n);
+      continue;
+    }
+    int P2 = 32;
+    while (P2 < n) P2 <<= 1;
+    for (int i = lane; i < P2; i += 32) buf[i] = i < n ? idx[o + i] : 0x7fffffff;
+    __syncwarp();
+    for (int k = 2; k <= P2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < P2; i += 32) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const int32_t x = buf[i], y = buf[ixj];
+            if (((i & k) == 0) == (x > y)) {
+              buf[i] = y;
+              buf[ixj] = x;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    for (int i = lane; i < n; i += 32) idx[o + i] = buf[i];
+    __syncwarp();
+  }
 }
 
 // Split each M2L row into the pairs the fixed-offset operators of the M2L
@@ -226,7 +290,8 @@ int64_t pairs_to_rows(fmm_plan_impl &P, const int2 *pairs, int64_t np, DBuf<int3
   if (np > 0) {
     k_row_fill<<<grid(np), kT, 0, s>>>(np, pairs, off.p, P.s_i32a.p, idx.p);
     FMM_LAUNCH_CHECK();
-    k_row_sort<<<grid(nb), kT, 0, s>>>(nb, off.p, idx.p);
+    k_row_sort<<<(unsigned)std::min<int64_t>(ceil_div(nb, (int64_t)kRowSortWarps), 152 * 16),
+                 32 * kRowSortWarps, 0, s>>>(nb, off.p, idx.p);
     FMM_LAUNCH_CHECK();
   }
   return np;
@@ -388,7 +453,7 @@ void build_dual_lists(fmm_plan_impl &P) {
   constexpr int kWarps = 8;
   k_box_radius2<<<(unsigned)ceil_div(P.nleaves, (int64_t)kWarps), 32 * kWarps, 0, s>>>(
       P.nleaves, P.leaves.p, P.box_geo.p, P.box_parent.p, P.box_first.p, P.box_count.p,
-      P.xyz_sorted.p, P.box_prob.p, P.prob_geom.p, P.box_side.p,
+      P.xyz_sorted.p, P.pl32.p, P.box_prob.p, P.prob_geom.p, P.box_side.p,
       reinterpret_cast<unsigned long long *>(r2.p));
   FMM_LAUNCH_CHECK();
   P.radius.resize(nb, s);
