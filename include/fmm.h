@@ -209,6 +209,14 @@ fmm_status fmm_profile_read(fmm_plan_t plan, double ms[FMM_NPASS], int64_t launc
 fmm_status fmm_tc_selftest(int n, int k, const float *d_a, const float *d_b, float *d_d, int mode,
                            void *stream);
 
+/* Diagnostic of the bounded device-side wait used by the tensor-core kernels:
+ * one thread waits on a shared-memory mbarrier that expects one arrival.
+ * arrive != 0: the thread arrives first, the wait completes, FMM_OK.
+ * arrive == 0: nothing arrives; the wait gives up after limit_cycles SM
+ * cycles (1..2e9), the kernel records it and returns, and the call reports
+ * FMM_ERR_TIMEOUT; the device stays usable.  Synchronous. */
+fmm_status fmm_wait_selftest(int arrive, long long limit_cycles, void *stream);
+
 /* Synchronise `stream`, then report FMM_ERR_TIMEOUT (once) if a bounded
  * device-side wait of this plan's kernels gave up since the last call, else
  * FMM_OK.  Results of an evaluation that timed out are not valid. */

@@ -21,6 +21,7 @@ _STATUS = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_CUDA", 3: "FMM_ERR
 EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_plan_set_points",
            "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_sync", "fmm_plan_sizes",
            "fmm_plan_export", "fmm_plan_destroy", "fmm_direct", "fmm_laplace7_apply",
+           "fmm_wait_selftest",
            "fmm_status_string", "fmm_last_error_message")
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
@@ -71,6 +72,7 @@ def library():
         L.fmm_plan_destroy.argtypes = [_vp]
         L.fmm_direct.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _vp]
         L.fmm_laplace7_apply.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp]
+        L.fmm_wait_selftest.argtypes = [_int, ctypes.c_longlong, _vp]
         L.fmm_status_string.argtypes = [_int]
         L.fmm_status_string.restype = ctypes.c_char_p
         L.fmm_last_error_message.restype = ctypes.c_char_p

@@ -84,11 +84,44 @@ __global__ void __launch_bounds__(128)
   if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
+// The bounded wait of the tensor-core kernels, on an mbarrier of one expected
+// arrival: with arrive != 0 the thread arrives first and the wait completes;
+// with arrive == 0 nothing arrives, the wait gives up after limit cycles and
+// the kernel records that in err and returns (no trap, no endless loop).
+__global__ void k_wait_probe(int arrive, long long limit, int *__restrict__ err) {
+  __shared__ uint64_t mbar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&mbar, 1);
+  if (arrive) tc::mbar_arrive(&mbar);
+  if (!tc::mbar_wait_bounded(&mbar, 0, limit)) *err = 1;
+}
+
 }  // namespace
 
 }  // namespace fmm
 
 using namespace fmm;
+
+extern "C" fmm_status fmm_wait_selftest(int arrive, long long limit_cycles, void *stream) {
+  if (limit_cycles < 1 || limit_cycles > kWaitCycles)
+    return record_error(FMM_ERR_INVALID_ARG, "fmm_wait_selftest: limit_cycles in 1..2e9");
+  try {
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<int> err;
+    err.resize(1, s);
+    FMM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    k_wait_probe<<<1, 32, 0, s>>>(arrive, limit_cycles, err.p);
+    FMM_LAUNCH_CHECK();
+    int h = 0;
+    FMM_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
+    err.release();
+    if (h) return record_error(FMM_ERR_TIMEOUT, "wait probe: the bounded mbarrier wait gave up");
+    return FMM_OK;
+  } catch (const Error &e) {
+    return record_error(e.status, e.what());
+  }
+}
 
 extern "C" fmm_status fmm_tc_selftest(int n, int k, const float *d_a, const float *d_b, float *d_d,
                                       int mode, void *stream) {

@@ -41,3 +41,25 @@ def test_tc_three_product_is_fp32_accurate(cuda, n, k):
     assert e1 < 5e-3
     assert e3 < 5e-6
     assert e3 < e1 / 50
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable(cuda):
+    """Failure detection without a GPU fault: a wait on an mbarrier that
+    nothing arrives at gives up after its limit (about a millisecond here),
+    the kernel returns, the host reads FMM_ERR_TIMEOUT, and the device then
+    runs an FMM that matches the oracle."""
+    import oracle
+    from paper_1602_02244_gb300 import workloads
+    L = binding.library()
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.fmm_wait_selftest(1, 2_000_000, s) == 0  # the arrival completes the wait
+    assert L.fmm_wait_selftest(0, 2_000_000, s) == 4  # FMM_ERR_TIMEOUT
+    assert b"gave up" in L.fmm_last_error_message()
+    assert L.fmm_wait_selftest(0, 0, s) == 1  # limit out of range: FMM_ERR_INVALID_ARG
+    xyz, q = workloads.uniform_cube_problem(3000, 4)
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=32, order=6, precision="mixed")
+    phi, _ = plan.eval(torch.tensor(q, device=cuda))
+    plan.close()
+    po = oracle.Tree(xyz, 32).eval(6, q, grad=False)
+    err = np.linalg.norm(phi.cpu().numpy() - po) / np.linalg.norm(po)
+    assert err < 1e-5
