@@ -322,39 +322,53 @@ __global__ void k_l2l(int p, int32_t b0, int32_t nbl, const int32_t *__restrict_
   if (Lout32) Lout32[(int64_t)b * ld + r] = (float)acc;
 }
 
-// FP32 M2M and L2L with four outputs per thread: thread (box, quad q) owns
+// FP32 M2M and L2L with four outputs per lane: lane (box, quad q) owns
 // coefficients 4q..4q+3 and reads the input-major operator as one 16-byte
 // load per input coefficient.  The triangular structure bounds the loops:
 // M2M output degree n uses inputs of degree <= n, L2L inputs of degree >= n.
-__global__ void k_m2m_f32q(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ child,
-                           const int32_t *__restrict__ nchild, const BoxGeo *__restrict__ geo,
-                           const float *__restrict__ Mc, const float4 *__restrict__ opT,
-                           float *__restrict__ Mp) {
+// M2M splits the children across 8 consecutive lanes: lane c of a group takes
+// the parent's c-th child (if any) and a 3-step shuffle reduction sums the
+// group, so each lane runs at most (p+1)^2 dependent multiply-adds instead of
+// up to 8 (p+1)^2 -- these small per-level launches are latency-bound.
+__global__ void k_m2m_f32q_split(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ child,
+                                 const int32_t *__restrict__ nchild, const BoxGeo *__restrict__ geo,
+                                 const float *__restrict__ Mc, const float4 *__restrict__ opT,
+                                 float *__restrict__ Mp) {
   const int nc = ncoef(p), ld = coef_pitch(p), nq = ld / 4;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nbl * nq) return;
-  const int32_t b = b0 + (int32_t)(t / nq);
-  const int q = (int)(t % nq);
-  const int nch = nchild[b];
-  if (nch == 0) return;  // a leaf keeps its P2M multipole
+  const int64_t g = t >> 3;  // (parent, quad) group of 8 lanes
+  const int c = (int)(t & 7);
+  const bool in = g < (int64_t)nbl * nq;
+  int32_t b = 0, nch = 0;
+  int q = 0;
+  if (in) {
+    b = b0 + (int32_t)(g / nq);
+    q = (int)(g % nq);
+    nch = nchild[b];
+  }
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (4 * q < nc) {  // rows beyond nc are the zero padding
+  if (in && c < nch && 4 * q < nc) {
     const int kmax = ncoef(degree_of(min(4 * q + 3, nc - 1)));
-    const int32_t c0 = child[b];
-    for (int32_t cc = c0; cc < c0 + nch; ++cc) {
-      const float4 *col = opT + (size_t)octant(geo[cc]) * nc * nq + q;
-      const float *m = Mc + (int64_t)cc * ld;
-      for (int k = 0; k < kmax; ++k) {
-        const float mk = m[k];
-        const float4 w = col[(size_t)k * nq];
-        acc.x = fmaf(w.x, mk, acc.x);
-        acc.y = fmaf(w.y, mk, acc.y);
-        acc.z = fmaf(w.z, mk, acc.z);
-        acc.w = fmaf(w.w, mk, acc.w);
-      }
+    const int32_t cc = child[b] + c;
+    const float4 *col = opT + (size_t)octant(geo[cc]) * nc * nq + q;
+    const float *m = Mc + (int64_t)cc * ld;
+    for (int k = 0; k < kmax; ++k) {
+      const float mk = m[k];
+      const float4 w = col[(size_t)k * nq];
+      acc.x = fmaf(w.x, mk, acc.x);
+      acc.y = fmaf(w.y, mk, acc.y);
+      acc.z = fmaf(w.z, mk, acc.z);
+      acc.w = fmaf(w.w, mk, acc.w);
     }
   }
-  reinterpret_cast<float4 *>(Mp + (int64_t)b * ld)[q] = acc;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {  // groups are 8-aligned within the warp
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+  }
+  if (in && c == 0 && nch > 0) reinterpret_cast<float4 *>(Mp + (int64_t)b * ld)[q] = acc;
 }
 
 __global__ void k_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ parent,
@@ -965,9 +979,9 @@ void launch_m2m_f32q(int p, int32_t b0, int32_t nbl, const int32_t *child, const
                      const BoxGeo *geo, const float *Mc, const float *opT, float *Mp,
                      cudaStream_t s) {
   if (nbl == 0) return;
-  const int64_t tot = (int64_t)nbl * (coef_pitch(p) / 4);
-  k_m2m_f32q<<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, child, nchild, geo, Mc,
-                                                reinterpret_cast<const float4 *>(opT), Mp);
+  const int64_t tot = (int64_t)nbl * (coef_pitch(p) / 4) * 8;
+  k_m2m_f32q_split<<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, child, nchild, geo, Mc,
+                                                      reinterpret_cast<const float4 *>(opT), Mp);
   FMM_LAUNCH_CHECK();
 }
 
