@@ -280,23 +280,31 @@ __global__ void k_m2m(int p, int32_t b0, int32_t nbl, const int32_t *__restrict_
                       const int32_t *__restrict__ nchild, const BoxGeo *__restrict__ geo,
                       const Tin *__restrict__ Mc, const Top *__restrict__ ops, Tout *__restrict__ Mp,
                       float *__restrict__ Mp32) {
+  // 8 consecutive lanes per (parent, output): lane c takes the c-th child
+  // and a 3-step shuffle reduction sums them (short dependent chains)
   const int nc = ncoef(p), ld = coef_pitch(p);
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nbl * ld) return;
-  const int32_t b = b0 + (int32_t)(t / ld);
-  const int r = (int)(t % ld);
-  const int nch = nchild[b];
-  if (nch == 0) return;
-  Tacc acc = Tacc(0);
-  if (r < nc) {  // the row padding is written as zero
-    const int kmax = ncoef(degree_of(r));
-    const int32_t c0 = child[b];
-    for (int32_t cc = c0; cc < c0 + nch; ++cc) {
-      const Top *row = ops + ((size_t)octant(geo[cc]) * nc + r) * nc;
-      const Tin *m = Mc + (int64_t)cc * ld;
-      for (int k = 0; k < kmax; ++k) acc += (Tacc)row[k] * (Tacc)m[k];
-    }
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t g = t >> 3;
+  const int c = (int)(t & 7);
+  const bool in = g < (int64_t)nbl * ld;
+  int32_t b = 0, nch = 0;
+  int r = 0;
+  if (in) {
+    b = b0 + (int32_t)(g / ld);
+    r = (int)(g % ld);
+    nch = nchild[b];
   }
+  Tacc acc = Tacc(0);
+  if (in && r < nc && c < nch) {  // the row padding is written as zero
+    const int kmax = ncoef(degree_of(r));
+    const int32_t cc = child[b] + c;
+    const Top *row = ops + ((size_t)octant(geo[cc]) * nc + r) * nc;
+    const Tin *m = Mc + (int64_t)cc * ld;
+    for (int k = 0; k < kmax; ++k) acc += (Tacc)row[k] * (Tacc)m[k];
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (!in || c != 0 || nch == 0) return;  // a leaf keeps its P2M multipole
   Mp[(int64_t)b * ld + r] = (Tout)acc;
   if (Mp32) Mp32[(int64_t)b * ld + r] = (float)acc;
 }
@@ -374,27 +382,50 @@ __global__ void k_m2m_f32q_split(int p, int32_t b0, int32_t nbl, const int32_t *
 __global__ void k_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ parent,
                            const BoxGeo *__restrict__ geo, const float4 *__restrict__ opT,
                            float *L) {
+  // 4 consecutive lanes per (box, quad) split the input range (k = k0 + c,
+  // k0 + c + 4, ...) and a 2-step shuffle reduction sums them
   const int nc = ncoef(p), ld = coef_pitch(p), nq = ld / 4;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nbl * nq) return;
-  const int32_t b = b0 + (int32_t)(t / nq);
-  const int q = (int)(t % nq);
-  if (4 * q >= nc) return;
-  const int32_t P = parent[b];
-  const int n0 = degree_of(4 * q);
-  const float4 *col = opT + (size_t)octant(geo[b]) * nc * nq + q;
-  const float *lp = L + (int64_t)P * ld;
-  float4 *out = reinterpret_cast<float4 *>(L + (int64_t)b * ld) + q;
-  float4 acc = *out;
-  for (int k = n0 * n0; k < nc; ++k) {
-    const float lk = lp[k];
-    const float4 w = col[(size_t)k * nq];
-    acc.x = fmaf(w.x, lk, acc.x);
-    acc.y = fmaf(w.y, lk, acc.y);
-    acc.z = fmaf(w.z, lk, acc.z);
-    acc.w = fmaf(w.w, lk, acc.w);
+  const int64_t g = t >> 2;
+  const int c = (int)(t & 3);
+  const bool in = g < (int64_t)nbl * nq;
+  int32_t b = 0;
+  int q = 0;
+  if (in) {
+    b = b0 + (int32_t)(g / nq);
+    q = (int)(g % nq);
   }
-  *out = acc;
+  const bool act = in && 4 * q < nc;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (act) {
+    const int32_t P = parent[b];
+    const int n0 = degree_of(4 * q);
+    const float4 *col = opT + (size_t)octant(geo[b]) * nc * nq + q;
+    const float *lp = L + (int64_t)P * ld;
+    for (int k = n0 * n0 + c; k < nc; k += 4) {
+      const float lk = lp[k];
+      const float4 w = col[(size_t)k * nq];
+      acc.x = fmaf(w.x, lk, acc.x);
+      acc.y = fmaf(w.y, lk, acc.y);
+      acc.z = fmaf(w.z, lk, acc.z);
+      acc.w = fmaf(w.w, lk, acc.w);
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+  }
+  if (!act || c != 0) return;
+  float4 *out = reinterpret_cast<float4 *>(L + (int64_t)b * ld) + q;
+  float4 v = *out;
+  v.x += acc.x;
+  v.y += acc.y;
+  v.z += acc.z;
+  v.w += acc.w;
+  *out = v;
 }
 
 template <typename Tin>
@@ -957,7 +988,7 @@ void launch_m2m(int p, int32_t b0, int32_t nbl, const int32_t *child, const int3
                 const BoxGeo *geo, const Tin *Mc, const Top *ops, Tout *Mp, float *Mp32,
                 cudaStream_t s) {
   if (nbl == 0) return;
-  int64_t tot = (int64_t)nbl * coef_pitch(p);
+  int64_t tot = (int64_t)nbl * coef_pitch(p) * 8;
   k_m2m<Tin, Tout, Top, Tacc><<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, child, nchild, geo, Mc,
                                                                  ops, Mp, Mp32);
   FMM_LAUNCH_CHECK();
@@ -988,7 +1019,7 @@ void launch_m2m_f32q(int p, int32_t b0, int32_t nbl, const int32_t *child, const
 void launch_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *parent, const BoxGeo *geo,
                      const float *opT, float *L, cudaStream_t s) {
   if (nbl == 0) return;
-  const int64_t tot = (int64_t)nbl * (coef_pitch(p) / 4);
+  const int64_t tot = (int64_t)nbl * (coef_pitch(p) / 4) * 4;
   k_l2l_f32q<<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, parent, geo,
                                                 reinterpret_cast<const float4 *>(opT), L);
   FMM_LAUNCH_CHECK();
