@@ -6,7 +6,8 @@
 // U-list sources in a warp-private shared buffer, already shifted into the
 // target leaf's local frame (offsets between box centres are exact), and
 // every lane sweeps the staged sources (broadcast shared loads) for its 1-4
-// targets:
+// targets (the FP32 kernel splits the sources over groups of lanes when the
+// leaf is small):
 //   r2 = |x_i - x_j|^2, rinv = rsqrt(r2),
 //   phi += q rinv,  grad -= q rinv^3 (x_i - x_j).
 // Zero distances occur only between points of the same leaf (coincident
@@ -228,16 +229,27 @@ __device__ __forceinline__ void interact2(const float4 &a, const float4 &b, cons
   }
 }
 
+// Source groups.  A leaf of c targets leaves most lanes idle in its last
+// target slot when c is not near a multiple of 32 (Plummer leaves hold ~37
+// points on average).  So the warp splits into G = 1, 2, 4 or 8 groups of
+// 32/G lanes: a group's lanes hold the targets (1-4 each), and group g sweeps
+// the staged pairs k = g (mod G).  The partial sums meet once per target tile
+// (an FP64 butterfly over the groups).  G is the largest that still holds
+// the leaf in one tile of 4 x 32/G targets: a second tile stages every
+// source again, which costs more than the idle slots it saves (measured).
+__device__ __forceinline__ int p2p_group_log2(int c) { return c <= 16 ? 3 : c <= 32 ? 2 : c <= 64 ? 1 : 0; }
+
+// staged pairs [0, ktot) of one batch: the pairs of group gi (k = gi mod G),
+// the target leaf's own piece [s0, s1) through the zero-distance mask
 template <int TPL>
-__device__ __forceinline__ void sweep2(const float4 *sa, const float4 *sb, int k0, int k1, bool self,
-                                       const float2 (&tx)[kMaxTPL], const float2 (&ty)[kMaxTPL],
+__device__ __forceinline__ void sweep2(const float4 *sa, const float4 *sb, int s0, int s1, int ktot, int gi,
+                                       int G, const float2 (&tx)[kMaxTPL], const float2 (&ty)[kMaxTPL],
                                        const float2 (&tz)[kMaxTPL], float2 (&acc)[kMaxTPL][4]) {
-  if (self) {
-    for (int k = k0; k < k1; ++k) interact2<TPL, true>(sa[k], sb[k], tx, ty, tz, acc);
-  } else {
 #pragma unroll 2
-    for (int k = k0; k < k1; ++k) interact2<TPL, false>(sa[k], sb[k], tx, ty, tz, acc);
-  }
+  for (int k = gi; k < s0; k += G) interact2<TPL, false>(sa[k], sb[k], tx, ty, tz, acc);
+  for (int k = s0 + ((gi - s0) & (G - 1)); k < s1; k += G) interact2<TPL, true>(sa[k], sb[k], tx, ty, tz, acc);
+#pragma unroll 2
+  for (int k = s1 + ((gi - s1) & (G - 1)); k < ktot; k += G) interact2<TPL, false>(sa[k], sb[k], tx, ty, tz, acc);
 }
 
 template <int CAP>
@@ -265,13 +277,17 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtasF32)
   const double sbs = side[B];
   const int32_t fb = first[B], cb = count[B];
   const int32_t e0 = uoff[B], e1 = uoff[B + 1];
-  for (int32_t tc = 0; tc < cb; tc += 32 * kMaxTPL) {
-    const int tcount = min(32 * kMaxTPL, cb - tc);
-    const int tpl = (tcount + 31) / 32;
+  const int lg = p2p_group_log2(cb);
+  const int G = 1 << lg, per = 32 >> lg;
+  const int gi = lane >> (5 - lg);  // this lane's source group
+  const int tl = lane & (per - 1);  // its target column within the group
+  for (int32_t tc = 0; tc < cb; tc += per * kMaxTPL) {
+    const int tcount = min(per * kMaxTPL, cb - tc);
+    const int tpl = (tcount + per - 1) / per;
     float2 tx[kMaxTPL], ty[kMaxTPL], tz[kMaxTPL];
 #pragma unroll
     for (int t = 0; t < kMaxTPL; ++t) {
-      const int i = lane + 32 * t;
+      const int i = tl + per * t;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (i < tcount) v = src[fb + tc + i];
       tx[t] = make_float2(v.x, v.x);
@@ -334,26 +350,33 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtasF32)
         }
       }
       __syncwarp();
-      // ---- sweep the staged pairs piece by piece
+      // ---- sweep the staged pairs: the pieces are contiguous and in one
+      // frame, so only the target leaf's own piece (at most one) is apart
       float2 acc[kMaxTPL][4];
 #pragma unroll
       for (int t = 0; t < kMaxTPL; ++t)
 #pragma unroll
         for (int a = 0; a < 4; ++a) acc[t][a] = make_float2(0.f, 0.f);
-      for (int k = 0; k < npiece; ++k) {
-        const bool self = __shfl_sync(0xffffffffu, A, k) == B;
-        const int32_t k0 = (k > 0 ? s_incl[k - 1] : 0) >> 1, k1 = s_incl[k] >> 1;
-        switch (tpl) {
-          case 1: sweep2<1>(sa, sb, k0, k1, self, tx, ty, tz, acc); break;
-          case 2: sweep2<2>(sa, sb, k0, k1, self, tx, ty, tz, acc); break;
-          case 3: sweep2<3>(sa, sb, k0, k1, self, tx, ty, tz, acc); break;
-          default: sweep2<4>(sa, sb, k0, k1, self, tx, ty, tz, acc); break;
-        }
+      const int ktot = s_incl[npiece - 1] >> 1;
+      const unsigned selfm = __ballot_sync(0xffffffffu, lane < npiece && A == B);
+      int s0 = ktot, s1 = ktot;
+      if (selfm) {
+        const int ks = __ffs(selfm) - 1;
+        s0 = (ks > 0 ? s_incl[ks - 1] : 0) >> 1;
+        s1 = s_incl[ks] >> 1;
+      }
+      switch (tpl) {
+        case 1: sweep2<1>(sa, sb, s0, s1, ktot, gi, G, tx, ty, tz, acc); break;
+        case 2: sweep2<2>(sa, sb, s0, s1, ktot, gi, G, tx, ty, tz, acc); break;
+        case 3: sweep2<3>(sa, sb, s0, s1, ktot, gi, G, tx, ty, tz, acc); break;
+        default: sweep2<4>(sa, sb, s0, s1, ktot, gi, G, tx, ty, tz, acc); break;
       }
 #pragma unroll
-      for (int t = 0; t < kMaxTPL; ++t)
+      for (int t = 0; t < kMaxTPL; ++t) {
+        if (t >= tpl) break;
 #pragma unroll
         for (int a = 0; a < 4; ++a) tot[t * 4 + a][lane] += (double)acc[t][a].x + (double)acc[t][a].y;
+      }
       if (m == 0) {
         off += CAP;
       } else {
@@ -362,14 +385,19 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PMinCtasF32)
       }
       __syncwarp();  // the staged batch is consumed before it is overwritten
     }
+    // ---- the groups' partial sums of each target meet (lanes tl, tl + per, ...)
 #pragma unroll
     for (int t = 0; t < kMaxTPL; ++t) {
-      const int i = lane + 32 * t;
-      if (i < tcount) {
-        const int64_t g = fb + tc + i;
-        reinterpret_cast<Dbl4 *>(near)[g] = make_dbl4(
-            tot[t * 4][lane], -tot[t * 4 + 1][lane], -tot[t * 4 + 2][lane], -tot[t * 4 + 3][lane]);
-      }
+      if (t >= tpl) break;
+      double v[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) v[a] = tot[t * 4 + a][lane];
+      for (int o = per; o < 32; o <<= 1)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o);
+      const int i = tl + per * t;
+      if (gi == 0 && i < tcount)
+        reinterpret_cast<Dbl4 *>(near)[fb + tc + i] = make_dbl4(v[0], -v[1], -v[2], -v[3]);
     }
   }
 }
