@@ -46,11 +46,11 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 # at the leaf sizes the autotuner chooses between
 # (profiles/p2p_traffic_plummer4m_p8.md); keyed by
 # (pass, N, order, leaf size, precision).  Any other configuration reports null.
-TRAFFIC_BYTES = {("P2P", 4194304, 8, 128, "mixed"): 180.0e6,
-                 ("P2P", 4194304, 8, 144, "mixed"): 176.4e6,
-                 ("P2P", 4194304, 8, 160, "mixed"): 175.8e6,
-                 ("P2P", 4194304, 8, 176, "mixed"): 172.1e6,
-                 ("P2P", 4194304, 8, 192, "mixed"): 170.2e6}
+TRAFFIC_BYTES = {("P2P", 4194304, 8, 96, "mixed"): 189.0e6,
+                 ("P2P", 4194304, 8, 112, "mixed"): 185.3e6,
+                 ("P2P", 4194304, 8, 128, "mixed"): 179.6e6,
+                 ("P2P", 4194304, 8, 144, "mixed"): 177.8e6,
+                 ("P2P", 4194304, 8, 160, "mixed"): 175.3e6}
 
 
 def parse():
