@@ -747,8 +747,12 @@ __global__ void __launch_bounds__(kM2PThreads)
 // on paired FP32 instructions for both targets, and each staged coefficient
 // 4-vector (one 16-byte broadcast load) serves both targets, which halves
 // the shared-memory traffic per evaluation (the scalar kernel is bound by
-// it).  Up to 256 targets per chunk; the 4 warps form 1, 2 or 4 replicas
-// that split the W list, as in the FP64 kernel.
+// it).  Up to 256 targets per chunk.  The 128 threads form replicas that
+// split the W list: a replica is the smallest multiple of 8 lanes that holds
+// the chunk's target pairs, so a leaf of 94 targets runs two replicas of 48
+// lanes rather than one of 64 (whole warps left 18 % of the lane slots idle
+// on Plummer W leaves).  Lanes of one warp may belong to two replicas; they
+// run the same instructions on different staged boxes.
 template <int PT>
 __global__ void __launch_bounds__(kM2PThreads)
     k_m2p_f32x2(int p_rt, int nstage, const int32_t *__restrict__ wleaves,
@@ -772,9 +776,9 @@ __global__ void __launch_bounds__(kM2PThreads)
   const int32_t f = first[B], c = count[B], e0 = woff[B], e1 = woff[B + 1];
   for (int32_t tc = 0; tc < c; tc += 2 * kM2PThreads) {
     const int tcount = min(2 * kM2PThreads, c - tc);
-    const int wpr = (tcount + 63) / 64;  // warps per replica
-    const int k = 4 / wpr;               // replicas
-    const int rep = warp / wpr, j = (warp - rep * wpr) * 32 + lane, ti = 2 * j;
+    const int L = ((tcount + 1) / 2 + 7) & ~7;  // lanes per replica
+    const int k = max(1, kM2PThreads / L);      // replicas
+    const int rep = tid / L, j = tid - rep * L, ti = 2 * j;
     const bool act = rep < k && ti < tcount;
     float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
     if (act) {
@@ -853,7 +857,7 @@ __global__ void __launch_bounds__(kM2PThreads)
       red[3][h][tid] = gz[h];
     }
     __syncthreads();
-    // target pair jj (targets 2 jj, 2 jj + 1): replica r holds it at thread r * 32 * wpr + jj
+    // target pair jj (targets 2 jj, 2 jj + 1): replica r holds it at thread r * L + jj
     if (tid < (tcount + 1) / 2) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -861,7 +865,7 @@ __global__ void __launch_bounds__(kM2PThreads)
         if (u < tcount) {
           double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
           for (int r = 0; r < k; ++r) {
-            const int o = r * 32 * wpr + tid;
+            const int o = r * L + tid;
             a0 += red[0][h][o];
             a1 += red[1][h][o];
             a2 += red[2][h][o];

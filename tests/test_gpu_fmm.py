@@ -106,6 +106,25 @@ def test_mixed_config3_plummer_4m(cuda):
     assert rel(g[sel], gd) <= 1e-4
 
 
+@pytest.mark.parametrize("c", [2, 5, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 300, 449, 1000])
+def test_mixed_near_field_of_one_leaf_is_the_direct_sum(cuda, c):
+    """A root that is a leaf: the mat-vec is the FP32 near-field kernel alone.
+    The counts straddle the lane-group thresholds (a leaf of <= 16, 32, 64
+    targets splits its sources over 8, 4, 2 groups of lanes), several target
+    tiles (> 128) and a leaf larger than one staged batch of sources (> 448).
+    Four coincident points contribute nothing to one another."""
+    xyz = workloads.rng(c).uniform(0.0, 1.0, (c, 3))
+    xyz[-3:] = xyz[0] if c >= 4 else xyz[-3:]
+    q = workloads.rng(c + 1).uniform(-1, 1, c)
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=c, order=4, precision="mixed")
+    assert plan.sizes()["nboxes"] == 1
+    phi, g = plan.eval(torch.tensor(q, device=cuda))
+    phi, g = phi.cpu().numpy(), g.cpu().numpy()
+    plan.close()
+    pd, gd = oracle.direct(xyz, q)
+    assert rel(phi, pd) <= 1e-5 and rel(g, gd) <= 1e-4
+
+
 def test_coincident_points_and_single_point(cuda):
     xyz = np.vstack([np.tile([[0.5, 0.5, 0.5]], (40, 1)), workloads.uniform_cube(200, 4)])
     q = workloads.rng(9).uniform(-1, 1, len(xyz))
