@@ -135,13 +135,23 @@ def test_coincident_points_and_single_point(cuda):
     assert phi1[0] == 0.0 and np.all(g1 == 0.0)
 
 
-def test_host_entry_point_matches_device_path(cuda):
-    xyz, q = workloads.uniform_cube_problem(30000, 5)
-    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=32, order=6)
-    phi_d, g_d = plan.eval(torch.tensor(q, device=cuda))
-    phi_h, g_h = plan.solve_host(xyz, q)
-    assert np.array_equal(phi_h, phi_d.cpu().numpy())
-    assert np.array_equal(g_h, g_d.cpu().numpy())
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_entry_point_matches_device_path(cuda, precision):
+    """fmm_solve_host (charges uploaded on a side stream while the tree is
+    built) equals the device path, call after call on new points."""
+    plan = None
+    for seed, (n, gen) in enumerate([(30000, workloads.uniform_cube_problem), (50000, workloads.uniform_cube_problem),
+                                     (20000, lambda n, s: (workloads.plummer_problem(n, s)[0],
+                                                           workloads.rng(s).uniform(-1, 1, n)))]):
+        xyz, q = gen(n, seed + 5)
+        dev = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=32, order=6, precision=precision)
+        phi_d, g_d = dev.eval(torch.tensor(q, device=cuda))
+        dev.close()
+        if plan is None:
+            plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=32, order=6, precision=precision)
+        phi_h, g_h = plan.solve_host(xyz, q)
+        assert np.array_equal(phi_h, phi_d.cpu().numpy())
+        assert np.array_equal(g_h, g_d.cpu().numpy())
     plan.close()
 
 
