@@ -155,9 +155,7 @@ fmm_status fmm_eval_graph(fmm_plan_t plan, const double *d_q, double *d_phi, dou
 /* End-to-end call on HOST buffers: copies h_xyz (n x 3) and h_q (n) to the
  * device, rebuilds `plan` for them, evaluates, and copies phi (n) and, if
  * h_grad is not NULL, grad (n x 3) back.  Pinned host memory is fastest.
- * The charges are copied on a side stream that the plan owns, while the tree
- * is built on `stream`; the evaluation waits for them.  Returns after the
- * results are on the host. */
+ * Returns after the results are on the host. */
 fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_q, int64_t n,
                           double *h_phi, double *h_grad, void *stream);
 

@@ -325,22 +325,11 @@ fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_
       build_tree(*plan, nullptr, 0);
       return;
     }
-    if (!plan->io_stream) {
-      FMM_CUDA(cudaStreamCreateWithFlags(&plan->io_stream, cudaStreamNonBlocking));
-      for (cudaEvent_t &e : plan->io_ev) FMM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
     plan->host_io.resize(8 * (size_t)n, s);
     double *d_xyz = plan->host_io.p, *d_q = d_xyz + 3 * n, *d_phi = d_q + n, *d_grad = d_phi + n;
-    // the charges travel while the tree is built (the eval waits for them);
-    // they start after the coordinates, which the tree needs first and which
-    // would otherwise share the host link with them
     FMM_CUDA(cudaMemcpyAsync(d_xyz, h_xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaEventRecord(plan->io_ev[0], s));
-    FMM_CUDA(cudaStreamWaitEvent(plan->io_stream, plan->io_ev[0], 0));
-    FMM_CUDA(cudaMemcpyAsync(d_q, h_q, sizeof(double) * n, cudaMemcpyHostToDevice, plan->io_stream));
-    FMM_CUDA(cudaEventRecord(plan->io_ev[1], plan->io_stream));
+    FMM_CUDA(cudaMemcpyAsync(d_q, h_q, sizeof(double) * n, cudaMemcpyHostToDevice, s));
     build_tree(*plan, d_xyz, n);
-    FMM_CUDA(cudaStreamWaitEvent(s, plan->io_ev[1], 0));
     eval_fmm(*plan, d_q, d_phi, h_grad ? d_grad : nullptr);
     FMM_CUDA(cudaMemcpyAsync(h_phi, d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     if (h_grad)
@@ -497,12 +486,6 @@ fmm_status fmm_plan_destroy(fmm_plan_t plan) {
     release_plan(*plan);
     FMM_CUDA(cudaStreamSynchronize(plan->stream));
     for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
-    if (plan->io_stream) {
-      cudaStreamSynchronize(plan->io_stream);
-      cudaStreamDestroy(plan->io_stream);
-    }
-    for (cudaEvent_t e : plan->io_ev)
-      if (e) cudaEventDestroy(e);
   });
   delete plan;
   return st;

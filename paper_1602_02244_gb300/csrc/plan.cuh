@@ -132,10 +132,6 @@ struct fmm_plan_impl {
   DBuf<double> adj_grad_w, adj_grad_q;  // n x 3 (adjoint)
   DBuf<double> adj_phi;
   DBuf<double> host_io;             // device staging for fmm_solve_host
-  // fmm_solve_host: the charges are uploaded on a side stream while the tree
-  // is built on the plan's stream (created on first use)
-  cudaStream_t io_stream = nullptr;
-  cudaEvent_t io_ev[2] = {nullptr, nullptr};
 
   // profiler: CUDA events around each pass on the plan's stream
   bool prof_on = false;

@@ -137,8 +137,7 @@ def test_coincident_points_and_single_point(cuda):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_host_entry_point_matches_device_path(cuda, precision):
-    """fmm_solve_host (charges uploaded on a side stream while the tree is
-    built) equals the device path, call after call on new points."""
+    """fmm_solve_host equals the device path, call after call on new points."""
     plan = None
     for seed, (n, gen) in enumerate([(30000, workloads.uniform_cube_problem), (50000, workloads.uniform_cube_problem),
                                      (20000, lambda n, s: (workloads.plummer_problem(n, s)[0],
