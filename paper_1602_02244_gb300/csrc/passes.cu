@@ -886,10 +886,10 @@ __global__ void __launch_bounds__(kM2PThreads)
   }
 }
 
-// final per-target reduction in FP64 and scatter to the caller's order
-// far + near per target, gathered into the caller's order: thread o reads the
-// two 32-byte records of its sorted position and writes phi[o], grad[o][:]
-// with consecutive threads on consecutive addresses
+// final per-target reduction in FP64: far + near per target, gathered into
+// the caller's order.  Thread o reads the two 32-byte records of its sorted
+// position and writes phi[o], grad[o][:], consecutive threads on consecutive
+// addresses.
 __global__ void k_combine(int64_t n, const int32_t *__restrict__ iperm,
                           const Dbl4 *__restrict__ far, const Dbl4 *__restrict__ near,
                           double *__restrict__ phi, double *__restrict__ grad) {

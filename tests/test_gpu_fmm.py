@@ -106,6 +106,29 @@ def test_mixed_config3_plummer_4m(cuda):
     assert rel(g[sel], gd) <= 1e-4
 
 
+def test_full_size_in_the_benchmarked_configuration_vs_oracle_fmm(cuda):
+    """4,194,304 Plummer points, p = 8, with the leaf size the autotuner picks
+    (the configuration the benchmark times): the FP64 mat-vec within 1e-12 of
+    the oracle's FMM on the same tree on every target, and the mixed-precision
+    mat-vec within the mixed bars of it."""
+    xyz, q = workloads.plummer_problem(4194304, 0)
+    X, Q = torch.tensor(xyz, device=cuda), torch.tensor(q, device=cuda)
+    mixed = binding.Plan(X, leaf_size=0, order=8, precision="mixed")
+    S = mixed.sizes()["leaf_size"]
+    phi_m, g_m = (a.cpu().numpy() for a in mixed.eval(Q))
+    mixed.close()
+    f64 = binding.Plan(X, leaf_size=S, order=8, precision="fp64")
+    phi_d, g_d = (a.cpu().numpy() for a in f64.eval(Q))
+    f64.close()
+    po, go = oracle.Tree(xyz, S).eval(8, q)
+    print("4M Plummer, leaf %d: fp64 vs oracle %.2e; mixed vs oracle phi %.2e grad %.2e"
+          % (S, rel(phi_d, po), rel(phi_m, po), rel(g_m, go)))
+    assert rel(phi_d, po) <= 1e-12
+    for a in range(3):
+        assert rel(g_d[:, a], go[:, a]) <= 1e-12
+    assert rel(phi_m, po) <= 1e-5 and rel(g_m, go) <= 1e-4
+
+
 @pytest.mark.parametrize("c", [2, 5, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 300, 449, 1000])
 def test_mixed_near_field_of_one_leaf_is_the_direct_sum(cuda, c):
     """A root that is a leaf: the mat-vec is the FP32 near-field kernel alone.
