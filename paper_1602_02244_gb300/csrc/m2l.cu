@@ -10,6 +10,7 @@
 // shared memory and accumulates in registers; targets without a source in
 // that slot contribute a zero row.  Each target's sum runs over slots in a
 // fixed order, so results do not depend on how targets are grouped.
+#include "async_copy.cuh"
 #include "eval_kernels.cuh"
 #include "m2l_config.cuh"
 
@@ -316,13 +317,6 @@ __global__ void __launch_bounds__(kRotThreads)
 }
 
 // ------------------------------------------------- staged FP32 M2L kernel
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 constexpr int kStagedTile = 64, kStagedTPT = 4, kStagedRG = 16;
 

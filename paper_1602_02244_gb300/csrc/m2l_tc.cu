@@ -22,6 +22,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "eval_kernels.cuh"
 #include "m2l_config.cuh"
 #include "tcgen05.cuh"
@@ -33,19 +34,6 @@ namespace {
 constexpr int kTcTile = 128;     // targets per CTA = MMA M
 constexpr int kTcKC = 32;        // K per stage
 constexpr long long kTcWaitCycles = 400000000ll;  // ~0.2 s: far beyond any legitimate wait
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(tc::smem_addr(smem)),
-               "l"(gmem), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 // Mhi/Mlo[b][k] (pitch kt, zero beyond the nc coefficients) from M[b][k] (pitch ld)
 __global__ void k_split_tf32(int64_t nb, int nc, int ld, int kt, const float *__restrict__ M,
