@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(kM2PThreads)
   __shared__ double s_ia[kM2PStage];
   __shared__ int32_t s_slot[kM2PStage];
   __shared__ double red[4][2][kM2PThreads];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x;
   const int ld1 = coef_pitch(p + 1), nc1 = ncoef(p + 1);
   const int32_t B = wleaves[blockIdx.x];
   const BoxGeo gb = geo[B];
