@@ -152,6 +152,51 @@ def test_p2m_m2p_within_greengard_rokhlin_bound(p):
     assert np.all(np.abs(phi - pd) <= bound * (1 + 1e-9) + 1e-15)
 
 
+@pytest.mark.parametrize("p", [2, 4, 8, 12])
+def test_p2l_l2p_within_local_expansion_bound(p):
+    """Sources at distance >= rho from c, targets at r < rho:
+    |phi_direct - phi_L2P(P2L)| <= sum|q| / (rho - r) * (r/rho)^(p+1)
+    (the local-expansion error bound of Greengard and Rokhlin)."""
+    rng = np.random.default_rng(20 + p)
+    c = np.array([-0.3, 0.2, 0.1])
+    d = rng.normal(size=(40, 3))
+    src = c + d / np.linalg.norm(d, axis=1)[:, None] * rng.uniform(2.0, 4.0, (40, 1))
+    q = rng.uniform(-1, 1, 40)
+    rho = np.linalg.norm(src - c, axis=1).min()
+    tgt = _cluster(rng, c, 1.6, 60)
+    r = np.linalg.norm(tgt - c, axis=1)
+    tgt, r = tgt[r < 0.9 * rho], r[r < 0.9 * rho]
+    L = oracle.p2l(p, c, src, q)
+    phi, _ = oracle.l2p(p, c, L, tgt)
+    pd, _ = oracle.direct(src, q, tgt)
+    bound = np.abs(q).sum() / (rho - r) * (r / rho) ** (p + 1)
+    assert len(tgt) > 20
+    assert np.all(np.abs(phi - pd) <= bound * (1 + 1e-9) + 1e-15)
+
+
+@pytest.mark.parametrize("p", [0, 1, 3, 8, 15])
+def test_single_charge_expansions_are_the_truncated_legendre_series(p):
+    """One unit charge, expansions of degree p about c.  By the addition
+    theorem for Legendre polynomials both the far-field pair (P2M then M2P)
+    and the near-field pair (P2L then L2P) give exactly the truncated series
+        sum_{n <= p} r_<^n / r_>^(n+1) P_n(cos g),
+    r_< and r_> the smaller and larger of |s - c| and |y - c|, g the angle
+    between s - c and y - c.  A wrong or missing term of any degree changes
+    the value by more than the tolerance."""
+    from scipy.special import eval_legendre
+    c = np.array([0.1, -0.2, 0.3])
+    near = c + np.array([0.3, 0.2, -0.25])
+    far = c + np.array([-0.9, 0.6, 0.8])
+    u, v = near - c, far - c
+    rs, rl = np.linalg.norm(u), np.linalg.norm(v)
+    cg = u @ v / (rs * rl)
+    series = sum(rs ** n / rl ** (n + 1) * eval_legendre(n, cg) for n in range(p + 1))
+    phi_far, _ = oracle.m2p(p, c, oracle.p2m(p, c, near[None], [1.0]), far[None])
+    phi_near, _ = oracle.l2p(p, c, oracle.p2l(p, c, far[None], [1.0]), near[None])
+    assert phi_far[0] == pytest.approx(series, rel=1e-13)
+    assert phi_near[0] == pytest.approx(series, rel=1e-13)
+
+
 def test_p2m_m2p_error_decreases_geometrically():
     rng = np.random.default_rng(2)
     c = np.zeros(3)
