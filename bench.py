@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--m2l-path", default="auto", choices=["auto", "simt", "tensor"],
                     help="M2L engine of the mixed path: auto (tensor cores), simt (FP32 CUDA "
                          "cores), tensor")
+    ap.add_argument("--p2p-tile", type=int, default=0,
+                    help="staging shape of the FP32 near-field kernel (0 = default)")
     ap.add_argument("--cpu-sample", type=int, default=1048576,
                     help="points in the oracle's CPU-baseline sample")
     ap.add_argument("--ref-sample", type=int, default=262144,
@@ -435,7 +437,7 @@ def run_ours(args):
     X = torch.tensor(xyz_np, device=dev)
     Q = torch.tensor(q_np, device=dev)
     plan = binding.Plan(X, leaf_size=S, order=p, precision=args.precision,
-                        m2l_path=args.m2l_path)  # S = 0: autotune
+                        m2l_path=args.m2l_path, p2p_tile=args.p2p_tile)  # S = 0: autotune
     S = plan.sizes()["leaf_size"]
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     grad = torch.empty(n, 3, dtype=torch.float64, device=dev)

@@ -82,7 +82,9 @@ typedef struct {
                                  r_B = max |x_j - c_B| over the box's points
                                  (Dehnen): M2L between cells of any sizes,
                                  P2P between the remaining leaf pairs          */
-  int reserved;           /* must be zero                                     */
+  int p2p_tile;           /* MIXED near field: staging shape of the FP32 P2P
+                             kernel, 1..4 (pairs per shared-memory buffer,
+                             buffers, resident warps); 0 = the default        */
   double mac_theta;       /* interaction 1: 0 < theta < 1 (0 = default, 0.5);
                              smaller is more accurate and slower              */
 } fmm_opts;

@@ -9,7 +9,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "plan.cuh"
+#include "eval_kernels.cuh"
 
 namespace fmm {
 
@@ -71,7 +71,8 @@ void check_opts(const fmm_opts *o) {
     throw Error(FMM_ERR_INVALID_ARG, "opts.interaction must be 0 or 1");
   if (!(o->mac_theta >= 0.0 && o->mac_theta < 1.0))
     throw Error(FMM_ERR_INVALID_ARG, "opts.mac_theta must be in [0, 1)");
-  if (o->reserved != 0) throw Error(FMM_ERR_INVALID_ARG, "opts.reserved must be zero");
+  if (o->p2p_tile < 0 || o->p2p_tile > p2p_num_tiles())
+    throw Error(FMM_ERR_INVALID_ARG, "opts.p2p_tile must be in 0.." + std::to_string(p2p_num_tiles()));
 }
 
 void apply_opts(fmm_plan_impl &P, const fmm_opts *o) {
@@ -82,6 +83,7 @@ void apply_opts(fmm_plan_impl &P, const fmm_opts *o) {
   P.max_depth = o->max_depth == 0 ? kMaxDepth : o->max_depth;
   P.dual = o->interaction == 1;
   P.theta = o->mac_theta > 0.0 ? o->mac_theta : 0.5;
+  P.p2p_tile = o->p2p_tile;
 }
 
 }  // namespace
@@ -139,7 +141,9 @@ void release_plan(fmm_plan_impl &P) {
   P.ops.m2m32t.release(); P.ops.l2l32t.release();
   P.radius.release(); P.dt_a.release(); P.dt_b.release(); P.dt_m2l.release();
   P.dt_p2p.release(); P.dt_cnt.release(); P.dt_toff.release(); P.dt_tidx.release();
-  P.dt_goff.release(); P.dt_gidx.release();
+  P.dt_goff.release(); P.dt_gidx.release(); P.p2p_pairs.release(); P.p2p_meta.release(); P.p2p_meta_z.release();
+  P.p2p_key.release(); P.p2p_key_tmp.release(); P.p2p_order.release(); P.p2p_order_tmp.release();
+  P.p2p_ticket.release();
 }
 
 }  // namespace fmm

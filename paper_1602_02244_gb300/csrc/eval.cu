@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "m2l_config.cuh"
+#include "sort.cuh"
 
 namespace fmm {
 
@@ -92,7 +93,7 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   {
     PassScope ps_(P, kPassP2P);
     launch_p2p<double>(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
-                       P.box_geo.p, P.src64.p, P.box_side.p, n, P.near_acc.p, s);
+                       P.box_geo.p, P.src64.p, P.box_side.p, n, P.near_acc.p, nullptr, s);
   }
   {
     PassScope ps_(P, kPassReduce);
@@ -209,8 +210,27 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   }
   {
     PassScope ps_(P, kPassP2P);
+    P.p2p_pairs.resize(p2p_pair_floats(n), s);
+    if (!P.p2p_meta_ok) {
+      // once per plan: staging records, and the leaves sorted by work
+      const size_t nl = std::max<int64_t>(P.nleaves, 1);
+      P.p2p_meta.resize(std::max<int64_t>(P.nu, 1), s);
+      P.p2p_meta_z.resize(std::max<int64_t>(P.nu, 1), s);
+      P.p2p_key.resize(nl, s);
+      P.p2p_order.resize(nl, s);
+      P.p2p_ticket.resize(1, s);
+      launch_p2p_meta(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
+                      P.box_geo.p, P.box_side.p, P.p2p_meta.p, P.p2p_meta_z.p, P.p2p_key.p,
+                      P.p2p_order.p, s);
+      radix_sort(P.p2p_key, P.p2p_order, P.p2p_key_tmp, P.p2p_order_tmp, P.nleaves, digit_shifts(0, 16),
+                 P.s_hist, P.s_scan, s);
+      P.p2p_meta_ok = true;
+    }
+    P2PScratch scratch{reinterpret_cast<float4 *>(P.p2p_pairs.p), P.p2p_meta.p, P.p2p_meta_z.p,
+                       P.p2p_order.p, P.p2p_ticket.p, P.p2p_tile > 0 ? P.p2p_tile : kP2PDefaultTile,
+                       P.dev_err.p};
     launch_p2p<float>(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
-                      P.box_geo.p, P.src32.p, P.box_side.p, n, P.near_acc.p, s);
+                      P.box_geo.p, P.src32.p, P.box_side.p, n, P.near_acc.p, &scratch, s);
   }
   {
     PassScope ps_(P, kPassReduce);

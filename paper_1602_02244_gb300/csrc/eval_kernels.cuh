@@ -87,10 +87,33 @@ template <typename T>
 void launch_m2l_dual(int p, int64_t nb, const int32_t *off, const int32_t *idx, const BoxGeo *geo,
                      const T *M, T *L, bool accumulate, cudaStream_t s);
 
-// p2p.cu
+// p2p.cu.  The FP32 path packs every leaf's sources in pairs once per
+// evaluation into `pairs` (p2p_pair_floats(n) floats).  Once per plan,
+// launch_p2p_meta writes one staging record per U entry (meta, meta_z: nu
+// entries each) and a sort key per leaf (cost_key, cost_leaf: nleaves each,
+// the key falling as the leaf's work grows); `order` is the leaves sorted by
+// that key.  `tile` (1..p2p_num_tiles()) picks the staging shape; `ticket` is
+// one device int of scratch; err is set if a bounded wait for a staging copy
+// gave up.  The FP64 path uses none of them.
+struct P2PScratch {
+  float4 *pairs;
+  const int4 *meta;
+  const float *meta_z;
+  const int32_t *order;
+  int *ticket;
+  int tile;
+  int *err;
+};
+size_t p2p_pair_floats(int64_t n);
+int p2p_num_tiles();
+constexpr int kP2PDefaultTile = 1;
+void launch_p2p_meta(int64_t nleaves, const int32_t *leaves, const int32_t *uoff, const int32_t *uidx,
+                     const int32_t *first, const int32_t *count, const BoxGeo *geo, const double *side,
+                     int4 *meta, float *meta_z, uint64_t *cost_key, int32_t *cost_leaf, cudaStream_t s);
 template <typename T>
 void launch_p2p(int64_t nleaves, const int32_t *leaves, const int32_t *uoff, const int32_t *uidx,
                 const int32_t *first, const int32_t *count, const BoxGeo *geo,
-                const typename V4<T>::type *src, const double *side, int64_t n, double *near, cudaStream_t s);
+                const typename V4<T>::type *src, const double *side, int64_t n, double *near,
+                P2PScratch *scratch, cudaStream_t s);
 
 }  // namespace fmm

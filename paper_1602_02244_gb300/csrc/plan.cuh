@@ -122,6 +122,14 @@ struct fmm_plan_impl {
   // evaluation workspace
   DBuf<Dbl4> src64;              // per sorted point: (local x, y, z, q)
   DBuf<float4> src32;
+  DBuf<float> p2p_pairs;            // FP32 near field: every leaf's sources packed in pairs
+  DBuf<int4> p2p_meta;              // FP32 near field: staging record per U entry
+  DBuf<float> p2p_meta_z;
+  DBuf<uint64_t> p2p_key, p2p_key_tmp;
+  DBuf<int32_t> p2p_order, p2p_order_tmp;  // leaves, most near-field work first
+  DBuf<int32_t> p2p_ticket;
+  bool p2p_meta_ok = false;         // p2p_meta and p2p_order match the current lists
+  int p2p_tile = 0;                 // FP32 near-field staging shape (0 = default)
   DBuf<double> M64, L64;            // nboxes x NC
   DBuf<float> M32, L32;
   DBuf<float> Mhi, Mlo;             // TF32 split of M32 for the tensor-core M2L

@@ -742,6 +742,7 @@ void set_points(fmm_plan_impl &P, const double *d_xyz) {
 void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   cudaStream_t s = P.stream;
   drop_graph(P);  // a captured graph refers to the old layout
+  P.p2p_meta_ok = false;
   P.n = n;
   P.nboxes = 0;
   P.nlevels = 0;
