@@ -3,19 +3,24 @@
 
 Workload: N = 4,194,304 Plummer-sphere points (scale 1, radii <= 10), equal
 charges 1/N, expansion order p = 8, mixed precision (FP32 P2P/M2L, FP64
-coarse M2M/L2L and per-target totals), leaf size 64.  One step = one pass of
-the whole hot path: root cube + Morton keys + radix sort + octree + U/V/W/X
-lists (fmm_plan_rebuild) and the mat-vec P2M/M2M/M2L/P2L/L2L/L2P/M2P/P2P +
-reduction (fmm_eval), producing potentials and gradients for all N targets.
+coarse M2M/L2L, compensated per-target totals), leaf size autotuned.  One
+step = one pass of the whole hot path, forward and adjoint, as a training
+step runs it: root cube + Morton keys + radix sort + octree + U/V/W/X lists
+(fmm_plan_rebuild), the mat-vec P2M/M2M/M2L/P2L/L2L/L2P/M2P/P2P + reduction
+for phi and grad phi (fmm_eval), and the adjoint of L = sum w_i phi_i with
+the forward gradient stored (fmm_adjoint: dL/dq and dL/dx, one more mat-vec).
 
 value      = N x ranks / (max over ranks of the mean device time per step)
-e2e        = the same through fmm_solve_host on pinned HOST buffers, with the
-             H2D copy of points+charges and the D2H copy of phi+grad inside
-             every timed step
+e2e        = the same step through fmm_solve_adjoint_host on pinned HOST
+             buffers, the H2D copy of points, charges and weights and the D2H
+             copy of phi, grad, dL/dq and dL/dx inside every timed step
 roofline   = the dominant pass, from CUDA events the library records on its
-             stream during the timed steps
-cpu_baseline = the CPU oracle (plain C, FP64, OpenMP) on a bounded sample of
-             the same distribution
+             stream during the timed steps, against the FP32 rate measured on
+             this GPU by fmm_fp32_peak
+cpu_baseline = the CPU oracle (plain C, FP64, OpenMP) on the same N = 4M
+             points at the same leaf size, forward and adjoint; the same leg
+             evaluates the oracle's direct sum at 4096 sampled targets, the
+             reference of the error statement
 
 `--impl reference` times the oracle itself as the reference arm.
 Multi-GPU (torchrun): replicas only -- every rank solves its own problem,
@@ -42,15 +47,10 @@ PASSES = ["keys+sort", "boxes", "lists", "P2M", "M2M", "M2L", "P2L", "L2L", "L2P
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel, taken from one ncu capture of the same kernel and workload
-# at the leaf sizes the autotuner chooses between
-# (profiles/p2p_traffic_plummer4m_p8.md); keyed by
-# (pass, N, order, leaf size, precision).  Any other configuration reports null.
-TRAFFIC_BYTES = {("P2P", 4194304, 8, 96, "mixed"): 189.0e6,
-                 ("P2P", 4194304, 8, 112, "mixed"): 185.3e6,
-                 ("P2P", 4194304, 8, 128, "mixed"): 179.6e6,
-                 ("P2P", 4194304, 8, 144, "mixed"): 177.8e6,
-                 ("P2P", 4194304, 8, 160, "mixed"): 175.3e6}
+# dominant kernel, from one ncu capture of the same kernel and workload, keyed
+# by (pass, N, order, leaf size, precision); any other configuration, or a
+# kernel changed since the capture, reports null.
+TRAFFIC_BYTES = {}
 
 
 def parse():
@@ -68,10 +68,13 @@ def parse():
                          "cores), tensor")
     ap.add_argument("--p2p-tile", type=int, default=0,
                     help="staging shape of the FP32 near-field kernel (0 = default)")
-    ap.add_argument("--cpu-sample", type=int, default=1048576,
-                    help="points in the oracle's CPU-baseline sample")
-    ap.add_argument("--ref-sample", type=int, default=262144,
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="points in the oracle's CPU-baseline run (0 = the full N)")
+    ap.add_argument("--ref-sample", type=int, default=524288,
                     help="points per step of the reference arm (the CPU oracle)")
+    ap.add_argument("--ref-leaf", type=int, default=128,
+                    help="leaf size of the reference arm (the GPU autotuner's choice for the "
+                         "4M Plummer workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true")
@@ -80,8 +83,8 @@ def parse():
                     help="also time the dual-tree walk (acceptance theta) on the same points; 0 skips")
     ap.add_argument("--precond", action="store_true",
                     help="add the FMM-preconditioned CG solve of the 7-point Laplace problem")
-    ap.add_argument("--lattice", action="store_true",
-                    help="add plan/eval time and peak device memory vs N on uniform lattices")
+    ap.add_argument("--no-lattice", action="store_true",
+                    help="skip plan/eval time and peak device memory vs N on uniform lattices")
     return ap.parse_args()
 
 
@@ -151,38 +154,51 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ oracle
-def cpu_baseline(n_sample, order, leaf, n_one_core=131072):
-    """The CPU oracle (FP64 plan + FMM with gradients) on a bounded Plummer
-    sample, on all host cores, and on one core (a subprocess with
-    OMP_NUM_THREADS=1) on a smaller sample."""
+def cpu_baseline(n_sample, order, leaf, sel, n_one_core=131072):
+    """The CPU oracle (FP64 plan + FMM with gradients, forward and adjoint: an
+    evaluation with the charges and one with the loss weights) on the Plummer
+    points of the benchmark (all of them when n_sample is the full N), on all
+    host cores, and on one core (a subprocess with OMP_NUM_THREADS=1) on a
+    smaller sample.  Also returns the oracle's FP64 direct sum (phi, grad) at
+    the sampled targets `sel`, the reference of the error statement."""
     import oracle
     from paper_1602_02244_gb300 import workloads
     xyz, q = workloads.plummer_problem(n_sample, 0)
+    w = workloads.rng(2).normal(size=n_sample)
     t0 = time.perf_counter()
     tree = oracle.Tree(xyz, leaf)
     tree.eval(order, q, grad=True)
+    tree.eval(order, w, grad=True)
     dt = time.perf_counter() - t0
+    del tree
     out = {"value": n_sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-           "sample": "Plummer N=%d (same distribution, charges 1/N), p=%d, leaf %d: plan + FP64 "
-                     "FMM eval with gradients, %.1f s" % (n_sample, order, leaf, dt)}
+           "sample": "Plummer N=%d (the benchmark's points, charges 1/N), p=%d, leaf %d: plan + "
+                     "FP64 FMM forward (phi, grad) + adjoint (the FMM with the loss weights), "
+                     "%.1f s" % (n_sample, order, leaf, dt)}
     code = ("import json, time, oracle\n"
             "from paper_1602_02244_gb300 import workloads\n"
             "xyz, q = workloads.plummer_problem(%d, 0)\n"
+            "w = workloads.rng(2).normal(size=%d)\n"
             "t0 = time.perf_counter()\n"
-            "oracle.Tree(xyz, %d).eval(%d, q, grad=True)\n"
+            "t = oracle.Tree(xyz, %d)\n"
+            "t.eval(%d, q, grad=True)\n"
+            "t.eval(%d, w, grad=True)\n"
             "print(json.dumps({'s': time.perf_counter() - t0, 'cores': oracle.num_threads()}))\n"
-            % (n_one_core, leaf, order))
+            % (n_one_core, n_one_core, leaf, order, order))
     try:
         env = dict(os.environ, OMP_NUM_THREADS="1")
         r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
                            text=True, timeout=300)
         one = json.loads(r.stdout.strip().splitlines()[-1])
         out["one_core"] = {"value": n_one_core / one["s"], "unit": UNIT, "cores": one["cores"],
-                           "sample": "Plummer N=%d, same order and leaf, %.1f s" % (n_one_core,
-                                                                                    one["s"])}
+                           "sample": "Plummer N=%d, same order, leaf and step, %.1f s"
+                                     % (n_one_core, one["s"])}
     except Exception as e:  # reported, not fatal
         out["one_core"] = {"error": str(e)[:200]}
-    return out
+    t0 = time.perf_counter()
+    ref = oracle.direct(xyz, q, xyz[sel])
+    out["direct_s"] = time.perf_counter() - t0
+    return out, ref
 
 
 def run_reference(args):
@@ -192,25 +208,35 @@ def run_reference(args):
     import oracle
     from paper_1602_02244_gb300 import workloads
     n = args.ref_sample
-    leaf = args.leaf or 256  # the leaf size the GPU autotuner settles on for this workload
+    leaf = args.leaf or args.ref_leaf
     xyz, q = workloads.plummer_problem(n, 0)
+    w = workloads.rng(2).normal(size=n)
+
+    def step():
+        t = oracle.Tree(xyz, leaf)
+        t.eval(args.order, q, grad=True)
+        t.eval(args.order, w, grad=True)
+
     for _ in range(min(args.warmup, 1)):
-        oracle.Tree(xyz, leaf).eval(args.order, q)
+        step()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.Tree(xyz, leaf).eval(args.order, q)
+        step()
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     val = n / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "Plummer N=%d (bounded CPU sample of the N=4,194,304 problem), "
-                                   "p=%d, leaf %d, FP64" % (n, args.order, leaf)},
+            "config": {"workload": "Plummer N=%d per step (bounded CPU sample of the N=4,194,304 "
+                                   "problem), p=%d, leaf %d, FP64; step = plan + forward (phi, "
+                                   "grad) + adjoint (the FMM with the loss weights)"
+                                   % (n, args.order, leaf)},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle",
-                             "sample": "Plummer N=%d per step: plan + FP64 FMM eval" % n},
+                             "sample": "Plummer N=%d per step: plan + FP64 FMM forward + adjoint, "
+                                       "leaf %d" % (n, leaf)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -289,9 +315,9 @@ def lattice_leg(dev, order=8):
     L.fmm_memory_usage.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                    ctypes.c_int]
     rows = []
+    from paper_1602_02244_gb300 import workloads
     for side in (16, 32, 64, 128, 160):
-        g = (np.arange(side) + 0.5) / side
-        xyz = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+        xyz = workloads.lattice(side)
         n = len(xyz)
         X = torch.tensor(xyz, device=dev)
         Q = torch.ones(n, dtype=torch.float64, device=dev)
@@ -410,6 +436,19 @@ def dual_leg(X, Q, S, p, precision, theta, rel_err, steps, stream, ms_lists, ms_
             "lists_over_dual_speedup_eval_only": ms_eval / ms_eval_lists}
 
 
+def err_stats(phi, grad, ref_phi, ref_grad, reference):
+    """Relative L2 error over the sampled targets and the largest relative
+    error of one target, for phi and for grad phi (vector norm per target)."""
+    dphi = np.abs(phi - ref_phi)
+    dg = np.linalg.norm(grad - ref_grad, axis=1)
+    gn = np.linalg.norm(ref_grad, axis=1)
+    return {"phi": float(np.linalg.norm(phi - ref_phi) / np.linalg.norm(ref_phi)),
+            "grad": float(np.linalg.norm(grad - ref_grad) / np.linalg.norm(ref_grad)),
+            "phi_max_target": float(np.max(dphi / np.abs(ref_phi))),
+            "grad_max_target": float(np.max(dg / np.where(gn > 0, gn, 1.0))),
+            "targets": int(len(ref_phi)), "reference": reference}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -434,24 +473,31 @@ def run_ours(args):
 
     n, p, S = args.n, args.order, args.leaf
     xyz_np, q_np = workloads.plummer_problem(n, rank)
+    w_np = workloads.rng(2).normal(size=n)  # loss weights: L = sum w_i phi_i
     X = torch.tensor(xyz_np, device=dev)
     Q = torch.tensor(q_np, device=dev)
+    W = torch.tensor(w_np, device=dev)
     plan = binding.Plan(X, leaf_size=S, order=p, precision=args.precision,
                         m2l_path=args.m2l_path, p2p_tile=args.p2p_tile)  # S = 0: autotune
     S = plan.sizes()["leaf_size"]
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     grad = torch.empty(n, 3, dtype=torch.float64, device=dev)
+    dq = torch.empty(n, dtype=torch.float64, device=dev)
+    dx = torch.empty(n, 3, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
     def step():
         plan.rebuild(X)
         plan.eval(Q, out=(phi, grad))
+        plan.adjoint(W, Q, grad_q=grad, out=(dq, dx))
 
+    evals_per_step = 2  # the forward mat-vec and the adjoint's mat-vec with the weights
     for _ in range(max(args.warmup, 3)):
         step()
     pairs, v_pairs, layout = algorithmic_work(plan)
     sizes = plan.sizes()
+    fp32_peak = binding.fp32_peak()  # TFLOP/s, measured on this GPU just before the timed steps
     ms_arr = (ctypes.c_double * 12)()
     la_arr = (ctypes.c_int64 * 12)()
     L.fmm_profile(plan._h, 1)
@@ -482,75 +528,91 @@ def run_ours(args):
     ms = max_over_ranks(float(np.mean(step_ms)), world, dev)
     value = n * world / (ms / 1e3)
 
-    # error statement: the result against the FP64 brute-force sum (fmm_direct)
-    # on 4096 sampled targets
+    # error statement, first against the GPU's FP64 brute-force sum
+    # (fmm_direct) on 4096 sampled targets; the CPU-baseline leg below adds
+    # the oracle's FP64 direct sum at the same targets
     sel = workloads.sample_targets(n, 4096, 1)
     sel_t = torch.tensor(sel, device=dev)
     pd, gd = binding.direct(X, Q, X[sel_t])
     pd, gd = pd.cpu().numpy(), gd.cpu().numpy()
 
     def rel_err(ph, gr):
-        return {"phi": float(np.linalg.norm(ph.cpu().numpy()[sel] - pd) / np.linalg.norm(pd)),
-                "grad": float(np.linalg.norm(gr.cpu().numpy()[sel] - gd) / np.linalg.norm(gd)),
-                "targets": int(len(sel)), "reference": "fmm_direct (FP64 brute force)"}
+        return err_stats(ph.cpu().numpy()[sel], gr.cpu().numpy()[sel], pd, gd,
+                         "fmm_direct (GPU, FP64 brute force)")
 
     err_mixed = rel_err(phi, grad)
+    phi_s, grad_s = phi.cpu().numpy()[sel], grad.cpu().numpy()[sel]
 
     # roofline of the dominant pass
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     max_mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s
+    fp32_nominal = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s
     nc = (p + 1) ** 2
-    work = {"P2P": ("alu", 20.0 * pairs / 1e12, "TFLOP/s", fp32_peak),
-            "M2L": ("alu", 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s", fp32_peak)}
+    work = {"P2P": ("alu", evals_per_step * 20.0 * pairs / 1e12, "TFLOP/s", fp32_peak),
+            "M2L": ("alu", evals_per_step * 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s", fp32_peak)}
     m2l_tensor = args.precision == "mixed" and p <= 10 and args.m2l_path != "simt"
     if m2l_tensor:
         # TF32 tensor peak: the measured sustained bf16 rate x the nominal
         # tf32/bf16 ratio (1.1 / 2.25 dense PFLOP/s); algorithmic flops count
         # one product, not the three of the hi/lo split
         tf32_peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
-        work["M2L"] = ("tensor", 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s", tf32_peak)
-    # bandwidth-bound passes: algorithmic bytes (read + write once) per pass
+        work["M2L"] = ("tensor", evals_per_step * 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s",
+                       tf32_peak)
+    # bandwidth-bound passes: algorithmic bytes (read + write once) per step
     hbm = peaks.get("hbm_gbs", 6800.0)
     nleaves = int(np.sum(layout["box_nchild"] == 0))
     nb = sizes["nboxes"]
     cb = 4 if args.precision == "mixed" else 8
+    e = evals_per_step
     hbm_bytes = {"keys+sort": n * (24 + 12) + 8 * 2 * n * 12,   # keys; 8 radix passes
-                 "P2M": n * 16 + nleaves * nc * cb,
-                 "M2M": 2 * nb * nc * cb,
-                 "L2L": 2 * nb * nc * cb,
-                 "L2P": n * 16 + nleaves * nc * cb + n * 32,
-                 "reduce": n * 64 + n * 32}
-    for k, b in hbm_bytes.items():
-        work[k] = ("hbm", b / 1e9, "GB/s", hbm)
+                 "P2M": e * (n * 16 + nleaves * nc * cb),
+                 "M2M": e * 2 * nb * nc * cb,
+                 "L2L": e * 2 * nb * nc * cb,
+                 "L2P": e * (n * 16 + nleaves * nc * cb + n * 32),
+                 "reduce": e * (n * 64 + n * 32)}
+    for k, bts in hbm_bytes.items():
+        work[k] = ("hbm", bts / 1e9, "GB/s", hbm)
     dom = max(pass_ms, key=pass_ms.get)
     if dom in work:
         bound, units, unit, peak = work[dom]
         achieved = units / (pass_ms[dom] / 1e3)
     else:
-        bound, unit, peak = "hbm", "GB/s", peaks.get("hbm_gbs", 6800.0)
+        bound, unit, peak = "hbm", "GB/s", hbm
         achieved = None
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": (achieved / peak) if achieved else None,
             "traffic": TRAFFIC_BYTES.get((dom, n, p, S, args.precision)),
-            "peak_source": ("FP32: %d SMs x %d lanes x 2 flop x %.0f MHz" % (sms, FP32_LANES_PER_SM, max_mhz)
+            "peak_source": ("FP32: fmm_fp32_peak, paired-FMA chains on this GPU (of measured); "
+                            "nominal %d SMs x %d lanes x 2 flop x %.0f MHz = %.1f TFLOP/s"
+                            % (sms, FP32_LANES_PER_SM, max_mhz, fp32_nominal)
                             if bound == "alu" else
                             "TF32 = measured sustained bf16 x 1.1/2.25 (of measured)" if bound == "tensor"
                             else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
+    if bound == "alu" and achieved:
+        roof["frac_of_nominal"] = achieved / fp32_nominal
     other = {k: {"bound": v[0], "achieved": v[1] / (pass_ms[k] / 1e3), "unit": v[2],
                  "peak": v[3], "frac": v[1] / (pass_ms[k] / 1e3) / v[3]}
              for k, v in work.items() if pass_ms.get(k)}
+    if pass_ms.get("M2L"):
+        # M2L bytes: the gathered source multipoles read once and the locals
+        # written once per evaluation, plus the operator table
+        m2l_bytes = e * (2 * nb * nc * cb) + 343 * nc * nc * cb
+        other["M2L_hbm"] = {"bound": "hbm", "achieved": m2l_bytes / 1e9 / (pass_ms["M2L"] / 1e3),
+                            "unit": "GB/s", "peak": hbm,
+                            "frac": m2l_bytes / 1e9 / (pass_ms["M2L"] / 1e3) / hbm}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": "Plummer N=%d, charges 1/N, p=%d, leaf %d (%s), %s precision; "
-                                   "step = plan (keys, sort, octree, U/V/W/X lists) + eval (phi and "
-                                   "grad)" % (n, p, S, "autotuned" if args.leaf == 0 else "fixed",
-                                              args.precision),
+                                   "step = plan (keys, sort, octree, U/V/W/X lists) + forward "
+                                   "(phi and grad) + adjoint of L = sum w phi (dL/dq, dL/dx; "
+                                   "forward gradient stored)"
+                                   % (n, p, S, "autotuned" if args.leaf == 0 else "fixed",
+                                      args.precision),
                        "m2l": "tensor cores (tcgen05 TF32, three-product split in two MMAs)"
                               if m2l_tensor
                               else "CUDA cores",
@@ -561,13 +623,22 @@ def run_ours(args):
                        "p2p_pairs": pairs},
             "clocks": clk, "gpu_launches": launches, "wall_s_timed": t_wall,
             "pass_ms": pass_ms, "pass_launches": pass_launch, "roofline": roof,
-            "pass_roofline": other, "rel_error_vs_direct": err_mixed}
+            "pass_roofline": other, "fp32_peak_tflops": fp32_peak,
+            "rel_error_vs_direct": err_mixed}
 
-    # plan-reused eval only (the paper's mat-vec application time)
-    L.fmm_profile(plan._h, 0)
+    # plan + forward only, and the mat-vecs without the plan (the paper's
+    # mat-vec application time)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.rebuild(X)
+        plan.eval(Q, out=(phi, grad))
+    e1.record(stream)
+    e1.synchronize()
+    ms_pf = e0.elapsed_time(e1) / args.steps
+    line["plan_forward"] = {"value": n / (ms_pf / 1e3), "unit": UNIT, "ms": ms_pf}
     e0.record(stream)
     for _ in range(args.steps):
         plan.eval(Q, out=(phi, grad))
@@ -575,15 +646,10 @@ def run_ours(args):
     e1.synchronize()
     ms_eval = e0.elapsed_time(e1) / args.steps
     line["eval_only"] = {"value": n / (ms_eval / 1e3), "unit": UNIT, "ms": ms_eval}
-
-    # forward + adjoint (dL/dq, dL/dx for L = sum w phi)
-    W = torch.tensor(workloads.rng(2).normal(size=n), device=dev)
-    plan.adjoint(W, Q, grad_q=grad)
-    barrier()
     e0.record(stream)
     for _ in range(args.steps):
         plan.eval(Q, out=(phi, grad))
-        plan.adjoint(W, Q, grad_q=grad)
+        plan.adjoint(W, Q, grad_q=grad, out=(dq, dx))
     e1.record(stream)
     e1.synchronize()
     ms_fa = e0.elapsed_time(e1) / args.steps
@@ -593,23 +659,34 @@ def run_ours(args):
     if not args.no_e2e:
         hx = torch.tensor(xyz_np).pin_memory()
         hq = torch.tensor(q_np).pin_memory()
+        hw = torch.tensor(w_np).pin_memory()
         hphi = torch.empty(n, dtype=torch.float64).pin_memory()
         hg = torch.empty(n, 3, dtype=torch.float64).pin_memory()
+        hdq = torch.empty(n, dtype=torch.float64).pin_memory()
+        hdx = torch.empty(n, 3, dtype=torch.float64).pin_memory()
+
+        def host_step():
+            plan.solve_adjoint_host_ptr(hx.data_ptr(), hq.data_ptr(), hw.data_ptr(), n,
+                                        hphi.data_ptr(), hg.data_ptr(), hdq.data_ptr(),
+                                        hdx.data_ptr())
+
         for _ in range(2):
-            plan.solve_host_ptr(hx.data_ptr(), hq.data_ptr(), n, hphi.data_ptr(), hg.data_ptr())
+            host_step()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            plan.solve_host_ptr(hx.data_ptr(), hq.data_ptr(), n, hphi.data_ptr(), hg.data_ptr())
+            host_step()
         t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
-        line["e2e"] = {"value": n * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
-                       "d2h_bytes_per_step": 32 * n, "ms": 1e3 * t_e2e}
+        line["e2e"] = {"value": n * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 40 * n,
+                       "d2h_bytes_per_step": 64 * n, "ms": 1e3 * t_e2e}
 
     # plain FP64 GPU FMM at the smallest order whose direct-sum error is no
-    # larger than the mixed-precision result's, for comparison
+    # larger than the mixed-precision result's, the same step timed
     if not args.no_fp64 and args.precision == "mixed":
         phi64 = torch.empty_like(phi)
         g64 = torch.empty_like(grad)
+        dq64 = torch.empty_like(dq)
+        dx64 = torch.empty_like(dx)
         tried = []
         for p64 in range(max(2, p - 3), 13):
             plan64 = binding.Plan(X, leaf_size=S, order=p64, precision="fp64")
@@ -619,12 +696,14 @@ def run_ours(args):
             if e64["phi"] <= err_mixed["phi"] or p64 == 12:
                 break
             plan64.close()
+        plan64.adjoint(W, Q, grad_q=g64, out=(dq64, dx64))
         barrier()
         reps = 2
         e0.record(stream)
         for _ in range(reps):
             plan64.rebuild(X)
             plan64.eval(Q, out=(phi64, g64))
+            plan64.adjoint(W, Q, grad_q=g64, out=(dq64, dx64))
         e1.record(stream)
         e1.synchronize()
         ms64 = e0.elapsed_time(e1) / reps
@@ -638,20 +717,31 @@ def run_ours(args):
                                     "rel_error_vs_direct": e64, "orders_tried": tried,
                                     "mixed_speedup": ms64 / ms,
                                     "mixed_speedup_eval_only": ms64_eval / ms_eval}
+        line["config"]["fp64_equal_error"] = {"order": p64, "ms_per_step": ms64,
+                                              "mixed_speedup": ms64 / ms}
         plan64.close()
 
     if args.dual_theta > 0:
         line["dual_tree"] = dual_leg(X, Q, S, p, args.precision, args.dual_theta, rel_err,
-                                     min(args.steps, 5), stream, ms, ms_eval)
+                                     min(args.steps, 5), stream, ms_pf, ms_eval)
     if not args.no_batch:
         line["batched"] = batched_leg(dev, args.steps, args.warmup)
-    if args.lattice:
+    if not args.no_lattice:
         line["lattice"] = lattice_leg(dev)
     if args.precond:
         line["precond"] = precond_leg(dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_sample, p, S)
+        ncpu = args.cpu_sample or n
+        cpu, ref = cpu_baseline(ncpu, p, S, sel if ncpu == n else workloads.sample_targets(ncpu, 4096, 1))
+        line["cpu_baseline"] = cpu
+        if ncpu == n:
+            # the error statement against the oracle: its FP64 direct sum at
+            # the same 4096 sampled targets
+            line["rel_error_vs_oracle_direct"] = err_stats(phi_s, grad_s, ref[0], ref[1],
+                                                           "oracle direct sum (CPU, FP64)")
+            line["fmm_direct_vs_oracle_direct"] = err_stats(pd, gd, ref[0], ref[1],
+                                                            "oracle direct sum (CPU, FP64)")
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -161,6 +161,17 @@ fmm_status fmm_eval_graph(fmm_plan_t plan, const double *d_q, double *d_phi, dou
 fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_q, int64_t n,
                           double *h_phi, double *h_grad, void *stream);
 
+/* The forward and adjoint step on HOST buffers: copies h_xyz (n x 3), h_q
+ * (n) and the loss weights h_w (n) to the device, rebuilds `plan` for the
+ * points, evaluates phi and grad phi (fmm_eval), then the adjoint of
+ * L = sum_i w_i phi_i with the forward gradient stored (fmm_adjoint), and
+ * copies phi (n), grad (n x 3), dL/dq (n) and dL/dx (n x 3) back.  All
+ * pointers are required.  Returns after the results are on the host.
+ * Errors as fmm_solve_host. */
+fmm_status fmm_solve_adjoint_host(fmm_plan_t plan, const double *h_xyz, const double *h_q,
+                                  const double *h_w, int64_t n, double *h_phi, double *h_grad,
+                                  double *h_dq, double *h_dx, void *stream);
+
 /* Plan layout, for tests and inspection.  sizes[0..9] =
  *   n, nboxes, nlevels, |U|, |V|, |W|, |X|, order, leaf_size, precision.
  * For a dual-tree plan |U| counts P2P leaf pairs and |V| M2L pairs. */
@@ -218,6 +229,14 @@ fmm_status fmm_tc_selftest(int n, int k, const float *d_a, const float *d_b, flo
  * cycles (1..2e9), the kernel records it and returns, and the call reports
  * FMM_ERR_TIMEOUT; the device stays usable.  Synchronous. */
 fmm_status fmm_wait_selftest(int arrive, long long limit_cycles, void *stream);
+
+/* Measured FP32 rate of the current device in TFLOP/s: every SM runs
+ * independent chains of paired fused multiply-adds (fma.rn.f32x2, the
+ * instruction form of the FP32 near field), timed with CUDA events on
+ * `stream`, best of five launches of about a millisecond; 2 flop per FMA.
+ * The roofline denominator of the FP32-bound passes.  Synchronous; a few
+ * milliseconds.  FMM_ERR_INVALID_ARG for a NULL output. */
+fmm_status fmm_fp32_peak(double *tflops, void *stream);
 
 /* Synchronise `stream`, then report FMM_ERR_TIMEOUT (once) if a bounded
  * device-side wait of this plan's kernels gave up since the last call, else

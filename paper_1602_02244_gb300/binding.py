@@ -19,9 +19,9 @@ _STATUS = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_CUDA", 3: "FMM_ERR
            4: "FMM_ERR_TIMEOUT", 5: "FMM_ERR_NONFINITE_INPUT", 6: "FMM_ERR_UNSUPPORTED"}
 
 EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_plan_set_points",
-           "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_sync", "fmm_plan_sizes",
-           "fmm_plan_export", "fmm_plan_destroy", "fmm_direct", "fmm_laplace7_apply",
-           "fmm_wait_selftest",
+           "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_solve_adjoint_host",
+           "fmm_sync", "fmm_plan_sizes", "fmm_plan_export", "fmm_plan_destroy", "fmm_direct",
+           "fmm_laplace7_apply", "fmm_wait_selftest", "fmm_fp32_peak",
            "fmm_status_string", "fmm_last_error_message")
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
@@ -67,6 +67,8 @@ def library():
         L.fmm_eval_graph.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.fmm_sync.argtypes = [_vp, _vp]
         L.fmm_solve_host.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _vp]
+        L.fmm_solve_adjoint_host.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]
+        L.fmm_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
         L.fmm_plan_sizes.argtypes = [_vp, ctypes.POINTER(_i64)]
         L.fmm_plan_export.argtypes = [_vp, _int, _vp, ctypes.c_size_t]
         L.fmm_plan_destroy.argtypes = [_vp]
@@ -188,14 +190,18 @@ class Plan:
 
     __call__ = eval
 
-    def adjoint(self, w, q, grad_q=None, want_dx=True, stream=None):
-        """dL/dq and dL/dx for L = sum w_i phi_i (frozen plan)."""
+    def adjoint(self, w, q, grad_q=None, want_dx=True, out=None, stream=None):
+        """dL/dq and dL/dx for L = sum w_i phi_i (frozen plan).  ``out``:
+        optional (dq, dx) tensors to write into."""
         w = _dev_f64(w, (self.n,), "w")
         q = _dev_f64(q, (self.n,), "q")
         if grad_q is not None:
             grad_q = _dev_f64(grad_q, (self.n, 3), "grad_q")
-        dq = torch.empty(self.n, dtype=torch.float64, device=self.device)
-        dx = torch.empty(self.n, 3, dtype=torch.float64, device=self.device) if want_dx else None
+        if out is not None:
+            dq, dx = out
+        else:
+            dq = torch.empty(self.n, dtype=torch.float64, device=self.device)
+            dx = torch.empty(self.n, 3, dtype=torch.float64, device=self.device) if want_dx else None
         with torch.cuda.device(self.device):
             _check(library().fmm_adjoint(self._h, _ptr(w), _ptr(q), _ptr(grad_q), _ptr(dq),
                                          _ptr(dx), _stream(stream)))
@@ -229,6 +235,16 @@ class Plan:
                                             _stream(stream)))
         self.n = n
         return phi, g
+
+    def solve_adjoint_host_ptr(self, xyz_ptr, q_ptr, w_ptr, n, phi_ptr, grad_ptr, dq_ptr, dx_ptr,
+                               stream=None):
+        """fmm_solve_adjoint_host on raw host pointers: rebuild, forward and
+        adjoint (stored forward gradient) with the copies both ways."""
+        with torch.cuda.device(self.device):
+            _check(library().fmm_solve_adjoint_host(self._h, _vp(xyz_ptr), _vp(q_ptr), _vp(w_ptr), n,
+                                                    _vp(phi_ptr), _vp(grad_ptr), _vp(dq_ptr),
+                                                    _vp(dx_ptr), _stream(stream)))
+        self.n = n
 
     def solve_host_ptr(self, xyz_ptr, q_ptr, n, phi_ptr, grad_ptr, stream=None):
         """fmm_solve_host on raw host pointers (e.g. pinned torch tensors)."""
@@ -311,6 +327,13 @@ def direct(points, q, targets, grad=True, stream=None):
         _check(library().fmm_direct(_ptr(pts), _ptr(qq), n, _ptr(tgt), m, _ptr(phi), _ptr(g),
                                     _stream(stream)))
     return phi, g
+
+
+def fp32_peak(stream=None):
+    """Measured FP32 rate of the current device in TFLOP/s (fmm_fp32_peak)."""
+    v = ctypes.c_double()
+    _check(library().fmm_fp32_peak(ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def laplace7(u, h, out=None, stream=None):

@@ -342,6 +342,40 @@ fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_
   });
 }
 
+fmm_status fmm_solve_adjoint_host(fmm_plan_t plan, const double *h_xyz, const double *h_q,
+                                  const double *h_w, int64_t n, double *h_phi, double *h_grad,
+                                  double *h_dq, double *h_dx, void *stream) {
+  if (!plan) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
+  if (n < 0 || n >= (int64_t(1) << 31)) return fail(FMM_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+  if (n > 0 && (!h_xyz || !h_q || !h_w || !h_phi || !h_grad || !h_dq || !h_dx))
+    return fail(FMM_ERR_INVALID_ARG, "a host pointer is NULL");
+  if (plan->nproblems > 1 && n != plan->prob_off_h.back())
+    return fail(FMM_ERR_INVALID_ARG, "a batch plan solves only for the same problem sizes");
+  return guarded([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->stream = s;
+    if (n == 0) {
+      build_tree(*plan, nullptr, 0);
+      return;
+    }
+    // device staging: xyz 3n, q n, w n | phi n, grad 3n, dq n, dx 3n
+    plan->host_io.resize(13 * (size_t)n, s);
+    double *d_xyz = plan->host_io.p, *d_q = d_xyz + 3 * n, *d_w = d_q + n;
+    double *d_phi = d_w + n, *d_grad = d_phi + n, *d_dq = d_grad + 3 * n, *d_dx = d_dq + n;
+    FMM_CUDA(cudaMemcpyAsync(d_xyz, h_xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaMemcpyAsync(d_q, h_q, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    build_tree(*plan, d_xyz, n);
+    eval_fmm(*plan, d_q, d_phi, d_grad);
+    adjoint_fmm(*plan, d_w, d_q, d_grad, d_dq, d_dx);
+    FMM_CUDA(cudaMemcpyAsync(h_phi, d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaMemcpyAsync(h_grad, d_grad, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaMemcpyAsync(h_dq, d_dq, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaMemcpyAsync(h_dx, d_dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
 fmm_status fmm_plan_sizes(fmm_plan_t plan, int64_t sizes[10]) {
   if (!plan || !sizes) return fail(FMM_ERR_INVALID_ARG, "plan or sizes is NULL");
   if (!plan->v_built) {

@@ -101,6 +101,27 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   }
 }
 
+// Once per plan, for the FP32 near field: the staging record of every U entry
+// and the leaves sorted by decreasing work (targets x sources).  Plan work:
+// the profiler books it under the lists.
+void prepare_p2p_f32(fmm_plan_impl &P) {
+  if (P.p2p_meta_ok) return;
+  cudaStream_t s = P.stream;
+  PassScope ps_(P, kPassLists);
+  const size_t nl = std::max<int64_t>(P.nleaves, 1);
+  P.p2p_meta.resize(std::max<int64_t>(P.nu, 1), s);
+  P.p2p_meta_z.resize(std::max<int64_t>(P.nu, 1), s);
+  P.p2p_key.resize(nl, s);
+  P.p2p_order.resize(nl, s);
+  P.p2p_ticket.resize(1, s);
+  launch_p2p_meta(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
+                  P.box_geo.p, P.box_side.p, P.p2p_meta.p, P.p2p_meta_z.p, P.p2p_key.p,
+                  P.p2p_order.p, s);
+  radix_sort(P.p2p_key, P.p2p_order, P.p2p_key_tmp, P.p2p_order_tmp, P.nleaves, digit_shifts(0, 16),
+             P.s_hist, P.s_scan, s);
+  P.p2p_meta_ok = true;
+}
+
 void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad) {
   const int p = P.order;
   const int64_t n = P.n;
@@ -108,6 +129,7 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   const int lc = P.coarse_fp64_levels;  // M2M/L2L into levels <= lc in FP64
   const bool coarse = lc >= 2;
   ensure_workspace(P, coarse, true);
+  prepare_p2p_f32(P);
   P.src32.resize(n, s);
   {
     PassScope ps_(P, kPassP2M);
@@ -211,21 +233,6 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   {
     PassScope ps_(P, kPassP2P);
     P.p2p_pairs.resize(p2p_pair_floats(n), s);
-    if (!P.p2p_meta_ok) {
-      // once per plan: staging records, and the leaves sorted by work
-      const size_t nl = std::max<int64_t>(P.nleaves, 1);
-      P.p2p_meta.resize(std::max<int64_t>(P.nu, 1), s);
-      P.p2p_meta_z.resize(std::max<int64_t>(P.nu, 1), s);
-      P.p2p_key.resize(nl, s);
-      P.p2p_order.resize(nl, s);
-      P.p2p_ticket.resize(1, s);
-      launch_p2p_meta(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
-                      P.box_geo.p, P.box_side.p, P.p2p_meta.p, P.p2p_meta_z.p, P.p2p_key.p,
-                      P.p2p_order.p, s);
-      radix_sort(P.p2p_key, P.p2p_order, P.p2p_key_tmp, P.p2p_order_tmp, P.nleaves, digit_shifts(0, 16),
-                 P.s_hist, P.s_scan, s);
-      P.p2p_meta_ok = true;
-    }
     P2PScratch scratch{reinterpret_cast<float4 *>(P.p2p_pairs.p), P.p2p_meta.p, P.p2p_meta_z.p,
                        P.p2p_order.p, P.p2p_ticket.p, P.p2p_tile > 0 ? P.p2p_tile : kP2PDefaultTile,
                        P.dev_err.p};

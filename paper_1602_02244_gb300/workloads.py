@@ -87,6 +87,15 @@ def batch_problem(count=256, seed=0, lo=2048, hi=65536):
     return sizes, pts, qs
 
 
+def lattice(side):
+    """side^3 points at the cell centres of a uniform lattice on [0, 1)^3
+    (the paper's benchmark inputs, §4.1): (i + 1/2) / side per axis.  Relative
+    to the root cube's corner they sit exactly on dyadic box boundaries when
+    side is a power of two."""
+    g = (np.arange(side) + 0.5) / side
+    return np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+
+
 def sample_targets(n, k=4096, seed=1):
     """k distinct target indices (all of them when n <= k)."""
     if n <= k:

@@ -44,3 +44,19 @@ def test_direct_edge_cases(cuda):
     phi, grad = binding.direct(X, Q, X)
     assert phi.tolist() == [2.5, 1.5]
     assert grad.tolist() == [[1.25, 0.0, 0.0], [-0.75, 0.0, 0.0]]
+
+
+def test_direct_at_full_size_matches_oracle(cuda):
+    """The reference of the benchmark's error statement: the GPU brute-force
+    sum on the 4,194,304-point Plummer problem at its 4096 sampled targets,
+    against the oracle's FP64 direct sum at the same targets."""
+    n = 4194304
+    xyz, q = workloads.plummer_problem(n, 0)
+    sel = workloads.sample_targets(n, 4096, 1)
+    X, Q = torch.tensor(xyz, device=cuda), torch.tensor(q, device=cuda)
+    phi, grad = binding.direct(X, Q, X[torch.tensor(sel, device=cuda)])
+    po, go = oracle.direct(xyz, q, xyz[sel])
+    phi, grad = phi.cpu().numpy(), grad.cpu().numpy()
+    assert rel(phi, po) <= 1e-13
+    assert rel(grad, go) <= 1e-12
+    assert np.max(np.abs(phi - po) / np.abs(po)) <= 1e-12

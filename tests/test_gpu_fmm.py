@@ -129,23 +129,40 @@ def test_full_size_in_the_benchmarked_configuration_vs_oracle_fmm(cuda):
     assert rel(phi_m, po) <= 1e-5 and rel(g_m, go) <= 1e-4
 
 
+@pytest.mark.parametrize("tile", [1, 2, 3, 4])
 @pytest.mark.parametrize("c", [2, 5, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 300, 449, 1000])
-def test_mixed_near_field_of_one_leaf_is_the_direct_sum(cuda, c):
-    """A root that is a leaf: the mat-vec is the FP32 near-field kernel alone.
-    The counts straddle the lane-group thresholds (a leaf of <= 16, 32, 64
-    targets splits its sources over 8, 4, 2 groups of lanes), several target
-    tiles (> 128) and a leaf larger than one staged batch of sources (> 448).
-    Four coincident points contribute nothing to one another."""
+def test_mixed_near_field_of_one_leaf_is_the_direct_sum(cuda, c, tile):
+    """A root that is a leaf: the mat-vec is the FP32 near-field kernel alone,
+    in each of its staging shapes (192-448 points per buffer).  The counts
+    straddle the lane-group thresholds (a leaf of <= 16, 32, 64 targets splits
+    its sources over 8, 4, 2 groups of lanes), several target tiles (> 128)
+    and a leaf larger than one staged batch (it is staged in parts).  Four
+    coincident points contribute nothing to one another."""
     xyz = workloads.rng(c).uniform(0.0, 1.0, (c, 3))
     xyz[-3:] = xyz[0] if c >= 4 else xyz[-3:]
     q = workloads.rng(c + 1).uniform(-1, 1, c)
-    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=c, order=4, precision="mixed")
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=c, order=4, precision="mixed",
+                        p2p_tile=tile)
     assert plan.sizes()["nboxes"] == 1
     phi, g = plan.eval(torch.tensor(q, device=cuda))
     phi, g = phi.cpu().numpy(), g.cpu().numpy()
     plan.close()
     pd, gd = oracle.direct(xyz, q)
     assert rel(phi, pd) <= 1e-5 and rel(g, gd) <= 1e-4
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3, 4])
+def test_p2p_staging_shapes_match_oracle(cuda, tile):
+    """Every staging shape of the FP32 near field on an adaptive Plummer
+    tree (leaves of 1..48 points, U lists of every length): the mat-vec
+    within the mixed bars of the FP64 oracle FMM, and the shapes within FP32
+    rounding of one another (they differ only in where batch sums start)."""
+    xyz, q = problem("plummer", 40000)
+    phi, g = run_gpu(cuda, xyz, q, 48, 6, precision="mixed", p2p_tile=tile)
+    ref_phi, ref_g = run_gpu(cuda, xyz, q, 48, 6, precision="mixed", p2p_tile=1)
+    po, go = oracle.Tree(xyz, 48).eval(6, q)
+    assert rel(phi, po) <= 1e-5 and rel(g, go) <= 1e-4
+    assert rel(phi, ref_phi) <= 1e-6 and rel(g, ref_g) <= 1e-5
 
 
 def test_coincident_points_and_single_point(cuda):
@@ -175,6 +192,55 @@ def test_host_entry_point_matches_device_path(cuda, precision):
         assert np.array_equal(phi_h, phi_d.cpu().numpy())
         assert np.array_equal(g_h, g_d.cpu().numpy())
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_forward_adjoint_entry_point_matches_device_path(cuda, precision):
+    """fmm_solve_adjoint_host (copies in, rebuild, forward, adjoint with the
+    stored forward gradient, copies out) equals the device calls bit for bit."""
+    xyz, q = problem("plummer", 30000, 3)
+    w = workloads.rng(4).normal(size=len(q))
+    X, Q, W = (torch.tensor(a, device=cuda) for a in (xyz, q, w))
+    dev = binding.Plan(X, leaf_size=32, order=6, precision=precision)
+    phi_d, g_d = dev.eval(Q)
+    dq_d, dx_d = dev.adjoint(W, Q, grad_q=g_d)
+    dev.close()
+    plan = binding.Plan(torch.tensor(workloads.uniform_cube(1000, 1), device=cuda), leaf_size=32,
+                        order=6, precision=precision)
+    n = len(q)
+    out = [np.empty(n), np.empty((n, 3)), np.empty(n), np.empty((n, 3))]
+    xyz_c, q_c, w_c = (np.ascontiguousarray(a) for a in (xyz, q, w))
+    plan.solve_adjoint_host_ptr(xyz_c.ctypes.data, q_c.ctypes.data, w_c.ctypes.data, n,
+                                *(a.ctypes.data for a in out))
+    plan.close()
+    for a, b in zip(out, (phi_d, g_d, dq_d, dx_d)):
+        assert np.array_equal(a, b.cpu().numpy())
+
+
+@pytest.mark.parametrize("side", [16, 64])
+def test_lattice_fp64_matches_oracle_fmm(cuda, side):
+    """The paper's uniform-lattice workload (§4.1), leaf 64, p = 8, unit
+    charges as in the benchmark's lattice leg: FP64 within 1e-12 of the oracle
+    FMM on the same tree, and the mixed path within its bars."""
+    xyz = workloads.lattice(side)
+    q = np.ones(len(xyz))
+    po, go = oracle.Tree(xyz, 64).eval(8, q)
+    phi, g = run_gpu(cuda, xyz, q, 64, 8)
+    assert rel(phi, po) <= 1e-12
+    for a in range(3):
+        assert rel(g[:, a], go[:, a]) <= 1e-12
+    phi_m, g_m = run_gpu(cuda, xyz, q, 64, 8, precision="mixed")
+    assert rel(phi_m, po) <= 1e-5 and rel(g_m, go) <= 1e-4
+
+
+def test_fp32_peak_probe(cuda):
+    """fmm_fp32_peak measures a rate between half and 1.05x the nominal FP32
+    peak of the device (SMs x 128 lanes x 2 flop x the highest SM clock)."""
+    v = binding.fp32_peak()
+    props = torch.cuda.get_device_properties(cuda)
+    nominal = props.multi_processor_count * 128 * 2 * 2.1e9 / 1e12
+    print("measured FP32 peak %.1f TFLOP/s (nominal at 2.1 GHz %.1f)" % (v, nominal))
+    assert 0.5 * nominal <= v <= 1.05 * nominal
 
 
 def test_rebuild_reuses_plan(cuda):

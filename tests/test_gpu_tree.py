@@ -91,3 +91,14 @@ def test_lists_of_a_mixed_plan_built_on_request(cuda):
     plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=24, order=8, precision="mixed")
     compare(plan, oracle.Tree(xyz, 24))
     plan.close()
+
+
+@pytest.mark.parametrize("side", [16, 64])
+def test_lattice_bit_exact(cuda, side):
+    """The paper's own workload (§4.1): a uniform lattice, leaf size 64.  Its
+    points sit exactly on dyadic box boundaries relative to the root cube's
+    corner, the edge case of the quantisation."""
+    xyz = workloads.lattice(side)
+    plan = gpu_plan(cuda, xyz, 64, order=8)
+    compare(plan, oracle.Tree(xyz, 64))
+    plan.close()

@@ -84,15 +84,23 @@ def test_fmm_operator_is_symmetric(kind):
     assert np.all(np.diag(A) == 0.0)
 
 
-def test_gradient_matches_fd_of_frozen_fmm_potential():
-    """dL/dq_k = (A~ w)_k by symmetry: the adjoint of phi = A~ q in q is the
-    same FMM applied to w (linearity checked exactly)."""
+def test_adjoint_in_q_is_the_fmm_of_the_weights():
+    """dL/dq_k = (A~ w)_k for L = w . A~ q (symmetry of the truncated
+    operator): checked by central finite differences of L in q (exact up to
+    rounding, L is linear in q), by the bilinear identity w . A~q = q . A~w,
+    and by linearity."""
     xyz, q = workloads.uniform_cube_problem(3000, seed=2)
     w = workloads.rng(3).normal(size=3000)
     t = oracle.Tree(xyz, 16)
     p = 6
     phi_q = t.eval(p, q, grad=False)
     phi_w = t.eval(p, w, grad=False)
+    h = 1e-4
+    for k in (0, 17, 1234, 2999):
+        e = np.zeros(3000)
+        e[k] = h
+        fd = (w @ t.eval(p, q + e, grad=False) - w @ t.eval(p, q - e, grad=False)) / (2 * h)
+        assert fd == pytest.approx(phi_w[k], rel=1e-7, abs=1e-9 * np.abs(phi_w).max())
     assert w @ phi_q == pytest.approx(q @ phi_w, rel=1e-12)
     a, b = 0.37, -1.9
     np.testing.assert_allclose(t.eval(p, a * q + b * w, grad=False), a * phi_q + b * phi_w,
