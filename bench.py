@@ -68,6 +68,8 @@ def parse():
                          "cores), tensor")
     ap.add_argument("--p2p-tile", type=int, default=0,
                     help="staging shape of the FP32 near-field kernel (0 = default)")
+    ap.add_argument("--m2l-tile", type=int, default=0,
+                    help="operand form of the tensor-core M2L: 1 TF32, 2 FP16 (0 = default)")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="points in the oracle's CPU-baseline run (0 = the full N)")
     ap.add_argument("--ref-sample", type=int, default=524288,
@@ -478,7 +480,8 @@ def run_ours(args):
     Q = torch.tensor(q_np, device=dev)
     W = torch.tensor(w_np, device=dev)
     plan = binding.Plan(X, leaf_size=S, order=p, precision=args.precision,
-                        m2l_path=args.m2l_path, p2p_tile=args.p2p_tile)  # S = 0: autotune
+                        m2l_path=args.m2l_path, p2p_tile=args.p2p_tile,
+                        m2l_tile=args.m2l_tile)  # S = 0: autotune
     S = plan.sizes()["leaf_size"]
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     grad = torch.empty(n, 3, dtype=torch.float64, device=dev)
@@ -613,7 +616,10 @@ def run_ours(args):
                                    "forward gradient stored)"
                                    % (n, p, S, "autotuned" if args.leaf == 0 else "fixed",
                                       args.precision),
-                       "m2l": "tensor cores (tcgen05 TF32, three-product split in two MMAs)"
+                       "m2l": ("tensor cores (tcgen05 kind::tf32, three-product TF32 split)"
+                               if args.m2l_tile == 1 else
+                               "tensor cores (tcgen05 kind::f16, three-product FP16 split with "
+                               "power-of-two scalings)")
                               if m2l_tensor
                               else "CUDA cores",
                        "parallelism": "replicas" if world > 1 else "single",

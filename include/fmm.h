@@ -87,6 +87,11 @@ typedef struct {
                              buffers, resident warps); 0 = the default        */
   double mac_theta;       /* interaction 1: 0 < theta < 1 (0 = default, 0.5);
                              smaller is more accurate and slower              */
+  int m2l_tile;           /* MIXED, tensor-core M2L: operand form, 1 = TF32
+                             hi/lo split (kind::tf32), 2 = FP16 hi/lo split
+                             with power-of-two scalings (kind::f16: half the
+                             operand bytes, twice the MMA rate); 0 = default */
+  int reserved;           /* must be zero                                     */
 } fmm_opts;
 
 /* Build a plan for n points (d_xyz: device, n x 3 FP64).

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("coarse_fp64_levels", ctypes.c_int),
                 ("max_depth", ctypes.c_int), ("m2l_path", ctypes.c_int),
                 ("interaction", ctypes.c_int), ("p2p_tile", ctypes.c_int),
-                ("mac_theta", ctypes.c_double)]
+                ("mac_theta", ctypes.c_double), ("m2l_tile", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 _lib = None
@@ -117,12 +118,13 @@ class Plan:
     over the concatenated points (fmm_plan_create_batch).  ``interaction`` is
     "lists" (U/V/W/X) or "dual" (dual-tree walk with acceptance criterion
     r_T + r_S < theta |c_T - c_S|; ``theta`` 0 = default 0.5).  ``p2p_tile``
-    picks the staging shape of the FP32 near-field kernel (0 = default).
+    picks the staging shape of the FP32 near-field kernel, ``m2l_tile`` the
+    operand form of the tensor-core M2L (1 TF32, 2 FP16; 0 = default).
     """
 
     def __init__(self, points, leaf_size=64, order=8, precision="fp64", coarse_fp64_levels=0,
                  max_depth=0, stream=None, offsets=None, m2l_path="auto", interaction="lists",
-                 theta=0.0, p2p_tile=0):
+                 theta=0.0, p2p_tile=0, m2l_tile=0):
         L = library()
         self.device = points.device
         self.n = int(points.shape[0])
@@ -135,6 +137,7 @@ class Plan:
         opts.interaction = {"lists": 0, "dual": 1}[interaction]
         opts.mac_theta = float(theta)
         opts.p2p_tile = int(p2p_tile)
+        opts.m2l_tile = int(m2l_tile)
         self.interaction = interaction
         self.precision, self.order, self.leaf_size = precision, order, leaf_size
         h = _vp()

@@ -71,6 +71,9 @@ void check_opts(const fmm_opts *o) {
     throw Error(FMM_ERR_INVALID_ARG, "opts.interaction must be 0 or 1");
   if (!(o->mac_theta >= 0.0 && o->mac_theta < 1.0))
     throw Error(FMM_ERR_INVALID_ARG, "opts.mac_theta must be in [0, 1)");
+  if (o->m2l_tile < 0 || o->m2l_tile > 2)
+    throw Error(FMM_ERR_INVALID_ARG, "opts.m2l_tile must be 0, 1 or 2");
+  if (o->reserved != 0) throw Error(FMM_ERR_INVALID_ARG, "opts.reserved must be zero");
   if (o->p2p_tile < 0 || o->p2p_tile > p2p_num_tiles())
     throw Error(FMM_ERR_INVALID_ARG, "opts.p2p_tile must be in 0.." + std::to_string(p2p_num_tiles()));
 }
@@ -84,6 +87,7 @@ void apply_opts(fmm_plan_impl &P, const fmm_opts *o) {
   P.dual = o->interaction == 1;
   P.theta = o->mac_theta > 0.0 ? o->mac_theta : 0.5;
   P.p2p_tile = o->p2p_tile;
+  P.m2l_tile = o->m2l_tile;
 }
 
 }  // namespace
@@ -135,7 +139,8 @@ void release_plan(fmm_plan_impl &P) {
   P.s_scan.release(); P.s_u64a.release(); P.s_u64b.release(); P.s_total.release();
   P.ca_off.release(); P.ca_idx.release(); P.m2l_src.release(); P.m2l_slots.release();
   P.m2l_nslots.release(); P.ops.m2l32p.release(); P.ops.m2l_tc.release(); P.Mhi.release();
-  P.Mlo.release(); P.dev_err.release();
+  P.Mlo.release(); P.dev_err.release(); P.Mscale.release(); P.ops.m2l_tc16.release();
+  P.ops.m2l_tc16_rows.release(); P.ops.m2l_tc16_cols.release();
   P.xslot.release(); P.K64.release(); P.K32.release(); P.box_prob.release();
   P.box_side.release(); P.prob_off.release(); P.prob_geom.release(); P.iperm.release();
   P.ops.m2m32t.release(); P.ops.l2l32t.release();

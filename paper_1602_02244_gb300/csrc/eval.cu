@@ -101,6 +101,20 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   }
 }
 
+// The tensor-core M2L's operand form (TF32 or FP16 split) and its buffers.
+M2LTcForm tc_form(fmm_plan_impl &P) {
+  cudaStream_t s = P.stream;
+  const size_t nb = (size_t)P.nboxes, kt = m2l_tc_pitch(P.order);
+  const bool f16 = P.m2l_tile == 0 ? kM2LTcDefaultF16 : P.m2l_tile == 2;
+  const size_t words = f16 ? kt / 2 : kt;  // floats per box and half
+  P.Mhi.resize(nb * words, s);
+  P.Mlo.resize(nb * words, s);
+  if (f16) P.Mscale.resize(nb, s);
+  return {f16, P.Mhi.p, P.Mlo.p,
+          f16 ? static_cast<const void *>(P.ops.m2l_tc16.p) : static_cast<const void *>(P.ops.m2l_tc.p),
+          P.ops.m2l_tc16_rows.p, P.ops.m2l_tc16_cols.p, P.Mscale.p};
+}
+
 // Once per plan, for the FP32 near field: the staging record of every U entry
 // and the leaves sorted by decreasing work (targets x sources).  Plan work:
 // the profiler books it under the lists.
@@ -167,12 +181,8 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
       const size_t b2 = (size_t)(P.nlevels > 2 ? P.level_off[2] : P.nboxes);
       FMM_CUDA(cudaMemsetAsync(P.L32.p, 0, sizeof(float) * b2 * ldc, s));
       if (P.m2l_tc) {
-        const size_t kt = m2l_tc_pitch(p);
-        P.Mhi.resize((size_t)P.nboxes * kt, s);
-        P.Mlo.resize((size_t)P.nboxes * kt, s);
         launch_m2l_tc(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_src.p, P.m2l_slots.p, P.m2l_nslots.p,
-                      P.m2l_order.p, P.nboxes, P.M32.p, P.Mhi.p, P.Mlo.p, P.ops.m2l_tc.p, P.L32.p,
-                      P.dev_err.p, s);
+                      P.m2l_order.p, P.nboxes, P.M32.p, tc_form(P), P.L32.p, P.dev_err.p, s);
       } else {
         launch_m2l_staged(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_src.p, P.m2l_slots.p,
                           P.m2l_nslots.p, P.m2l_order.p, P.M32.p, P.ops.m2l32p.p, P.L32.p, s);
@@ -184,12 +194,8 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
                             P.m2l_slots.p, P.m2l_nslots.p, P.m2l_order.p, P.M32.p, P.ops.rot32.p,
                             P.ops.zt32.p, P.L32.p, s);
     } else if (P.m2l_tc) {
-      const size_t kt = m2l_tc_pitch(p);
-      P.Mhi.resize((size_t)P.nboxes * kt, s);
-      P.Mlo.resize((size_t)P.nboxes * kt, s);
       launch_m2l_tc(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_src.p, P.m2l_slots.p, P.m2l_nslots.p,
-                    P.m2l_order.p, P.nboxes, P.M32.p, P.Mhi.p, P.Mlo.p, P.ops.m2l_tc.p, P.L32.p,
-                    P.dev_err.p, s);
+                    P.m2l_order.p, P.nboxes, P.M32.p, tc_form(P), P.L32.p, P.dev_err.p, s);
     } else if (p <= kM2LStagedMaxOrder)
       launch_m2l_staged(p, P.nm2l_tiles, P.m2l_tiles.p, P.m2l_src.p, P.m2l_slots.p, P.m2l_nslots.p,
                         P.m2l_order.p, P.M32.p, P.ops.m2l32p.p, P.L32.p, s);

@@ -74,12 +74,22 @@ void launch_m2l_staged(int p, int64_t ntiles, const M2LTile *tiles, const int32_
                        const int16_t *slots, const int32_t *nslots, const int32_t *order,
                        const float *M, const float *opsp, float *L, cudaStream_t s);
 
-// m2l_tc.cu: splits M into Mhi/Mlo (pitch m2l_rows(p)), then contracts on
-// the tensor cores; err is set if a bounded wait gave up
+// m2l_tc.cu: splits M into Mhi/Mlo (pitch m2l_tc_pitch(p) values), then
+// contracts on the tensor cores; err is set if a bounded wait gave up.
+// TF32 form: Mhi/Mlo FP32 (TF32 values), opt from pack_m2l_tc_operators.
+// FP16 form: Mhi/Mlo FP16, opt from pack_m2l_tc16_operators with its row and
+// column scales, mscale one float per box (written by the split).
+constexpr bool kM2LTcDefaultF16 = true;  // the form m2l_tile 0 selects
+struct M2LTcForm {
+  bool f16;
+  void *Mhi, *Mlo;
+  const void *opt;
+  const float *rowscale, *colscale;
+  float *mscale;
+};
 void launch_m2l_tc(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *table,
                    const int16_t *slots, const int32_t *nslots, const int32_t *order, int64_t nb,
-                   const float *M, float *Mhi, float *Mlo, const float *opt, float *L, int *err,
-                   cudaStream_t s);
+                   const float *M, const M2LTcForm &form, float *L, int *err, cudaStream_t s);
 
 // dual.cu: M2L over the dual-tree pairs (cells of any two sizes); writes
 // (or, with accumulate, adds to) L of every box

@@ -19,8 +19,23 @@
 // stage is refilled only after the mbarrier signalled by tcgen05.commit says
 // its MMAs have finished.  All waits are bounded; a timeout sets an error
 // word and the CTA still frees its tensor memory.
+//
+// The FP16 form (kind::f16) carries the same 22 significant bits in half the
+// bytes and at twice the MMA rate: X = X_hi + X_lo with both halves FP16.
+// FP16's exponent range is made to fit by exact power-of-two scalings: the
+// operators are balanced once per order, T'[n][k] = T[n][k] 2^-(e_n + f_k)
+// (all |T'| <= 1); each source multipole is stored as
+// M'_k = M_k 2^(f_k) / s_A with s_A the power of two at or above its largest
+// |M_k 2^(f_k)|; the drain warps add each finished slot as s_A x (slot sum),
+// and the stored local is 2^(e_n) x the accumulated sum.  Rounding stays
+// relative to the largest entry of each row, as in FP32.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <vector>
 #include <type_traits>
+
+#include <cuda_fp16.h>
 
 #include "async_copy.cuh"
 #include "eval_kernels.cuh"
@@ -32,7 +47,8 @@ namespace fmm {
 namespace {
 
 constexpr int kTcTile = 128;     // targets per CTA = MMA M
-constexpr int kTcKC = 32;        // K per stage
+constexpr int kTcKC = 32;        // K per stage (TF32); a stage row is 128 bytes in both forms
+constexpr int kTcRowBytes = 128;
 constexpr long long kTcWaitCycles = 400000000ll;  // ~0.2 s: far beyond any legitimate wait
 
 // Mhi/Mlo[b][k] (pitch kt, zero beyond the nc coefficients) from M[b][k] (pitch ld)
@@ -49,6 +65,35 @@ __global__ void k_split_tf32(int64_t nb, int nc, int ld, int kt, const float *__
 }
 
 __host__ __device__ constexpr int tc_k(int p) { return (ncoef(p) + kTcKC - 1) / kTcKC * kTcKC; }
+
+// FP16 form: M'_b = M_b[k] colscale[k] / s_b split into FP16 halves (pitch kt
+// halves, zero beyond nc), s_b = the power of two at or above max |M_b[k]
+// colscale[k]| (1 for an all-zero row); a warp per box
+__global__ void k_split_f16(int64_t nb, int nc, int ld, int kt, const float *__restrict__ M,
+                            const float *__restrict__ colscale, __half *__restrict__ Mhi,
+                            __half *__restrict__ Mlo, float *__restrict__ mscale) {
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= nb) return;
+  float mx = 0.f;
+  for (int k = lane; k < nc; k += 32) mx = fmaxf(mx, fabsf(M[b * ld + k] * colscale[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  // power of two >= mx: 2^ceil(log2 mx) from the exponent bits (exact)
+  int e = 0;
+  if (mx > 0.f) {
+    const float m = frexpf(mx, &e);  // mx = m 2^e, 0.5 <= m < 1
+    if (m == 0.5f) e -= 1;           // mx is itself a power of two
+  }
+  const float sc = mx > 0.f ? ldexpf(1.f, e) : 1.f, inv = mx > 0.f ? ldexpf(1.f, -e) : 1.f;
+  if (lane == 0) mscale[b] = sc;
+  for (int k = lane; k < kt; k += 32) {
+    const float v = k < nc ? M[b * ld + k] * colscale[k] * inv : 0.f;
+    const __half h = __float2half_rn(v);
+    Mhi[b * kt + k] = h;
+    Mlo[b * kt + k] = __float2half_rn(v - __half2float(h));
+  }
+}
 
 // The tensor core's FP32 accumulation does not round to nearest, so its error
 // grows with the number of accumulations into one tile.  Every slot therefore
@@ -91,14 +136,19 @@ __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity, volatil
   return true;
 }
 
-template <int NT, int NSTAGE>
+// F16: the FP16 form (operands of 2 bytes, kind::f16, scalings as described
+// at the top of the file); else the TF32 form.  Either way a stage row holds
+// 128 bytes of K (32 TF32 or 64 FP16 values), and the last K chunk of an
+// FP16 slot may hold only 32 values (64 bytes, two MMA K steps).
+template <int NT, int NSTAGE, bool F16>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(int p, int kt, const M2LTile *__restrict__ tiles,
              const int32_t *__restrict__ table,
              const int16_t *__restrict__ slots, const int32_t *__restrict__ nslots,
-             const int32_t *__restrict__ order, const float *__restrict__ Mhi,
-             const float *__restrict__ Mlo, const float *__restrict__ opt, float *__restrict__ L,
-             int *__restrict__ err) {
+             const int32_t *__restrict__ order, const unsigned char *__restrict__ Mhi,
+             const unsigned char *__restrict__ Mlo, const unsigned char *__restrict__ opt,
+             const float *__restrict__ mscale, const float *__restrict__ rowscale,
+             float *__restrict__ L, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   __shared__ uint64_t full[NSTAGE], bfull[NSTAGE], empty[NSTAGE], accf[2], acce[2], done;
   __shared__ uint32_t tslot;
@@ -108,8 +158,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // an accumulator holds [A_hi B_hi + A_lo B_hi | A_hi B_lo]: 2N columns
   constexpr uint32_t kCols = 2 * N <= 32 ? 32 : 2 * N <= 64 ? 64 : 2 * N <= 128 ? 128 : 256;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nc = ncoef(p), ld = coef_pitch(p), nch = kt / kTcKC;
-  constexpr uint32_t a_bytes = kTcTile * kTcKC * 4, b_bytes = (uint32_t)N * kTcKC * 4;
+  constexpr int kEsz = F16 ? 2 : 4;  // operand bytes
+  const int nc = ncoef(p), ld = coef_pitch(p);
+  const int kt_bytes = kt * kEsz, nch = (kt_bytes + kTcRowBytes - 1) / kTcRowBytes;
+  // bytes of K in chunk c (128 except possibly the last FP16 chunk)
+  auto chunk_bytes = [&](int c) { return min(kTcRowBytes, kt_bytes - c * kTcRowBytes); };
+  constexpr uint32_t a_bytes = kTcTile * kTcRowBytes, b_bytes = (uint32_t)N * kTcRowBytes;
   constexpr uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;  // a multiple of 1024
   // the swizzled A tiles need a 1024-byte-aligned base (1 KB of slack is allocated)
   unsigned char *sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
@@ -149,8 +203,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp < kTcDrainWarps) {
     // ---------------------------------------------------------------- drain
+    // FP16 form: the scale s_A of this row's source in slot j, looked up one
+    // slot ahead (0 where the slot has no source for this target)
+    const int t = warp * 32 + lane;
+    const int32_t *tab_t = table + (size_t)blockIdx.x * 216 * kTcTile + t;
+    const int16_t *sl = slots + (size_t)blockIdx.x * 216;
+    auto row_scale = [&](int j) {
+      if (!F16 || j >= ns) return 1.f;
+      const int32_t src = tab_t[(int)sl[j] * kTcTile];
+      return src >= 0 ? mscale[src] : 0.f;
+    };
+    float sc_next = row_scale(0);
     for (int j = 0; j < ns; ++j) {
       const int a = j & 1;
+      const float sc = sc_next;
+      sc_next = row_scale(j + 1);
       // warp-uniform outcome: tcgen05.ld is a warp-collective instruction
       const bool ok = __all_sync(0xffffffffu, tc_wait(&accf[a], (uint32_t)(j >> 1) & 1, abort));
       if (!ok) break;
@@ -162,7 +229,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc::tmem_ld16(base + (uint32_t)c0, v);
         tc::tmem_ld16(base + (uint32_t)(N + c0), w);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i] + w[i];
+        for (int i = 0; i < 16; ++i) {
+          if (F16) acc[c0 + i] = fmaf(sc, v[i] + w[i], acc[c0 + i]);
+          else acc[c0 + i] += v[i] + w[i];
+        }
       }
       tc::fence_before_sync();
       tc::mbar_arrive(&acce[a]);
@@ -171,8 +241,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
       // the hi and lo operator slabs are contiguous, i.e. one 2N-row operand
-      const uint32_t idesc2 = tc::idesc_tf32(kTcTile, 2 * N), idesc1 = tc::idesc_tf32(kTcTile, N);
-      constexpr uint32_t sbo = (kTcKC / 4) * 128;
+      const uint32_t idesc2 = F16 ? tc::idesc_f16(kTcTile, 2 * N) : tc::idesc_tf32(kTcTile, 2 * N);
+      const uint32_t idesc1 = F16 ? tc::idesc_f16(kTcTile, N) : tc::idesc_tf32(kTcTile, N);
       bool ok = true;
       for (int j = 0; j < ns && ok; ++j) {
         const int a = j & 1;
@@ -190,14 +260,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tc::fence_after_sync();
           const uint32_t base = tc::smem_addr(sm + (st % NSTAGE) * stage_bytes);
           const uint32_t ah = base, al = base + a_bytes, bh = base + 2 * a_bytes;
-#pragma unroll
-          for (int ks = 0; ks < kTcKC / 8; ++ks) {
+          // the operator slab of this chunk: N rows of cb bytes, core-matrix order
+          const int cb = chunk_bytes(c);
+          const uint32_t sbo = (uint32_t)(cb / 16) * 128;
+          for (int ks = 0; ks < cb / 32; ++ks) {
             const uint64_t dah = tc::smem_desc_sw128(ah + (uint32_t)ks * 32);
             const uint64_t dal = tc::smem_desc_sw128(al + (uint32_t)ks * 32);
             const uint64_t dbh = tc::smem_desc(bh + (uint32_t)ks * 256, 128, sbo);
             // A_hi [B_hi; B_lo] into all 2N columns, then A_lo B_hi into the first N
-            tc::mma_tf32(dtm, dah, dbh, idesc2, (c > 0 || ks > 0) ? 1u : 0u);
-            tc::mma_tf32(dtm, dal, dbh, idesc1, 1u);
+            if (F16) {
+              tc::mma_f16(dtm, dah, dbh, idesc2, (c > 0 || ks > 0) ? 1u : 0u);
+              tc::mma_f16(dtm, dal, dbh, idesc1, 1u);
+            } else {
+              tc::mma_tf32(dtm, dah, dbh, idesc2, (c > 0 || ks > 0) ? 1u : 0u);
+              tc::mma_tf32(dtm, dal, dbh, idesc1, 1u);
+            }
           }
           tc::mma_commit(&empty[st % NSTAGE]);
         }
@@ -225,7 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // missing sources (row -1) are zero-filled by the copy itself (source
     // size 0): pointing them at a shared zero row would make every SM hit the
     // same L2 lines
-    const float *rp[kTcRowsPerProd];
+    const unsigned char *rp[kTcRowsPerProd];
     int rsz[kTcRowsPerProd];
     int32_t next[kTcRowsPerProd];
     int code = 0, next_code = 0;
@@ -245,7 +322,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (c == 0) {
 #pragma unroll
         for (int i = 0; i < kTcRowsPerProd; ++i) {
-          rp[i] = Mhi + (size_t)(next[i] >= 0 ? next[i] : 0) * kt + 4 * kk;
+          rp[i] = Mhi + (size_t)(next[i] >= 0 ? next[i] : 0) * kt_bytes + 16 * kk;
           rsz[i] = next[i] >= 0 ? 16 : 0;
         }
         code = next_code;
@@ -253,16 +330,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       // rows rq + 16 i share (row & 7) = rq & 7, hence the chunk position
       unsigned char *base = sm + s * stage_bytes + tc::sw128_offset(rq, 4 * kk);
+      const int cb = chunk_bytes(c);
+      if (16 * kk < cb) {  // the MMAs of a 64-byte chunk read its first four 16-byte pieces
 #pragma unroll
-      for (int i = 0; i < kTcRowsPerProd; ++i) {
-        const float *src = rp[i] + c * kTcKC;
-        cp_async16(base + i * 16 * 128, src, rsz[i]);
-        cp_async16(base + a_bytes + i * 16 * 128, src + lo_off, rsz[i]);
+        for (int i = 0; i < kTcRowsPerProd; ++i) {
+          const unsigned char *src = rp[i] + c * kTcRowBytes;
+          cp_async16(base + i * 16 * 128, src, rsz[i]);
+          cp_async16(base + a_bytes + i * 16 * 128, src + lo_off, rsz[i]);
+        }
       }
       if (pt == 0) {  // the operator slab (hi and lo halves) is contiguous: one bulk copy
-        const float *bsrc = opt + ((size_t)code * nch + c) * 2 * N * kTcKC;
-        tc::mbar_arrive_expect_tx(&bfull[s], 2 * b_bytes);
-        tc::bulk_g2s(sm + s * stage_bytes + 2 * a_bytes, bsrc, 2 * b_bytes, &bfull[s]);
+        const uint32_t slab = 2u * (uint32_t)N * (uint32_t)cb;
+        const unsigned char *bsrc = opt + (size_t)code * 2 * N * kt_bytes + (size_t)c * 2 * N * kTcRowBytes;
+        tc::mbar_arrive_expect_tx(&bfull[s], slab);
+        tc::bulk_g2s(sm + s * stage_bytes + 2 * a_bytes, bsrc, slab, &bfull[s]);
       }
       cp_async_commit();
       if (st >= kLag) {  // the stage issued kLag steps ago has landed
@@ -294,7 +375,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int32_t B = order[tile.start + t];
 #pragma unroll
       for (int i = 0; i < N; ++i)
-        if (i < nc) L[(size_t)B * ld + i] = acc[i];
+        if (i < nc) L[(size_t)B * ld + i] = F16 ? acc[i] * rowscale[i] : acc[i];
     }
   }
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * kCols);
@@ -342,35 +423,112 @@ void pack_m2l_tc_operators(int p, const double *m2l_in_major, float *out) {
     }
 }
 
+// FP16 form of the operators: exact power-of-two balancing of the 343
+// scale-free matrices, T'[n][k] = T[n][k] 2^-(e_n + f_k) with every |T'| <= 1
+// (alternating row and column maxima over all offsets, a few rounds), then
+// per offset code and K chunk the hi and lo FP16 halves of T' in the K-major
+// core-matrix layout of an N x kc operand (kc = 64, or 32 for a short last
+// chunk).  rowscale[n] = 2^(e_n) (N entries), colscale[k] = 2^(f_k) (kt
+// entries; 1 in the padding).
+size_t m2l_tc16_operator_halves(int p) { return (size_t)343 * 2 * m2l_rows(p) * tc_k(p); }
+
+void pack_m2l_tc16_operators(int p, const double *m2l_in_major, uint16_t *out, float *rowscale,
+                             float *colscale) {
+  const int nc = ncoef(p), N = m2l_rows(p), kt = tc_k(p);
+  const size_t nn = (size_t)nc * nc;
+  auto T = [&](int code, int n, int k) { return m2l_in_major[code * nn + (size_t)k * nc + n]; };
+  std::vector<int> e(nc, 0), f(nc, 0);
+  auto cexp = [](double v) {  // smallest e with v <= 2^e (v > 0)
+    int x = 0;
+    const double m = std::frexp(v, &x);
+    return m == 0.5 ? x - 1 : x;
+  };
+  for (int round = 0; round < 4; ++round) {
+    for (int n = 0; n < nc; ++n) {
+      double mx = 0.0;
+      for (int code = 0; code < 343; ++code)
+        for (int k = 0; k < nc; ++k) mx = std::max(mx, std::fabs(T(code, n, k)) * std::ldexp(1.0, -f[k]));
+      e[n] = mx > 0.0 ? cexp(mx) : 0;
+    }
+    for (int k = 0; k < nc; ++k) {
+      double mx = 0.0;
+      for (int code = 0; code < 343; ++code)
+        for (int n = 0; n < nc; ++n) mx = std::max(mx, std::fabs(T(code, n, k)) * std::ldexp(1.0, -e[n]));
+      f[k] = mx > 0.0 ? cexp(mx) : 0;
+    }
+  }
+  for (int n = 0; n < N; ++n) rowscale[n] = n < nc ? std::ldexp(1.0f, e[n]) : 1.0f;
+  for (int k = 0; k < kt; ++k) colscale[k] = k < nc ? std::ldexp(1.0f, f[k]) : 1.0f;
+  const int kt_bytes = 2 * kt, nch = (kt_bytes + kTcRowBytes - 1) / kTcRowBytes;
+  for (int code = 0; code < 343; ++code)
+    for (int c = 0; c < nch; ++c) {
+      const int kc = std::min(kTcRowBytes, kt_bytes - c * kTcRowBytes) / 2;  // halves in this chunk
+      uint16_t *hi = out + (size_t)code * 2 * N * kt + (size_t)c * 2 * N * (kTcRowBytes / 2);
+      uint16_t *lo = hi + (size_t)N * kc;
+      for (int n = 0; n < N; ++n)
+        for (int kl = 0; kl < kc; ++kl) {
+          const int k = c * (kTcRowBytes / 2) + kl;
+          const float v = (n < nc && k < nc)
+                              ? (float)(T(code, n, k) * std::ldexp(1.0, -e[n] - f[k]))
+                              : 0.f;
+          const __half h = __float2half_rn(v);
+          const __half l = __float2half_rn(v - __half2float(h));
+          // core matrices of 8 rows x 16 bytes; next along K 128 bytes on,
+          // next along N (kc / 8) x 128 bytes on
+          const size_t o = ((size_t)(n / 8) * (kc / 8) * 128 + (size_t)(kl / 8) * 128 + (n % 8) * 16 +
+                            (kl % 8) * 2) / 2;
+          hi[o] = __half_as_ushort(h);
+          lo[o] = __half_as_ushort(l);
+        }
+    }
+}
+
 void launch_m2l_tc(int p, int64_t ntiles, const M2LTile *tiles, const int32_t *table,
                    const int16_t *slots, const int32_t *nslots, const int32_t *order, int64_t nb,
-                   const float *M, float *Mhi, float *Mlo, const float *opt, float *L, int *err,
-                   cudaStream_t s) {
+                   const float *M, const M2LTcForm &form, float *L, int *err, cudaStream_t s) {
   if (ntiles == 0) return;
   const int nc = ncoef(p), ld = coef_pitch(p), kt = tc_k(p), N = m2l_rows(p);
-  k_split_tf32<<<ceil_div(nb * kt, 256), 256, 0, s>>>(nb, nc, ld, kt, M, Mhi, Mlo);
+  const bool f16 = form.f16;
+  if (f16) {
+    k_split_f16<<<ceil_div(nb * 32, 256), 256, 0, s>>>(nb, nc, ld, kt, M, form.colscale,
+                                                        reinterpret_cast<__half *>(form.Mhi),
+                                                        reinterpret_cast<__half *>(form.Mlo),
+                                                        form.mscale);
+  } else {
+    k_split_tf32<<<ceil_div(nb * kt, 256), 256, 0, s>>>(nb, nc, ld, kt, M,
+                                                         reinterpret_cast<float *>(form.Mhi),
+                                                         reinterpret_cast<float *>(form.Mlo));
+  }
   FMM_LAUNCH_CHECK();
   // four stages where they fit in the 227 KB of shared memory per CTA, else three
-  auto run = [&](auto NC) {
+  auto run = [&](auto NC, auto F) {
     constexpr int NTT = decltype(NC)::value;
-    constexpr size_t stage = (size_t)2 * (kTcTile + NTT) * kTcKC * 4;
+    constexpr bool kF16 = decltype(F)::value;
+    constexpr size_t stage = (size_t)2 * (kTcTile + NTT) * kTcRowBytes;
     constexpr int kStages = 4 * stage + 1024 + 512 <= 227 * 1024 ? 4 : 3;
     const size_t smem = kStages * stage + 1024;  // + alignment slack
-    auto kern = k_m2l_tc<NTT, kStages>;
+    auto kern = k_m2l_tc<NTT, kStages, kF16>;
     FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)ntiles, kTcThreads, smem, s>>>(p, kt, tiles, table, slots, nslots, order, Mhi,
-                                                    Mlo, opt, L, err);
+    kern<<<(unsigned)ntiles, kTcThreads, smem, s>>>(
+        p, kt, tiles, table, slots, nslots, order,
+        reinterpret_cast<const unsigned char *>(form.Mhi),
+        reinterpret_cast<const unsigned char *>(form.Mlo),
+        reinterpret_cast<const unsigned char *>(form.opt), form.mscale, form.rowscale, L, err);
   };
-  switch (N) {
-    case 16: run(std::integral_constant<int, 16>()); break;
-    case 32: run(std::integral_constant<int, 32>()); break;
-    case 48: run(std::integral_constant<int, 48>()); break;
-    case 64: run(std::integral_constant<int, 64>()); break;
-    case 96: run(std::integral_constant<int, 96>()); break;
-    case 112: run(std::integral_constant<int, 112>()); break;
-    case 128: run(std::integral_constant<int, 128>()); break;
-    default: throw Error(FMM_ERR_UNSUPPORTED, "tensor-core M2L: unsupported operator size");
-  }
+  auto run_n = [&](auto F) {
+    switch (N) {
+      case 16: run(std::integral_constant<int, 16>(), F); break;
+      case 32: run(std::integral_constant<int, 32>(), F); break;
+      case 48: run(std::integral_constant<int, 48>(), F); break;
+      case 64: run(std::integral_constant<int, 64>(), F); break;
+      case 96: run(std::integral_constant<int, 96>(), F); break;
+      case 112: run(std::integral_constant<int, 112>(), F); break;
+      case 128: run(std::integral_constant<int, 128>(), F); break;
+      default: throw Error(FMM_ERR_UNSUPPORTED, "tensor-core M2L: unsupported operator size");
+    }
+  };
+  if (f16) run_n(std::true_type());
+  else run_n(std::false_type());
   FMM_LAUNCH_CHECK();
 }
 

@@ -336,6 +336,19 @@ void build_operators(fmm_plan_impl &P) {
     P.ops.m2l_tc.resize(packed.size(), s);
     FMM_CUDA(cudaMemcpyAsync(P.ops.m2l_tc.p, packed.data(), packed.size() * sizeof(float),
                              cudaMemcpyHostToDevice, s));
+    // and the FP16 form with its power-of-two scales
+    std::vector<uint16_t> packed16(m2l_tc16_operator_halves(p));
+    std::vector<float> rows(m2l_rows(p)), cols(m2l_tc_pitch(p));
+    pack_m2l_tc16_operators(p, m2l.data(), packed16.data(), rows.data(), cols.data());
+    P.ops.m2l_tc16.resize(packed16.size(), s);
+    P.ops.m2l_tc16_rows.resize(rows.size(), s);
+    P.ops.m2l_tc16_cols.resize(cols.size(), s);
+    FMM_CUDA(cudaMemcpyAsync(P.ops.m2l_tc16.p, packed16.data(), packed16.size() * sizeof(uint16_t),
+                             cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaMemcpyAsync(P.ops.m2l_tc16_rows.p, rows.data(), rows.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, s));
+    FMM_CUDA(cudaMemcpyAsync(P.ops.m2l_tc16_cols.p, cols.data(), cols.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, s));
     FMM_CUDA(cudaStreamSynchronize(s));
   }
   up(m2m, P.ops.m2m64, P.ops.m2m32);

@@ -287,9 +287,15 @@ __device__ __forceinline__ void sweep2(const float4 *s, int s0, int s1, int ktot
 
 // Per U-list entry of the FP32 path, built once per plan (k_p2p_meta): the
 // source leaf's first point and count, and the shift from its frame to the
-// target leaf's (c_A - c_B, exact in FP32: box centres are odd multiples of
-// half a box side in a power-of-two root cube).  One coalesced load per lane
-// gives the warp a whole batch's staging plan.
+// target leaf's, c_A - c_B.  Both centres are (anchor + 1/2) x side with
+// anchors below 2^21 and power-of-two sides, so they and their difference (a
+// multiple of half the smaller side, at most a side apart) are exact in FP32:
+// no FP64 arithmetic, which is scarce on this GPU.  One coalesced load per
+// lane gives the warp a whole batch's staging plan.
+__device__ __forceinline__ float center_f32(int32_t anchor, float side) {
+  return ((float)anchor + 0.5f) * side;
+}
+
 __global__ void k_p2p_meta(int64_t nleaves, const int32_t *__restrict__ leaves,
                            const int32_t *__restrict__ uoff, const int32_t *__restrict__ uidx,
                            const int32_t *__restrict__ first, const int32_t *__restrict__ count,
@@ -301,24 +307,25 @@ __global__ void k_p2p_meta(int64_t nleaves, const int32_t *__restrict__ leaves,
   if (w >= nleaves) return;
   const int32_t B = leaves[w];
   const BoxGeo gb = geo[B];
-  const double sb = side[B];
-  int64_t nsrc = 0;
+  const float sb = (float)side[B];
+  const float bx = center_f32(gb.ix, sb), by = center_f32(gb.iy, sb), bz = center_f32(gb.iz, sb);
+  int32_t nsrc = 0;
   for (int32_t e = uoff[B] + lane; e < uoff[B + 1]; e += 32) {
     const int32_t A = uidx[e];
     const BoxGeo ga = geo[A];
-    const double sa = side[A];
+    const float sa = (float)side[A];
     const int32_t cA = count[A];
     nsrc += cA;
-    meta[e] = make_int4(first[A], cA, __float_as_int((float)center_delta(ga.ix, sa, gb.ix, sb)),
-                        __float_as_int((float)center_delta(ga.iy, sa, gb.iy, sb)));
-    meta_z[e] = (float)center_delta(ga.iz, sa, gb.iz, sb);
+    meta[e] = make_int4(first[A], cA, __float_as_int(center_f32(ga.ix, sa) - bx),
+                        __float_as_int(center_f32(ga.iy, sa) - by));
+    meta_z[e] = center_f32(ga.iz, sa) - bz;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nsrc += __shfl_xor_sync(0xffffffffu, nsrc, o);
   if (lane == 0) {
     // longest first: the key falls as log2(targets x sources) grows (16 bits)
-    const double work = (double)count[B] * (double)nsrc + 1.0;
-    const int lv = (int)fmin(65535.0, log2(work) * 1024.0);
+    const float work = (float)count[B] * (float)nsrc + 1.0f;
+    const int lv = min(65535, (int)(__log2f(work) * 1024.0f));
     cost_key[w] = (uint64_t)(65535 - lv);
     cost_leaf[w] = B;
   }

@@ -24,8 +24,12 @@ struct Operators {
   DBuf<float> m2m32t, l2l32t;
   // FP32 M2L, output-major and zero padded: m2l32p[343][m2l_rows(p)][coef_pitch(p)]
   DBuf<float> m2l32p;
-  // tensor-core M2L: TF32 hi/lo halves in the MMA's core-matrix order
+  // tensor-core M2L: TF32 hi/lo halves in the MMA's core-matrix order, and
+  // the FP16 form (hi/lo halves of the balanced operators, their row and
+  // column power-of-two scales)
   DBuf<float> m2l_tc;
+  DBuf<uint16_t> m2l_tc16;
+  DBuf<float> m2l_tc16_rows, m2l_tc16_cols;
   // rotated M2L (built when a plan uses it): per offset code, the real
   // block-diagonal rotation taking the offset to the z axis, applied to the
   // multipole (rot[code][0]) and back to the local (rot[code][1]), each
@@ -49,6 +53,7 @@ struct fmm_plan_impl {
   bool dual = false;                 // lists from the dual-tree walk (else U/V/W/X)
   double theta = 0.5;                // dual tree: acceptance r_T + r_S < theta |c_T - c_S|
   bool m2l_tc = false;               // this plan's M2L runs on the tensor cores
+  int m2l_tile = 0;                  // tensor-core form: 0 default, 1 TF32 split, 2 FP16 split
   int order = 0, leaf_size = 1, autotune = 0, precision = FMM_FP64, coarse_fp64_levels = 3, max_depth = kMaxDepth;
   cudaStream_t stream = nullptr;
 
@@ -132,7 +137,8 @@ struct fmm_plan_impl {
   int p2p_tile = 0;                 // FP32 near-field staging shape (0 = default)
   DBuf<double> M64, L64;            // nboxes x NC
   DBuf<float> M32, L32;
-  DBuf<float> Mhi, Mlo;             // TF32 split of M32 for the tensor-core M2L
+  DBuf<float> Mhi, Mlo;             // split of M32 for the tensor-core M2L (TF32 or FP16 halves)
+  DBuf<float> Mscale;               // FP16 form: power-of-two scale of each box's split multipole
   DBuf<int> dev_err;                // set by a bounded device wait that gave up
   DBuf<double> K64;                 // M2P coefficient sets of the W sources
   DBuf<float> K32;
@@ -219,8 +225,11 @@ size_t rotation_entries(int p);  // sum_n (2n+1)^2 over n <= p
 void build_m2l_tables(fmm_plan_impl &P);
 // m2l_tc.cu
 size_t m2l_tc_operator_floats(int p);
-size_t m2l_tc_pitch(int p);  // row pitch of the TF32-split multipoles
+size_t m2l_tc_pitch(int p);  // row pitch (values) of the split multipoles
 void pack_m2l_tc_operators(int p, const double *m2l_in_major, float *out);
+size_t m2l_tc16_operator_halves(int p);
+void pack_m2l_tc16_operators(int p, const double *m2l_in_major, uint16_t *out, float *rowscale,
+                             float *colscale);
 // tune.cu: fastest leaf size for these points (cached per size bucket, order, precision)
 int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n);
 // eval.cu

@@ -258,15 +258,18 @@ def test_rebuild_reuses_plan(cuda):
                                        ("sphere", 20000, 16, 6), ("plummer", 8000, 8, 5),
                                        ("uniform", 6000, 12, 9), ("plummer", 5000, 6, 3),
                                        ("uniform", 3000, 20, 4)])
-def test_tensor_core_m2l_matches_cuda_core_path(cuda, kind, n, S, p):
-    """Mixed precision with M2L on the tensor cores (tcgen05, three-product
-    TF32 split) against the same plan with M2L on FP32 CUDA cores, and
-    against the FP64 oracle."""
+@pytest.mark.parametrize("form", [1, 2])
+def test_tensor_core_m2l_matches_cuda_core_path(cuda, kind, n, S, p, form):
+    """Mixed precision with M2L on the tensor cores (tcgen05; form 1: the
+    three-product TF32 split, form 2: the FP16 split with power-of-two
+    scalings) against the same plan with M2L on FP32 CUDA cores, and against
+    the FP64 oracle."""
     xyz, q = problem(kind, n)
     X, Q = torch.tensor(xyz, device=cuda), torch.tensor(q, device=cuda)
     out = {}
     for path in ("simt", "tensor"):
-        plan = binding.Plan(X, leaf_size=S, order=p, precision="mixed", m2l_path=path)
+        plan = binding.Plan(X, leaf_size=S, order=p, precision="mixed", m2l_path=path,
+                            m2l_tile=form)
         phi, g = plan.eval(Q)
         plan.sync()
         out[path] = phi.cpu().numpy(), g.cpu().numpy()
@@ -274,7 +277,7 @@ def test_tensor_core_m2l_matches_cuda_core_path(cuda, kind, n, S, p):
     po, go = oracle.Tree(xyz, S).eval(p, q)
     e_paths = rel(out["tensor"][0], out["simt"][0])
     e_or = rel(out["tensor"][0], po)
-    print(kind, n, S, p, "tensor vs cuda-core %.2e, tensor vs oracle %.2e (cuda-core %.2e)"
+    print(kind, n, S, p, form, "tensor vs cuda-core %.2e, tensor vs oracle %.2e (cuda-core %.2e)"
           % (e_paths, e_or, rel(out["simt"][0], po)))
     assert e_paths <= 3e-6
     assert rel(out["tensor"][1], out["simt"][1]) <= 3e-5
