@@ -541,8 +541,8 @@ __global__ void __launch_bounds__(32 * kL2PWarps, 4)
     K[r] = make_float4(w * k0, w * kx, w * ky, w * kz);
   }
   __syncwarp();
-  const double a = side[b], ia = 1.0 / a, ia2 = ia * ia;
-  const float inva = (float)ia;
+  // 1/a and 1/a^2 are powers of two: the scalings below are exact in FP32
+  const float inva = (float)(1.0 / side[b]), inva2 = inva * inva;
   for (int32_t tc = 0; tc < c; tc += 64) {
     const int32_t i0 = f + tc + lane, i1 = i0 + 32;
     const bool v0 = tc + lane < c, v1 = tc + lane + 32 < c;
@@ -572,8 +572,12 @@ __global__ void __launch_bounds__(32 * kL2PWarps, 4)
                         fz.y = fmaf(kn.w, im.y, fz.y);
                       }
                     });
-    if (v0) out[i0] = make_dbl4((double)fp.x * ia, (double)fx.x * ia2, (double)fy.x * ia2, (double)fz.x * ia2);
-    if (v1) out[i1] = make_dbl4((double)fp.y * ia, (double)fx.y * ia2, (double)fy.y * ia2, (double)fz.y * ia2);
+    if (v0)
+      out[i0] = make_dbl4((double)(fp.x * inva), (double)(fx.x * inva2), (double)(fy.x * inva2),
+                          (double)(fz.x * inva2));
+    if (v1)
+      out[i1] = make_dbl4((double)(fp.y * inva), (double)(fx.y * inva2), (double)(fy.y * inva2),
+                          (double)(fz.y * inva2));
   }
 }
 
@@ -625,6 +629,16 @@ __global__ void k_m2p_prep(int p, int64_t nx, const int32_t *__restrict__ xboxes
   v.z = w * ky;
   v.w = w * kz;
   K[j * ld1 + r] = v;
+}
+
+// hi + lo += v without FP64 arithmetic (scarce on this GPU): Knuth's two_sum
+// gives the rounding error of hi + v exactly, which is carried in lo
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bv = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(v, bv));
+  hi = s;
+  lo = __fadd_rn(lo, err);
 }
 
 // One CTA of 128 threads per target leaf (chunks of 128 targets).  Targets
@@ -752,7 +766,9 @@ __global__ void __launch_bounds__(kM2PThreads)
 // the chunk's target pairs, so a leaf of 94 targets runs two replicas of 48
 // lanes rather than one of 64 (whole warps left 18 % of the lane slots idle
 // on Plummer W leaves).  Lanes of one warp may belong to two replicas; they
-// run the same instructions on different staged boxes.
+// run the same instructions on different staged boxes.  Each box's sums are
+// scaled by its 1/a (a power of two, exact) and added to compensated FP32
+// totals; FP64 only for the per-target results.
 template <int PT>
 __global__ void __launch_bounds__(kM2PThreads)
     k_m2p_f32x2(int p_rt, int nstage, const int32_t *__restrict__ wleaves,
@@ -765,7 +781,6 @@ __global__ void __launch_bounds__(kM2PThreads)
   extern __shared__ __align__(32) unsigned char m2p_smem[];
   float4 *ks = reinterpret_cast<float4 *>(m2p_smem);  // [nstage][ld1]
   __shared__ float s_off[kM2PStage][3], s_inva[kM2PStage];
-  __shared__ double s_ia[kM2PStage];
   __shared__ int32_t s_slot[kM2PStage];
   __shared__ double red[4][2][kM2PThreads];
   const int tid = threadIdx.x;
@@ -785,7 +800,9 @@ __global__ void __launch_bounds__(kM2PThreads)
       s0 = src[f + tc + ti];
       s1 = ti + 1 < tcount ? src[f + tc + ti + 1] : s0;  // a duplicate is evaluated, not stored
     }
-    double phi[2] = {0, 0}, gx[2] = {0, 0}, gy[2] = {0, 0}, gz[2] = {0, 0};
+    // compensated FP32 totals per target and component, (sum, error) pairs:
+    // [component phi, gx, gy, gz][target of the pair]
+    float th[4][2] = {}, tl[4][2] = {};
     for (int32_t e = e0; e < e1; e += nstage) {
       const int nb = min(nstage, e1 - e);
       __syncthreads();  // the previous batch has been consumed
@@ -797,8 +814,7 @@ __global__ void __launch_bounds__(kM2PThreads)
         s_off[tid][0] = (float)center_delta(gb.ix, sb, ga.ix, aa);
         s_off[tid][1] = (float)center_delta(gb.iy, sb, ga.iy, aa);
         s_off[tid][2] = (float)center_delta(gb.iz, sb, ga.iz, aa);
-        s_inva[tid] = (float)(1.0 / aa);
-        s_ia[tid] = 1.0 / aa;
+        s_inva[tid] = (float)(1.0 / aa);  // a power of two: exact
       }
       __syncthreads();
       for (int q = tid; q < nb * nc1; q += kM2PThreads) {
@@ -837,25 +853,20 @@ __global__ void __launch_bounds__(kM2PThreads)
                                 fz.y = fmaf(kn.w, im.y, fz.y);
                               }
                             });
-          const double ia = s_ia[b], ia2 = ia * ia;
-          phi[0] += (double)fp.x * ia;
-          phi[1] += (double)fp.y * ia;
-          gx[0] += (double)fx.x * ia2;
-          gx[1] += (double)fx.y * ia2;
-          gy[0] += (double)fy.x * ia2;
-          gy[1] += (double)fy.y * ia2;
-          gz[0] += (double)fz.x * ia2;
-          gz[1] += (double)fz.y * ia2;
+          const float ia2 = inva * inva;  // exact, as inva
+          const float v[4][2] = {{fp.x * inva, fp.y * inva}, {fx.x * ia2, fx.y * ia2},
+                                 {fy.x * ia2, fy.y * ia2}, {fz.x * ia2, fz.y * ia2}};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) two_sum_acc(th[q][h], tl[q][h], v[q][h]);
         }
       }
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      red[0][h][tid] = phi[h];
-      red[1][h][tid] = gx[h];
-      red[2][h][tid] = gy[h];
-      red[3][h][tid] = gz[h];
-    }
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[q][h][tid] = (double)th[q][h] + (double)tl[q][h];
     __syncthreads();
     // target pair jj (targets 2 jj, 2 jj + 1): replica r holds it at thread r * L + jj
     if (tid < (tcount + 1) / 2) {
