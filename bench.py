@@ -626,7 +626,7 @@ def run_ours(args):
                        "l2": "256 MB flush between steps; working set >> L2",
                        "boxes": sizes["nboxes"], "levels": sizes["nlevels"], "U": sizes["nu"],
                        "V": sizes["nv"], "W": sizes["nw"], "X": sizes["nx"],
-                       "p2p_pairs": pairs},
+                       "p2p_pairs": pairs, "tiles": plan.tiles()},
             "clocks": clk, "gpu_launches": launches, "wall_s_timed": t_wall,
             "pass_ms": pass_ms, "pass_launches": pass_launch, "roofline": roof,
             "pass_roofline": other, "fp32_peak_tflops": fp32_peak,

@@ -182,6 +182,13 @@ fmm_status fmm_solve_adjoint_host(fmm_plan_t plan, const double *h_xyz, const do
  * For a dual-tree plan |U| counts P2P leaf pairs and |V| M2L pairs. */
 fmm_status fmm_plan_sizes(fmm_plan_t plan, int64_t sizes[10]);
 
+/* The kernel shapes a mixed-precision plan evaluates with: the staging shape
+ * of the FP32 near field (1..4, see fmm_opts.p2p_tile) and the operand form
+ * of the tensor-core M2L (1 TF32, 2 FP16) -- the caller's options, else the
+ * autotuner's choice (leaf_size 0), else the defaults.  Either output may be
+ * NULL.  FMM_ERR_INVALID_ARG for a NULL plan. */
+fmm_status fmm_plan_tiles(fmm_plan_t plan, int *p2p_tile, int *m2l_tile);
+
 /* Copy one plan array to host memory (synchronous).  Arrays (element type,
  * length in elements):
  *   0 keys      (uint64, n)         sorted Morton keys
@@ -293,9 +300,11 @@ uint64_t fmm_kernel_launches(void);
  * Scratch comes from one fixed device array of this library (12,906,752
  * bytes: room for FMM_NOALLOC_MAX_POINTS points) that every GPU loading the
  * library holds until the process exits.  n above FMM_NOALLOC_MAX_POINTS is
- * rejected with FMM_ERR_INVALID_ARG.  The first call on a device looks up
- * the array's device address (once per device), so make that first call
- * before any stream capture.  All calls share the array: calls that can
+ * rejected with FMM_ERR_INVALID_ARG, and so is a stream of another device
+ * than the current one.  The first call on a device looks up the array's
+ * device address (once per device; a cudaDeviceReset needs the library
+ * reloaded), so make that first call before any stream capture.  All calls
+ * share the array: calls that can
  * overlap on the GPU (different streams, or different host threads on one
  * device) race and must be serialised by the caller.  Synchronises `stream`
  * (the root cube and the finiteness check are read back).

@@ -21,7 +21,7 @@ _STATUS = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_CUDA", 3: "FMM_ERR
 EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_plan_set_points",
            "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_solve_adjoint_host",
            "fmm_sync", "fmm_plan_sizes", "fmm_plan_export", "fmm_plan_destroy", "fmm_direct",
-           "fmm_laplace7_apply", "fmm_wait_selftest", "fmm_fp32_peak",
+           "fmm_laplace7_apply", "fmm_wait_selftest", "fmm_fp32_peak", "fmm_plan_tiles",
            "fmm_status_string", "fmm_last_error_message")
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
@@ -70,6 +70,7 @@ def library():
         L.fmm_solve_host.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _vp]
         L.fmm_solve_adjoint_host.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]
         L.fmm_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
+        L.fmm_plan_tiles.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]
         L.fmm_plan_sizes.argtypes = [_vp, ctypes.POINTER(_i64)]
         L.fmm_plan_export.argtypes = [_vp, _int, _vp, ctypes.c_size_t]
         L.fmm_plan_destroy.argtypes = [_vp]
@@ -262,6 +263,12 @@ class Plan:
         _check(library().fmm_plan_sizes(self._h, s))
         keys = ("n", "nboxes", "nlevels", "nu", "nv", "nw", "nx", "order", "leaf_size", "precision")
         return dict(zip(keys, [int(v) for v in s]))
+
+    def tiles(self):
+        """(p2p_tile, m2l_tile) this plan evaluates with (fmm_plan_tiles)."""
+        a, b = _int(), _int()
+        _check(library().fmm_plan_tiles(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return {"p2p_tile": a.value, "m2l_tile": b.value}
 
     def export(self):
         """All plan arrays as numpy arrays (see fmm_plan_export)."""

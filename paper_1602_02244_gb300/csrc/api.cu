@@ -86,8 +86,8 @@ void apply_opts(fmm_plan_impl &P, const fmm_opts *o) {
   P.max_depth = o->max_depth == 0 ? kMaxDepth : o->max_depth;
   P.dual = o->interaction == 1;
   P.theta = o->mac_theta > 0.0 ? o->mac_theta : 0.5;
-  P.p2p_tile = o->p2p_tile;
-  P.m2l_tile = o->m2l_tile;
+  P.p2p_tile = P.p2p_tile_user = o->p2p_tile;
+  P.m2l_tile = P.m2l_tile_user = o->m2l_tile;
 }
 
 }  // namespace
@@ -379,6 +379,13 @@ fmm_status fmm_solve_adjoint_host(fmm_plan_t plan, const double *h_xyz, const do
     FMM_CUDA(cudaMemcpyAsync(h_dx, d_dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
     FMM_CUDA(cudaStreamSynchronize(s));
   });
+}
+
+fmm_status fmm_plan_tiles(fmm_plan_t plan, int *p2p_tile, int *m2l_tile) {
+  if (!plan) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
+  if (p2p_tile) *p2p_tile = plan->p2p_tile > 0 ? plan->p2p_tile : kP2PDefaultTile;
+  if (m2l_tile) *m2l_tile = plan->m2l_tile > 0 ? plan->m2l_tile : (kM2LTcDefaultF16 ? 2 : 1);
+  return FMM_OK;
 }
 
 fmm_status fmm_plan_sizes(fmm_plan_t plan, int64_t sizes[10]) {

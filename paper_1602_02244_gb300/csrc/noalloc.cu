@@ -11,6 +11,7 @@
 // and held until the process exits.  The caller provides the inputs and
 // outputs.
 #include <mutex>
+#include <vector>
 
 #include "plan.cuh"
 #include "sort.cuh"
@@ -49,9 +50,22 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_scratch_mu;
 unsigned char *g_scratch_addr[kMaxDevices] = {};
 
-unsigned char *scratch_for_current_device() {
+// The radix passes: the digits of a Morton key (3 bits per level), padded to
+// an even pass count so that the sorted result ends in the caller's arrays.
+constexpr int kKeyBits = 3 * kMaxDepth;
+constexpr int kPasses = ((kKeyBits + 7) / 8 + 1) / 2 * 2;
+static_assert(kPasses == 8, "the 63-bit keys take eight 8-bit passes");
+
+unsigned char *scratch_for_device(cudaStream_t s) {
   int dev = 0;
   FMM_CUDA(cudaGetDevice(&dev));
+  if (s) {  // a stream of another device would run the kernels against that device's array
+    int sdev = dev;
+    FMM_CUDA(cudaStreamGetDevice(s, &sdev));
+    if (sdev != dev)
+      throw Error(FMM_ERR_INVALID_ARG,
+                  "fmm_morton_sort_noalloc: the stream belongs to another device than the current one");
+  }
   if (dev < 0 || dev >= kMaxDevices) throw Error(FMM_ERR_UNSUPPORTED, "device index out of range");
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
@@ -84,7 +98,7 @@ extern "C" fmm_status fmm_morton_sort_noalloc(const double *d_xyz, int64_t n, ui
     return record_error(FMM_ERR_INVALID_ARG, "fmm_morton_sort_noalloc: a device pointer is NULL");
   try {
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned char *base = scratch_for_current_device();
+    unsigned char *base = scratch_for_device(s);
     if (n == 0) return FMM_OK;
     double *partial = reinterpret_cast<double *>(base + kPartialOff);
     double *geom = reinterpret_cast<double *>(base + kGeomOff);
@@ -98,9 +112,11 @@ extern "C" fmm_status fmm_morton_sort_noalloc(const double *d_xyz, int64_t n, ui
       return record_error(FMM_ERR_NONFINITE_INPUT, "a coordinate is NaN or infinite");
     if (h_root)
       for (int a = 0; a < 4; ++a) h_root[a] = hg[a];
-    const int shifts[8] = {0, 8, 16, 24, 32, 40, 48, 56};  // 63-bit keys, even pass count
+    // the plan's digit order (digit_shifts(0, 3 * kMaxDepth)), padded to kPasses
+    std::vector<int> shifts = digit_shifts(0, kKeyBits);
+    while ((int)shifts.size() < kPasses) shifts.push_back(shifts.back() + 8);
     radix_sort_raw(d_keys, d_perm, reinterpret_cast<uint64_t *>(base + kTmpKeysOff),
-                   reinterpret_cast<int32_t *>(base + kTmpValsOff), n, shifts, 8,
+                   reinterpret_cast<int32_t *>(base + kTmpValsOff), n, shifts.data(), kPasses,
                    reinterpret_cast<int32_t *>(base + kHistOff),
                    reinterpret_cast<int32_t *>(base + kScanOff), s);
     return FMM_OK;

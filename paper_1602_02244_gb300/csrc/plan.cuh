@@ -135,6 +135,7 @@ struct fmm_plan_impl {
   DBuf<int32_t> p2p_ticket;
   bool p2p_meta_ok = false;         // p2p_meta and p2p_order match the current lists
   int p2p_tile = 0;                 // FP32 near-field staging shape (0 = default)
+  int p2p_tile_user = 0, m2l_tile_user = 0;  // the caller's tile options (0 = tuned or default)
   DBuf<double> M64, L64;            // nboxes x NC
   DBuf<float> M32, L32;
   DBuf<float> Mhi, Mlo;             // split of M32 for the tensor-core M2L (TF32 or FP16 halves)

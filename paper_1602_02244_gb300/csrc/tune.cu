@@ -1,15 +1,19 @@
-// tune.cu -- leaf-size autotuner.  fmm_plan_create/rebuild with leaf_size 0
-// times plan + mat-vec on the caller's own points for a ladder of leaf sizes
-// and keeps the fastest.  The balance it settles is the paper's compute-memory
+// tune.cu -- autotuner.  fmm_plan_create/rebuild with leaf_size 0 times
+// plan + mat-vec on the caller's own points for a ladder of leaf sizes and
+// keeps the fastest.  The balance it settles is the paper's compute-memory
 // trade-off inside the FMM (§1): larger leaves move work from the
-// translations (M2L) to the dense near field (P2P).  Results are cached per
-// (size bucket, order, precision, list builder) for the life of the process.
+// translations (M2L) to the dense near field (P2P).  A mixed-precision plan
+// then times the mat-vec at that leaf size with each staging shape of the
+// FP32 near-field kernel and each operand form of the tensor-core M2L (the
+// tile options the caller left at 0).  Results are cached per (size bucket,
+// order, precision, list builder and theta, the caller's tile options) for
+// the life of the process.
 #include <cmath>
 #include <map>
 #include <mutex>
 #include <tuple>
 
-#include "plan.cuh"
+#include "eval_kernels.cuh"
 
 namespace fmm {
 
@@ -20,18 +24,28 @@ __global__ void k_fill(int64_t n, double v, double *out) {
   if (i < n) out[i] = v;
 }
 
+struct Tuned {
+  int leaf, p2p_tile, m2l_tile;  // tiles: 0 = the caller's choice stands
+};
+
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, double>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int, double, int, int>, Tuned> g_tune_cache;
 
 }  // namespace
 
 int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   const int bucket = n > 0 ? (int)std::floor(std::log2((double)n)) : 0;
-  const auto key = std::make_tuple(bucket, P.order, P.precision, (int)P.dual, P.dual ? P.theta : 0.0);
+  const auto key = std::make_tuple(bucket, P.order, P.precision, (int)P.dual, P.dual ? P.theta : 0.0,
+                                   P.p2p_tile_user, P.m2l_tile_user);
+  auto apply = [&](const Tuned &t) {
+    if (t.p2p_tile) P.p2p_tile = t.p2p_tile;
+    if (t.m2l_tile) P.m2l_tile = t.m2l_tile;
+    return t.leaf;
+  };
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end()) return it->second;
+    if (it != g_tune_cache.end()) return apply(it->second);
   }
   // finer steps where the optimum usually sits (64..256 for p = 6..10)
   static const int ladder[] = {16,  24,  32,  48,  64,  80,  96,  112, 128,
@@ -48,6 +62,7 @@ int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   FMM_CUDA(cudaEventCreate(&b));
   int best = 64;
   float best_ms = 1e30f;
+  Tuned tuned = {0, 0, 0};
   const bool prof = P.prof_on;
   P.prof_on = false;
   try {
@@ -71,6 +86,40 @@ int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
         best = S;
       }
     }
+    if (P.precision == FMM_MIXED) {
+      // the kernel shapes at the chosen leaf size: the mat-vec alone
+      P.leaf_size = best;
+      build_tree(P, d_xyz, n);
+      auto time_eval = [&]() {
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          FMM_CUDA(cudaEventRecord(a, s));
+          eval_fmm(P, q.p, phi.p, grad.p);
+          FMM_CUDA(cudaEventRecord(b, s));
+          FMM_CUDA(cudaEventSynchronize(b));
+          float t = 0.f;
+          FMM_CUDA(cudaEventElapsedTime(&t, a, b));
+          if (rep > 0) t_min = std::min(t_min, t);  // the first run builds workspace
+        }
+        return t_min;
+      };
+      auto pick = [&](int &field, int lo, int hi) {
+        int choice = lo;
+        float choice_ms = 1e30f;
+        for (int v = lo; v <= hi; ++v) {
+          field = v;
+          const float t = time_eval();
+          if (t < choice_ms) {
+            choice_ms = t;
+            choice = v;
+          }
+        }
+        field = choice;
+        return choice;
+      };
+      if (P.p2p_tile_user == 0) tuned.p2p_tile = pick(P.p2p_tile, 1, p2p_num_tiles());
+      if (P.m2l_tc && P.m2l_tile_user == 0) tuned.m2l_tile = pick(P.m2l_tile, 1, 2);
+    }
   } catch (...) {
     P.prof_on = prof;
     cudaEventDestroy(a);
@@ -86,8 +135,9 @@ int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   q.release();
   phi.release();
   grad.release();
+  tuned.leaf = best;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = best;
+  g_tune_cache[key] = tuned;
   return best;
 }
 

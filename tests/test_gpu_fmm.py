@@ -309,3 +309,24 @@ def test_rotated_m2l_mixed_vs_oracle(cuda, kind, n, S, p):
     po, go = oracle.Tree(xyz, S).eval(p, q)
     assert rel(phi, po) <= 1e-5
     assert rel(g, go) <= 1e-4
+
+
+def test_autotuner_picks_kernel_shapes(cuda):
+    """leaf_size 0 on a mixed plan: the autotuner also chooses the FP32
+    near-field staging shape and the tensor-core M2L operand form (reported
+    by fmm_plan_tiles and kept by a rebuild); explicit options stand."""
+    xyz, q = problem("plummer", 60000, 7)
+    X, Q = torch.tensor(xyz, device=cuda), torch.tensor(q, device=cuda)
+    plan = binding.Plan(X, leaf_size=0, order=6, precision="mixed")
+    t = plan.tiles()
+    assert 1 <= t["p2p_tile"] <= 4 and t["m2l_tile"] in (1, 2)
+    S = plan.sizes()["leaf_size"]
+    phi, g = plan.eval(Q)
+    plan.rebuild(X)
+    assert plan.tiles() == t and plan.sizes()["leaf_size"] == S
+    plan.close()
+    po, go = oracle.Tree(xyz, S).eval(6, q)
+    assert rel(phi.cpu().numpy(), po) <= 1e-5 and rel(g.cpu().numpy(), go) <= 1e-4
+    fixed = binding.Plan(X, leaf_size=0, order=6, precision="mixed", p2p_tile=3, m2l_tile=1)
+    assert fixed.tiles() == {"p2p_tile": 3, "m2l_tile": 1}
+    fixed.close()
