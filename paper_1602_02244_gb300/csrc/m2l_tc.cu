@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ uint64_t full[NSTAGE], bfull[NSTAGE], empty[NSTAGE], accf[2], acce[2], done;
   __shared__ uint32_t tslot;
   __shared__ int abort_word;
+  __shared__ int16_t s_slots[216];  // the tile's occupied slots, in order
   volatile int *abort = &abort_word;
   constexpr int N = NT;
   // an accumulator holds [A_hi B_hi + A_lo B_hi | A_hi B_lo]: 2N columns
@@ -191,6 +192,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::mbar_init(&done, 1);
     abort_word = 0;
   }
+  for (int j = tid; j < ns; j += kTcThreads) s_slots[j] = slots[(size_t)blockIdx.x * 216 + j];
   if (warp == 0) tc::tmem_alloc(&tslot, 2 * kCols);
   tc::fence_before_sync();
   __syncthreads();
@@ -203,21 +205,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp < kTcDrainWarps) {
     // ---------------------------------------------------------------- drain
-    // FP16 form: the scale s_A of this row's source in slot j, looked up one
-    // slot ahead (0 where the slot has no source for this target)
+    // FP16 form: the scale s_A of this row's source in slot j (0 where the
+    // slot has no source for this target).  Its two dependent loads (source
+    // box, then scale) are pipelined over the slots: at slot j the box of
+    // slot j + 2 and the scale of slot j + 1 are requested, so no load is
+    // waited for within the slot it was issued in.
     const int t = warp * 32 + lane;
     const int32_t *tab_t = table + (size_t)blockIdx.x * 216 * kTcTile + t;
-    const int16_t *sl = slots + (size_t)blockIdx.x * 216;
-    auto row_scale = [&](int j) {
-      if (!F16 || j >= ns) return 1.f;
-      const int32_t src = tab_t[(int)sl[j] * kTcTile];
-      return src >= 0 ? mscale[src] : 0.f;
-    };
-    float sc_next = row_scale(0);
+    auto src_of = [&](int j) { return F16 && j < ns ? tab_t[(int)s_slots[j] * kTcTile] : -1; };
+    auto scale_of = [&](int32_t src) { return src >= 0 ? mscale[src] : 0.f; };
+    int32_t src_next = src_of(1);
+    float sc_next = F16 ? scale_of(src_of(0)) : 1.f;
     for (int j = 0; j < ns; ++j) {
       const int a = j & 1;
       const float sc = sc_next;
-      sc_next = row_scale(j + 1);
+      if (F16) {
+        const int32_t src_after = src_of(j + 2);
+        sc_next = scale_of(src_next);
+        src_next = src_after;
+      }
       // warp-uniform outcome: tcgen05.ld is a warp-collective instruction
       const bool ok = __all_sync(0xffffffffu, tc_wait(&accf[a], (uint32_t)(j >> 1) & 1, abort));
       if (!ok) break;
@@ -297,7 +303,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int kk = pt & 7, rq = pt >> 3;
     const int px = tile.parity & 1, py = (tile.parity >> 1) & 1, pz = (tile.parity >> 2) & 1;
     const int32_t *tab = table + (size_t)blockIdx.x * 216 * kTcTile;
-    const int16_t *sl = slots + (size_t)blockIdx.x * 216;
     const size_t lo_off = (size_t)(Mlo - Mhi);
     // missing sources (row -1) are zero-filled by the copy itself (source
     // size 0): pointing them at a shared zero row would make every SM hit the
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int32_t next[kTcRowsPerProd];
     int code = 0, next_code = 0;
     auto fetch = [&](int j) {  // source rows and operator code of slot j
-      const int slot = sl[j];
+      const int slot = s_slots[j];
       const int sx = slot / 36, sy = (slot / 6) % 6, sz = slot % 6;
       next_code = (2 + px - sx + 3) * 49 + (2 + py - sy + 3) * 7 + (2 + pz - sz + 3);
 #pragma unroll
