@@ -245,8 +245,9 @@ fmm_status fmm_wait_selftest(int arrive, long long limit_cycles, void *stream);
 /* Measured FP32 rate of the current device in TFLOP/s: every SM runs
  * independent chains of paired fused multiply-adds (fma.rn.f32x2, the
  * instruction form of the FP32 near field), timed with CUDA events on
- * `stream`, best of five launches of about a millisecond; 2 flop per FMA.
- * The roofline denominator of the FP32-bound passes.  Synchronous; a few
+ * `stream`, the best over four launch shapes (8 or 16 chains per thread,
+ * 256 or 512 threads per block) of five launches each; 2 flop per FMA.  The
+ * roofline denominator of the FP32-bound passes.  Synchronous; some tens of
  * milliseconds.  FMM_ERR_INVALID_ARG for a NULL output. */
 fmm_status fmm_fp32_peak(double *tflops, void *stream);
 
