@@ -170,9 +170,11 @@ fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_
  * (n) and the loss weights h_w (n) to the device, rebuilds `plan` for the
  * points, evaluates phi and grad phi (fmm_eval), then the adjoint of
  * L = sum_i w_i phi_i with the forward gradient stored (fmm_adjoint), and
- * copies phi (n), grad (n x 3), dL/dq (n) and dL/dx (n x 3) back.  All
- * pointers are required.  Returns after the results are on the host.
- * Errors as fmm_solve_host. */
+ * copies phi (n), grad (n x 3), dL/dq (n) and dL/dx (n x 3) back.  The
+ * weights' upload overlaps the tree build, and phi and grad come down while
+ * the adjoint runs, on a side stream of the plan ordered by events.  All
+ * pointers are required; pinned host memory is fastest.  Returns after the
+ * results are on the host.  Errors as fmm_solve_host. */
 fmm_status fmm_solve_adjoint_host(fmm_plan_t plan, const double *h_xyz, const double *h_q,
                                   const double *h_w, int64_t n, double *h_phi, double *h_grad,
                                   double *h_dq, double *h_dx, void *stream);

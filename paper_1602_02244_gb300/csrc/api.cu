@@ -122,6 +122,15 @@ void drop_graph(fmm_plan_impl &P) {
 
 void release_plan(fmm_plan_impl &P) {
   drop_graph(P);
+  for (auto &e : P.copy_ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+  if (P.copy_stream) {
+    cudaStreamDestroy(P.copy_stream);
+    P.copy_stream = nullptr;
+  }
   P.geom.release(); P.partial.release(); P.keys.release(); P.keys_tmp.release();
   P.perm.release(); P.perm_tmp.release(); P.xyz_sorted.release(); P.pl64.release();
   P.pl32.release(); P.box_key.release(); P.box_level.release(); P.box_first.release();
@@ -363,20 +372,35 @@ fmm_status fmm_solve_adjoint_host(fmm_plan_t plan, const double *h_xyz, const do
       build_tree(*plan, nullptr, 0);
       return;
     }
+    fmm_plan_impl &P = *plan;
+    if (!P.copy_stream) FMM_CUDA(cudaStreamCreateWithFlags(&P.copy_stream, cudaStreamNonBlocking));
+    for (auto &e : P.copy_ev)
+      if (!e) FMM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaStream_t c = P.copy_stream;
     // device staging: xyz 3n, q n, w n | phi n, grad 3n, dq n, dx 3n
-    plan->host_io.resize(13 * (size_t)n, s);
-    double *d_xyz = plan->host_io.p, *d_q = d_xyz + 3 * n, *d_w = d_q + n;
+    P.host_io.resize(13 * (size_t)n, s);
+    double *d_xyz = P.host_io.p, *d_q = d_xyz + 3 * n, *d_w = d_q + n;
     double *d_phi = d_w + n, *d_grad = d_phi + n, *d_dq = d_grad + 3 * n, *d_dx = d_dq + n;
+    // the side stream starts after the staging buffer exists (stream order on s)
+    FMM_CUDA(cudaEventRecord(P.copy_ev[0], s));
+    FMM_CUDA(cudaStreamWaitEvent(c, P.copy_ev[0], 0));
     FMM_CUDA(cudaMemcpyAsync(d_xyz, h_xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
     FMM_CUDA(cudaMemcpyAsync(d_q, h_q, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    build_tree(*plan, d_xyz, n);
-    eval_fmm(*plan, d_q, d_phi, d_grad);
-    adjoint_fmm(*plan, d_w, d_q, d_grad, d_dq, d_dx);
-    FMM_CUDA(cudaMemcpyAsync(h_phi, d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    FMM_CUDA(cudaMemcpyAsync(h_grad, d_grad, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    // the loss weights go up while the tree is built
+    FMM_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(double) * n, cudaMemcpyHostToDevice, c));
+    FMM_CUDA(cudaEventRecord(P.copy_ev[1], c));
+    build_tree(P, d_xyz, n);
+    eval_fmm(P, d_q, d_phi, d_grad);
+    // phi and grad come down while the adjoint runs (it only reads d_grad)
+    FMM_CUDA(cudaEventRecord(P.copy_ev[2], s));
+    FMM_CUDA(cudaStreamWaitEvent(c, P.copy_ev[2], 0));
+    FMM_CUDA(cudaMemcpyAsync(h_phi, d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, c));
+    FMM_CUDA(cudaMemcpyAsync(h_grad, d_grad, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c));
+    FMM_CUDA(cudaStreamWaitEvent(s, P.copy_ev[1], 0));  // w has landed
+    adjoint_fmm(P, d_w, d_q, d_grad, d_dq, d_dx);
     FMM_CUDA(cudaMemcpyAsync(h_dq, d_dq, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     FMM_CUDA(cudaMemcpyAsync(h_dx, d_dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaStreamSynchronize(c));
     FMM_CUDA(cudaStreamSynchronize(s));
   });
 }

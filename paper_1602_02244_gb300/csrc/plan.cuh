@@ -56,6 +56,10 @@ struct fmm_plan_impl {
   int m2l_tile = 0;                  // tensor-core form: 0 default, 1 TF32 split, 2 FP16 split
   int order = 0, leaf_size = 1, autotune = 0, precision = FMM_FP64, coarse_fp64_levels = 3, max_depth = kMaxDepth;
   cudaStream_t stream = nullptr;
+  // host-buffer calls: a side stream for copies that overlap the computation,
+  // and the events that order it against `stream` (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[3] = {nullptr, nullptr, nullptr};
 
   // problems: a plan holds one problem, or a batch of independent problems
   // (a forest: each problem has its own root cube and tree; they never
