@@ -48,9 +48,12 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel, from one ncu capture of the same kernel and workload, keyed
-# by (pass, N, order, leaf size, precision); any other configuration, or a
+# by (pass, N, order, leaf size, precision, staging shape); any other
+# configuration, or a
 # kernel changed since the capture, reports null.
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {
+    ("P2P", 4194304, 8, 128, "mixed", 1): 423.07e6,  # k_p2p_f32<160, 2, 16>
+}
 
 
 def parse():
@@ -81,6 +84,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-problem leg")
+    ap.add_argument("--batch-leaf", type=int, default=0,
+                    help="leaf size of the batched leg; 0 = autotune (default)")
     ap.add_argument("--dual-theta", type=float, default=0.75,
                     help="also time the dual-tree walk (acceptance theta) on the same points; 0 skips")
     ap.add_argument("--precond", action="store_true",
@@ -269,10 +274,10 @@ def algorithmic_work(plan):
     return pairs, v_pairs, e
 
 
-def batched_leg(dev, steps, warmup):
+def batched_leg(dev, steps, warmup, leaf=0):
     """256 independent uniform problems, N log-uniform in [2048, 65536], p = 6,
-    mixed precision, autotuned leaf size: forward (phi, grad) plus adjoint
-    (dL/dq, dL/dx) replayed as one CUDA graph per step."""
+    mixed precision, leaf size `leaf` (0: autotuned): forward (phi, grad) plus
+    adjoint (dL/dq, dL/dx) replayed as one CUDA graph per step."""
     import torch
     from paper_1602_02244_gb300 import binding, workloads
     sizes, pts, qs = workloads.batch_problem(256, 0)
@@ -281,7 +286,7 @@ def batched_leg(dev, steps, warmup):
     X = torch.tensor(np.vstack(pts), device=dev)
     Q = torch.tensor(np.concatenate(qs), device=dev)
     W = torch.tensor(workloads.rng(2).normal(size=total), device=dev)
-    plan = binding.Plan(X, leaf_size=0, order=6, precision="mixed", offsets=off)
+    plan = binding.Plan(X, leaf_size=leaf, order=6, precision="mixed", offsets=off)
     s = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(s):
         phi = torch.empty(total, dtype=torch.float64, device=dev)
@@ -499,6 +504,8 @@ def run_ours(args):
     for _ in range(max(args.warmup, 3)):
         step()
     pairs, v_pairs, layout = algorithmic_work(plan)
+    tiles = plan.tiles()
+    m2l_form = tiles["m2l_tile"]
     sizes = plan.sizes()
     fp32_peak = binding.fp32_peak()  # TFLOP/s, measured on this GPU just before the timed steps
     ms_arr = (ctypes.c_double * 12)()
@@ -557,12 +564,14 @@ def run_ours(args):
             "M2L": ("alu", evals_per_step * 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s", fp32_peak)}
     m2l_tensor = args.precision == "mixed" and p <= 10 and args.m2l_path != "simt"
     if m2l_tensor:
-        # TF32 tensor peak: the measured sustained bf16 rate x the nominal
+        # the tensor peak of the operand form: FP16 (kind::f16) runs at the
+        # measured sustained bf16 rate, TF32 at that rate x the nominal
         # tf32/bf16 ratio (1.1 / 2.25 dense PFLOP/s); algorithmic flops count
         # one product, not the three of the hi/lo split
-        tf32_peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
+        bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        tc_peak = bf16_peak if m2l_form == 2 else bf16_peak * 1.1 / 2.25
         work["M2L"] = ("tensor", evals_per_step * 2.0 * nc * nc * v_pairs / 1e12, "TFLOP/s",
-                       tf32_peak)
+                       tc_peak)
     # bandwidth-bound passes: algorithmic bytes (read + write once) per step
     hbm = peaks.get("hbm_gbs", 6800.0)
     nleaves = int(np.sum(layout["box_nchild"] == 0))
@@ -586,12 +595,15 @@ def run_ours(args):
         achieved = None
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": (achieved / peak) if achieved else None,
-            "traffic": TRAFFIC_BYTES.get((dom, n, p, S, args.precision)),
+            "traffic": TRAFFIC_BYTES.get((dom, n, p, S, args.precision, tiles["p2p_tile"]))
+                       if dom == "P2P" else None,
             "peak_source": ("FP32: fmm_fp32_peak, paired-FMA chains on this GPU (of measured); "
                             "nominal %d SMs x %d lanes x 2 flop x %.0f MHz = %.1f TFLOP/s"
                             % (sms, FP32_LANES_PER_SM, max_mhz, fp32_nominal)
                             if bound == "alu" else
-                            "TF32 = measured sustained bf16 x 1.1/2.25 (of measured)" if bound == "tensor"
+                            ("FP16 = measured sustained bf16 (of measured)" if m2l_form == 2 else
+                             "TF32 = measured sustained bf16 x 1.1/2.25 (of measured)")
+                            if bound == "tensor"
                             else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
     if bound == "alu" and achieved:
         roof["frac_of_nominal"] = achieved / fp32_nominal
@@ -626,7 +638,7 @@ def run_ours(args):
                        "l2": "256 MB flush between steps; working set >> L2",
                        "boxes": sizes["nboxes"], "levels": sizes["nlevels"], "U": sizes["nu"],
                        "V": sizes["nv"], "W": sizes["nw"], "X": sizes["nx"],
-                       "p2p_pairs": pairs, "tiles": plan.tiles()},
+                       "p2p_pairs": pairs, "tiles": tiles},
             "clocks": clk, "gpu_launches": launches, "wall_s_timed": t_wall,
             "pass_ms": pass_ms, "pass_launches": pass_launch, "roofline": roof,
             "pass_roofline": other, "fp32_peak_tflops": fp32_peak,
@@ -731,7 +743,7 @@ def run_ours(args):
         line["dual_tree"] = dual_leg(X, Q, S, p, args.precision, args.dual_theta, rel_err,
                                      min(args.steps, 5), stream, ms_pf, ms_eval)
     if not args.no_batch:
-        line["batched"] = batched_leg(dev, args.steps, args.warmup)
+        line["batched"] = batched_leg(dev, args.steps, args.warmup, args.batch_leaf)
     if not args.no_lattice:
         line["lattice"] = lattice_leg(dev)
     if args.precond:
