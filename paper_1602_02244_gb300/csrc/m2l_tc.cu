@@ -111,10 +111,12 @@ __global__ void k_split_f16(int64_t nb, int nc, int ld, int kt, const float *__r
 //              the async proxy and arrive on the stage's `full` barrier; one
 //              of them also moves the stage's operator slab with a bulk async
 //              copy that completes its bytes on the same barrier.
-// Barriers: full[s] (128 producer arrivals) and bfull[s] (the slab's bytes)
-// -> MMA; empty[s] (commit) ->
-// producers; accf[a] (commit after a slot) -> drain; acce[a] (128 drain
-// arrivals) -> MMA before it overwrites accumulator a.
+// Barriers: full[s] (128 producer arrivals once the rows have landed, plus
+// one arrival that announces the slab's bytes, which the bulk copy completes)
+// -> MMA; empty[s] (commit) -> producers; accf[a] (commit after a slot) ->
+// drain; acce[a] (128 drain arrivals) -> MMA before it overwrites
+// accumulator a.  The MMA thread thus waits on one barrier per stage: each
+// of its waits costs a few hundred cycles in which the tensor core idles.
 constexpr int kTcDrainWarps = 4;
 constexpr int kTcProdWarps = 4;
 constexpr int kTcProdThreads = 32 * kTcProdWarps;
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
              const float *__restrict__ mscale, const float *__restrict__ rowscale,
              float *__restrict__ L, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
-  __shared__ uint64_t full[NSTAGE], bfull[NSTAGE], empty[NSTAGE], accf[2], acce[2], done;
+  __shared__ uint64_t full[NSTAGE], empty[NSTAGE], accf[2], acce[2], done;
   __shared__ uint32_t tslot;
   __shared__ int abort_word;
   __shared__ int16_t s_slots[216];  // the tile's occupied slots, in order
@@ -181,8 +183,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   if (tid == 0) {
     for (int q = 0; q < NSTAGE; ++q) {
-      tc::mbar_init(&full[q], kTcProdThreads);
-      tc::mbar_init(&bfull[q], 1);
+      tc::mbar_init(&full[q], kTcProdThreads + 1);
       tc::mbar_init(&empty[q], 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -260,8 +261,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t dtm = tmem + (uint32_t)(a * kCols);
         for (int c = 0; c < nch; ++c) {
           const int st = j * nch + c;
-          ok = tc_wait(&full[st % NSTAGE], (uint32_t)(st / NSTAGE) & 1, abort) &&
-               tc_wait(&bfull[st % NSTAGE], (uint32_t)(st / NSTAGE) & 1, abort);
+          ok = tc_wait(&full[st % NSTAGE], (uint32_t)(st / NSTAGE) & 1, abort);
           if (!ok) break;
           tc::fence_after_sync();
           const uint32_t base = tc::smem_addr(sm + (st % NSTAGE) * stage_bytes);
@@ -347,8 +347,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (pt == 0) {  // the operator slab (hi and lo halves) is contiguous: one bulk copy
         const uint32_t slab = 2u * (uint32_t)N * (uint32_t)cb;
         const unsigned char *bsrc = opt + (size_t)code * 2 * N * kt_bytes + (size_t)c * 2 * N * kTcRowBytes;
-        tc::mbar_arrive_expect_tx(&bfull[s], slab);
-        tc::bulk_g2s(sm + s * stage_bytes + 2 * a_bytes, bsrc, slab, &bfull[s]);
+        tc::mbar_arrive_expect_tx(&full[s], slab);
+        tc::bulk_g2s(sm + s * stage_bytes + 2 * a_bytes, bsrc, slab, &full[s]);
       }
       cp_async_commit();
       if (st >= kLag) {  // the stage issued kLag steps ago has landed
@@ -359,14 +359,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
     cp_async_wait<0>();
-    if (!*abort) {
-      tc::fence_async_shared();
-      for (; signalled < st; ++signalled) tc::mbar_arrive(&full[signalled % NSTAGE]);
-    } else if (pt == 0) {
-      // slabs of the last NSTAGE issued stages may still be in flight: let
-      // them land before the CTA's shared memory is released
+    tc::fence_async_shared();
+    for (; signalled < st; ++signalled) tc::mbar_arrive(&full[signalled % NSTAGE]);
+    if (*abort && pt == 0) {
+      // slabs of the last NSTAGE issued stages may still be in flight: their
+      // bytes complete those stages' full phases, so waiting (bounded) on
+      // them lets the copies land before the CTA's shared memory is released
       for (int q = st - NSTAGE > 0 ? st - NSTAGE : 0; q < st; ++q)
-        tc::mbar_wait_bounded(&bfull[q % NSTAGE], (uint32_t)(q / NSTAGE) & 1, kTcWaitCycles);
+        tc::mbar_wait_bounded(&full[q % NSTAGE], (uint32_t)(q / NSTAGE) & 1, kTcWaitCycles);
     }
   }
 
