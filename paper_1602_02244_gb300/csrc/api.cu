@@ -158,6 +158,7 @@ void release_plan(fmm_plan_impl &P) {
   P.dt_goff.release(); P.dt_gidx.release(); P.p2p_pairs.release(); P.p2p_meta.release(); P.p2p_meta_z.release();
   P.p2p_key.release(); P.p2p_key_tmp.release(); P.p2p_order.release(); P.p2p_order_tmp.release();
   P.p2p_ticket.release();
+  P.oct_off.release(); P.oct_order.release(); P.oct_pos.release(); P.m2m_part.release();
 }
 
 }  // namespace fmm

@@ -136,6 +136,23 @@ void prepare_p2p_f32(fmm_plan_impl &P) {
   P.p2p_meta_ok = true;
 }
 
+// Once per plan, for the FP32 M2M / L2L: the boxes of each level grouped by
+// their octant within the parent (plan work: the profiler books it under the
+// lists), and the scratch of the children's translated multipoles.
+void prepare_oct_groups(fmm_plan_impl &P) {
+  if (P.oct_ok) return;
+  cudaStream_t s = P.stream;
+  PassScope ps_(P, kPassLists);
+  const size_t nb = std::max<int64_t>(P.nboxes, 1);
+  P.oct_off.resize((size_t)9 * std::max(P.nlevels, 1), s);
+  P.oct_order.resize(nb, s);
+  P.oct_pos.resize(nb, s);
+  P.m2m_part.resize(nb * (size_t)coef_pitch(P.order), s);
+  launch_octant_groups(P.nlevels, P.level_off.data(), 0, (int32_t)P.nboxes, P.box_geo.p,
+                       P.oct_off.p, P.oct_pos.p, P.oct_order.p, s);
+  P.oct_ok = true;
+}
+
 void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad) {
   const int p = P.order;
   const int64_t n = P.n;
@@ -144,6 +161,7 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   const bool coarse = lc >= 2;
   ensure_workspace(P, coarse, true);
   prepare_p2p_f32(P);
+  prepare_oct_groups(P);
   P.src32.resize(n, s);
   {
     PassScope ps_(P, kPassP2M);
@@ -165,8 +183,9 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
                                                   P.box_geo.p, P.M32.p, P.ops.m2m64.p, P.M64.p,
                                                   P.M32.p, s);
     } else {
-      launch_m2m_f32q(p, b0, nbl, P.box_child.p, P.box_nchild.p, P.box_geo.p, P.M32.p,
-                      P.ops.m2m32t.p, P.M32.p, s);
+      launch_m2m_f32q(p, l, b0, nbl, P.level_off[l + 2] - P.level_off[l + 1], P.oct_off.p,
+                      P.oct_order.p, P.box_child.p, P.box_nchild.p, P.ops.m2m32t.p,
+                      P.m2m_part.p, P.M32.p, s);
     }
   }
   {
@@ -222,7 +241,8 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
                                                         P.L32.p, P.L64.p, P.ops.l2l64.p, P.L64.p,
                                                         P.L32.p, s);
     else
-      launch_l2l_f32q(p, b0, nbl, P.box_parent.p, P.box_geo.p, P.ops.l2l32t.p, P.L32.p, s);
+      launch_l2l_f32q(p, l, nbl, P.oct_off.p, P.oct_order.p, P.box_parent.p, P.ops.l2l32t.p,
+                      P.L32.p, s);
   }
   {
     PassScope ps_(P, kPassL2P);

@@ -48,11 +48,19 @@ void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, 
                 int64_t nx, const int32_t *xboxes, const int32_t *xslot, const int32_t *first,
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
                 const T *M, T *K, int64_t n, double *far, cudaStream_t s);
-void launch_m2m_f32q(int p, int32_t b0, int32_t nbl, const int32_t *child, const int32_t *nchild,
-                     const BoxGeo *geo, const float *Mc, const float *opT, float *Mp,
-                     cudaStream_t s);
-void launch_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *parent, const BoxGeo *geo,
-                     const float *opT, float *L, cudaStream_t s);
+// FP32 M2M into the parents [b0, b0 + nbl) of level l from the children of
+// level l + 1 (oct_off / oct_order: boxes grouped by level and octant; part:
+// nboxes x coef_pitch(p) scratch for the translated children)
+void launch_m2m_f32q(int p, int l, int32_t b0, int32_t nbl, int32_t nchildren,
+                     const int32_t *oct_off, const int32_t *oct_order, const int32_t *child,
+                     const int32_t *nchild, const float *opT, float *part, float *M, cudaStream_t s);
+// the boxes of levels [l0, nlevels) grouped by octant within each level
+void launch_octant_groups(int nlevels, const int32_t *level_off_host, int32_t b0, int32_t nb,
+                          const BoxGeo *geo, int32_t *oct_off, int32_t *oct_pos, int32_t *oct_order,
+                          cudaStream_t s);
+// FP32 L2L into the nbl boxes of level l from their parents
+void launch_l2l_f32q(int p, int l, int32_t nbl, const int32_t *oct_off, const int32_t *oct_order,
+                     const int32_t *parent, const float *opT, float *L, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *iperm, const double *far, const double *near,
                     double *phi, double *grad, cudaStream_t s);
 void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double *gq,

@@ -330,102 +330,159 @@ __global__ void k_l2l(int p, int32_t b0, int32_t nbl, const int32_t *__restrict_
   if (Lout32) Lout32[(int64_t)b * ld + r] = (float)acc;
 }
 
-// FP32 M2M and L2L with four outputs per lane: lane (box, quad q) owns
-// coefficients 4q..4q+3 and reads the input-major operator as one 16-byte
-// load per input coefficient.  The triangular structure bounds the loops:
-// M2M output degree n uses inputs of degree <= n, L2L inputs of degree >= n.
-// M2M splits the children across 8 consecutive lanes: lane c of a group takes
-// the parent's c-th child (if any) and a 3-step shuffle reduction sums the
-// group, so each lane runs at most (p+1)^2 dependent multiply-adds instead of
-// up to 8 (p+1)^2 -- these small per-level launches are latency-bound.
-__global__ void k_m2m_f32q_split(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ child,
-                                 const int32_t *__restrict__ nchild, const BoxGeo *__restrict__ geo,
-                                 const float *__restrict__ Mc, const float4 *__restrict__ opT,
-                                 float *__restrict__ Mp) {
-  const int nc = ncoef(p), ld = coef_pitch(p), nq = ld / 4;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t g = t >> 3;  // (parent, quad) group of 8 lanes
-  const int c = (int)(t & 7);
-  const bool in = g < (int64_t)nbl * nq;
-  int32_t b = 0, nch = 0;
-  int q = 0;
-  if (in) {
-    b = b0 + (int32_t)(g / nq);
-    q = (int)(g % nq);
-    nch = nchild[b];
-  }
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (in && c < nch && 4 * q < nc) {
-    const int kmax = ncoef(degree_of(min(4 * q + 3, nc - 1)));
-    const int32_t cc = child[b] + c;
-    const float4 *col = opT + (size_t)octant(geo[cc]) * nc * nq + q;
-    const float *m = Mc + (int64_t)cc * ld;
-    for (int k = 0; k < kmax; ++k) {
-      const float mk = m[k];
-      const float4 w = col[(size_t)k * nq];
-      acc.x = fmaf(w.x, mk, acc.x);
-      acc.y = fmaf(w.y, mk, acc.y);
-      acc.z = fmaf(w.z, mk, acc.z);
-      acc.w = fmaf(w.w, mk, acc.w);
-    }
-  }
-#pragma unroll
-  for (int o = 1; o < 8; o <<= 1) {  // groups are 8-aligned within the warp
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
-    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
-  }
-  if (in && c == 0 && nch > 0) reinterpret_cast<float4 *>(Mp + (int64_t)b * ld)[q] = acc;
+// FP32 M2M and L2L as small GEMMs per child octant.  The boxes of a level
+// are grouped by their octant within the parent (plan time), so a CTA takes
+// up to kTrRows boxes of one level and one octant, all translated by the same
+// operator: the input-major operator opT[o] ((p+1)^2 x coef_pitch(p) floats)
+// and the tile's input rows (k-major) are staged in shared memory, and each
+// thread accumulates one output quad (4 coefficients) of 8 rows in
+// registers -- per input coefficient one 16-byte operator load (different per
+// quad, conflict-free) and two broadcast 16-byte loads of the 8 inputs serve
+// 32 multiply-adds.  The triangular structure bounds the loops: M2M output
+// degree n uses inputs of degree <= n, L2L inputs of degree >= n.
+//   M2M: part[child] = opT[o]^T M[child], then each parent sums its children's
+//        parts in child order (deterministic);
+//   L2L: L[child] += opT[o]^T L[parent of child].
+constexpr int kTrRows = 64;              // boxes per CTA
+constexpr int kTrPitch = kTrRows + 4;    // shared input row: 16-byte aligned, fewer conflicts
+constexpr int kMaxLevels = 32;
+struct LevelOffsets {
+  int32_t off[kMaxLevels + 1];
+  int n;  // levels
+};
+
+__device__ __forceinline__ int level_of(const LevelOffsets &lo, int32_t b) {
+  int l = 0;
+  while (l + 1 < lo.n && lo.off[l + 1] <= b) ++l;
+  return l;
 }
 
-__global__ void k_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ parent,
-                           const BoxGeo *__restrict__ geo, const float4 *__restrict__ opT,
-                           float *L) {
-  // 4 consecutive lanes per (box, quad) split the input range (k = k0 + c,
-  // k0 + c + 4, ...) and a 2-step shuffle reduction sums them
-  const int nc = ncoef(p), ld = coef_pitch(p), nq = ld / 4;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t g = t >> 2;
-  const int c = (int)(t & 3);
-  const bool in = g < (int64_t)nbl * nq;
-  int32_t b = 0;
-  int q = 0;
-  if (in) {
-    b = b0 + (int32_t)(g / nq);
-    q = (int)(g % nq);
+__global__ void k_oct_count(int32_t b0, int32_t nb, LevelOffsets lo, const BoxGeo *__restrict__ geo,
+                            int32_t *__restrict__ cnt, int32_t *__restrict__ pos) {
+  const int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= nb) return;
+  const int32_t b = b0 + i;
+  pos[i] = atomicAdd(&cnt[level_of(lo, b) * 9 + octant(geo[b])], 1);
+}
+
+__global__ void k_oct_scan(LevelOffsets lo, int32_t *__restrict__ off) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int l = 0; l < lo.n; ++l) {
+    int32_t run = lo.off[l];
+    for (int o = 0; o < 8; ++o) {
+      const int32_t c = off[l * 9 + o];
+      off[l * 9 + o] = run;
+      run += c;
+    }
+    off[l * 9 + 8] = lo.off[l + 1];
   }
-  const bool act = in && 4 * q < nc;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (act) {
-    const int32_t P = parent[b];
-    const int n0 = degree_of(4 * q);
-    const float4 *col = opT + (size_t)octant(geo[b]) * nc * nq + q;
-    const float *lp = L + (int64_t)P * ld;
-    for (int k = n0 * n0 + c; k < nc; k += 4) {
-      const float lk = lp[k];
-      const float4 w = col[(size_t)k * nq];
-      acc.x = fmaf(w.x, lk, acc.x);
-      acc.y = fmaf(w.y, lk, acc.y);
-      acc.z = fmaf(w.z, lk, acc.z);
-      acc.w = fmaf(w.w, lk, acc.w);
+}
+
+__global__ void k_oct_scatter(int32_t b0, int32_t nb, LevelOffsets lo, const BoxGeo *__restrict__ geo,
+                              const int32_t *__restrict__ off, const int32_t *__restrict__ pos,
+                              int32_t *__restrict__ order) {
+  const int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= nb) return;
+  const int32_t b = b0 + i;
+  order[off[level_of(lo, b) * 9 + octant(geo[b])] + pos[i]] = b;
+}
+
+template <bool L2L>
+__global__ void k_trans_oct(int p, int l, const int32_t *__restrict__ oct_off,
+                            const int32_t *__restrict__ oct_order, const int32_t *__restrict__ parent,
+                            const float4 *__restrict__ opT, const float *in, float *out) {
+  extern __shared__ __align__(16) float tr_sm[];
+  __shared__ int32_t s_off[9], s_src[kTrRows], s_dst[kTrRows];
+  const int nc = ncoef(p), ld = coef_pitch(p), nq = ld / 4;
+  float *B = tr_sm;                    // [nc][ld]: opT[o]
+  float *A = tr_sm + (size_t)nc * ld;  // [nc][kTrPitch]: input k of row j at A[k][j]
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid < 9) s_off[tid] = oct_off[l * 9 + tid];
+  __syncthreads();
+  // this CTA's octant and tile (the same in every thread)
+  int o = 0, t = (int)blockIdx.x;
+  for (; o < 8; ++o) {
+    const int nt = (s_off[o + 1] - s_off[o] + kTrRows - 1) / kTrRows;
+    if (t < nt) break;
+    t -= nt;
+  }
+  if (o == 8) return;
+  const int32_t r0 = s_off[o] + t * kTrRows;
+  const int nr = min(kTrRows, s_off[o + 1] - r0);
+  for (int j = tid; j < nr; j += nthr) {
+    const int32_t box = oct_order[r0 + j];
+    s_dst[j] = box;
+    s_src[j] = L2L ? parent[box] : box;
+  }
+  const float4 *src = opT + (size_t)o * nc * nq;
+  for (int i = tid; i < nc * nq; i += nthr) reinterpret_cast<float4 *>(B)[i] = src[i];
+  __syncthreads();
+  for (int i = tid; i < kTrRows * nc; i += nthr) {
+    const int j = i / nc, k = i - j * nc;
+    A[k * kTrPitch + j] = j < nr ? in[(int64_t)s_src[j] * ld + k] : 0.f;
+  }
+  __syncthreads();
+  // compute role: output quad q of rows 8 g .. 8 g + 7
+  if (tid >= 8 * nq) return;
+  const int q = tid % nq, g = tid / nq;
+  if (8 * g >= nr) return;
+  const int dq = degree_of(min(4 * q + 3, nc - 1)), d0 = degree_of(4 * q);
+  const int k0 = L2L ? d0 * d0 : 0, k1 = L2L ? nc : (dq + 1) * (dq + 1);
+  float4 acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = k0; k < k1; ++k) {
+    const float4 w = reinterpret_cast<const float4 *>(B + (size_t)k * ld)[q];
+    const float4 a0 = reinterpret_cast<const float4 *>(A + (size_t)k * kTrPitch)[2 * g];
+    const float4 a1 = reinterpret_cast<const float4 *>(A + (size_t)k * kTrPitch)[2 * g + 1];
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      acc[i].x = fmaf(w.x, a[i], acc[i].x);
+      acc[i].y = fmaf(w.y, a[i], acc[i].y);
+      acc[i].z = fmaf(w.z, a[i], acc[i].z);
+      acc[i].w = fmaf(w.w, a[i], acc[i].w);
     }
   }
 #pragma unroll
-  for (int o = 1; o < 4; o <<= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
-    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+  for (int i = 0; i < 8; ++i) {
+    const int j = 8 * g + i;
+    if (j >= nr) break;
+    float4 *dst = reinterpret_cast<float4 *>(out + (int64_t)s_dst[j] * ld) + q;
+    if (L2L) {
+      float4 v = *dst;
+      v.x += acc[i].x;
+      v.y += acc[i].y;
+      v.z += acc[i].z;
+      v.w += acc[i].w;
+      *dst = v;
+    } else {
+      *dst = acc[i];
+    }
   }
-  if (!act || c != 0) return;
-  float4 *out = reinterpret_cast<float4 *>(L + (int64_t)b * ld) + q;
-  float4 v = *out;
-  v.x += acc.x;
-  v.y += acc.y;
-  v.z += acc.z;
-  v.w += acc.w;
-  *out = v;
+}
+
+// M2M: each parent of [b0, b0 + nbl) with children sums their parts in child order
+__global__ void k_m2m_sum(int p, int32_t b0, int32_t nbl, const int32_t *__restrict__ child,
+                          const int32_t *__restrict__ nchild, const float4 *__restrict__ part,
+                          float4 *__restrict__ M) {
+  const int nq = coef_pitch(p) / 4;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nbl * nq) return;
+  const int32_t b = b0 + (int32_t)(i / nq);
+  const int q = (int)(i % nq);
+  const int32_t nch = nchild[b];
+  if (nch == 0) return;
+  const int32_t c0 = child[b];
+  float4 acc = part[(int64_t)c0 * nq + q];
+  for (int c = 1; c < nch; ++c) {
+    const float4 v = part[(int64_t)(c0 + c) * nq + q];
+    acc.x += v.x;
+    acc.y += v.y;
+    acc.z += v.z;
+    acc.w += v.w;
+  }
+  M[(int64_t)b * nq + q] = acc;
 }
 
 template <typename Tin>
@@ -1021,23 +1078,59 @@ void launch_l2l(int p, int32_t b0, int32_t nbl, const int32_t *parent, const Box
   FMM_LAUNCH_CHECK();
 }
 
-void launch_m2m_f32q(int p, int32_t b0, int32_t nbl, const int32_t *child, const int32_t *nchild,
-                     const BoxGeo *geo, const float *Mc, const float *opT, float *Mp,
-                     cudaStream_t s) {
-  if (nbl == 0) return;
-  const int64_t tot = (int64_t)nbl * (coef_pitch(p) / 4) * 8;
-  k_m2m_f32q_split<<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, child, nchild, geo, Mc,
-                                                      reinterpret_cast<const float4 *>(opT), Mp);
+namespace {
+template <bool L2L>
+void launch_trans_oct(int p, int l, int32_t nrows, const int32_t *oct_off, const int32_t *oct_order,
+                      const int32_t *parent, const float *opT, const float *in, float *out,
+                      cudaStream_t s) {
+  if (nrows <= 0) return;
+  const int nc = ncoef(p), ld = coef_pitch(p);
+  const size_t sm = sizeof(float) * ((size_t)nc * ld + (size_t)nc * kTrPitch);
+  const int threads = (8 * (ld / 4) + 31) / 32 * 32;
+  // each octant's last tile may be partial: at most 8 tiles more than nrows / kTrRows
+  const int64_t grid = ceil_div((int64_t)nrows, (int64_t)kTrRows) + 8;
+  allow_smem(k_trans_oct<L2L>, sm);
+  k_trans_oct<L2L><<<(unsigned)grid, threads, sm, s>>>(p, l, oct_off, oct_order, parent,
+                                                     reinterpret_cast<const float4 *>(opT), in, out);
+  FMM_LAUNCH_CHECK();
+}
+}  // namespace
+
+void launch_octant_groups(int nlevels, const int32_t *level_off_host, int32_t b0, int32_t nb,
+                          const BoxGeo *geo, int32_t *oct_off, int32_t *oct_pos, int32_t *oct_order,
+                          cudaStream_t s) {
+  if (nlevels > kMaxLevels) throw Error(FMM_ERR_UNSUPPORTED, "too many tree levels");
+  LevelOffsets lo{};
+  lo.n = nlevels;
+  for (int l = 0; l <= nlevels; ++l) lo.off[l] = level_off_host[l];
+  FMM_CUDA(cudaMemsetAsync(oct_off, 0, sizeof(int32_t) * 9 * (size_t)nlevels, s));
+  if (nb > 0) {
+    k_oct_count<<<ceil_div(nb, 256), 256, 0, s>>>(b0, nb, lo, geo, oct_off, oct_pos);
+    FMM_LAUNCH_CHECK();
+  }
+  k_oct_scan<<<1, 32, 0, s>>>(lo, oct_off);
+  FMM_LAUNCH_CHECK();
+  if (nb > 0) {
+    k_oct_scatter<<<ceil_div(nb, 256), 256, 0, s>>>(b0, nb, lo, geo, oct_off, oct_pos, oct_order);
+    FMM_LAUNCH_CHECK();
+  }
+}
+
+void launch_m2m_f32q(int p, int l, int32_t b0, int32_t nbl, int32_t nchildren,
+                     const int32_t *oct_off, const int32_t *oct_order, const int32_t *child,
+                     const int32_t *nchild, const float *opT, float *part, float *M, cudaStream_t s) {
+  if (nbl <= 0 || nchildren <= 0) return;
+  launch_trans_oct<false>(p, l + 1, nchildren, oct_off, oct_order, nullptr, opT, M, part, s);
+  const int64_t tot = (int64_t)nbl * (coef_pitch(p) / 4);
+  k_m2m_sum<<<ceil_div(tot, 256), 256, 0, s>>>(p, b0, nbl, child, nchild,
+                                              reinterpret_cast<const float4 *>(part),
+                                              reinterpret_cast<float4 *>(M));
   FMM_LAUNCH_CHECK();
 }
 
-void launch_l2l_f32q(int p, int32_t b0, int32_t nbl, const int32_t *parent, const BoxGeo *geo,
-                     const float *opT, float *L, cudaStream_t s) {
-  if (nbl == 0) return;
-  const int64_t tot = (int64_t)nbl * (coef_pitch(p) / 4) * 4;
-  k_l2l_f32q<<<ceil_div(tot, 128), 128, 0, s>>>(p, b0, nbl, parent, geo,
-                                                reinterpret_cast<const float4 *>(opT), L);
-  FMM_LAUNCH_CHECK();
+void launch_l2l_f32q(int p, int l, int32_t nbl, const int32_t *oct_off, const int32_t *oct_order,
+                     const int32_t *parent, const float *opT, float *L, cudaStream_t s) {
+  launch_trans_oct<true>(p, l, nbl, oct_off, oct_order, parent, opT, L, L, s);
 }
 
 template <typename Tin>

@@ -138,6 +138,12 @@ struct fmm_plan_impl {
   DBuf<int32_t> p2p_order, p2p_order_tmp;  // leaves, most near-field work first
   DBuf<int32_t> p2p_ticket;
   bool p2p_meta_ok = false;         // p2p_meta and p2p_order match the current lists
+  // FP32 M2M / L2L: the boxes of each level grouped by octant within the
+  // parent (oct_order), group l * 9 + o starting at oct_off[l * 9 + o]
+  // (oct_off[l * 9 + 8] = end of level l); oct_pos is scratch
+  DBuf<int32_t> oct_off, oct_order, oct_pos;
+  bool oct_ok = false;
+  DBuf<float> m2m_part;             // FP32 M2M: each child's translated multipole (nboxes x NC)
   int p2p_tile = 0;                 // FP32 near-field staging shape (0 = default)
   int p2p_tile_user = 0, m2l_tile_user = 0;  // the caller's tile options (0 = tuned or default)
   DBuf<double> M64, L64;            // nboxes x NC

@@ -743,6 +743,7 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   cudaStream_t s = P.stream;
   drop_graph(P);  // a captured graph refers to the old layout
   P.p2p_meta_ok = false;
+  P.oct_ok = false;
   P.n = n;
   P.nboxes = 0;
   P.nlevels = 0;
