@@ -159,6 +159,7 @@ void release_plan(fmm_plan_impl &P) {
   P.p2p_key.release(); P.p2p_key_tmp.release(); P.p2p_order.release(); P.p2p_order_tmp.release();
   P.p2p_ticket.release();
   P.oct_off.release(); P.oct_order.release(); P.oct_pos.release(); P.m2m_part.release();
+  P.far32.release();
 }
 
 }  // namespace fmm

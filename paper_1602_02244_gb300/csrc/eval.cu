@@ -23,8 +23,12 @@ void ensure_workspace(fmm_plan_impl &P, bool need64, bool need32) {
   const size_t nc = (size_t)coef_pitch(P.order);  // row pitch of the coefficient arrays
   const size_t nb = (size_t)P.nboxes;
   cudaStream_t s = P.stream;
-  P.far_acc.resize(4 * (size_t)P.n, s);
-  P.near_acc.resize(4 * (size_t)P.n, s);
+  if (need32) {  // mixed: the far field in FP32; the near field finishes each target
+    P.far32.resize((size_t)P.n, s);
+  } else {
+    P.far_acc.resize(4 * (size_t)P.n, s);
+    P.near_acc.resize(4 * (size_t)P.n, s);
+  }
   if (need64) {
     P.M64.resize(nb * nc, s);
     P.L64.resize(nb * nc, s);
@@ -81,14 +85,14 @@ void eval_fp64(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gra
   {
     PassScope ps_(P, kPassL2P);
     launch_l2p<double>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src64.p,
-                       P.box_side.p, P.L64.p, n, P.far_acc.p, ltop, s);
+                       P.box_side.p, P.L64.p, n, reinterpret_cast<Dbl4 *>(P.far_acc.p), ltop, s);
   }
   if (P.nwleaves > 0) {
     PassScope ps_(P, kPassM2P);
     P.K64.resize(std::max<size_t>(1, (size_t)P.nxboxes * 4 * coef_pitch(p + 1)), s);
     launch_m2p<double>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.nxboxes, P.xboxes.p,
                        P.xslot.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src64.p, P.box_side.p, P.M64.p,
-                       P.K64.p, n, P.far_acc.p, s);
+                       P.K64.p, n, reinterpret_cast<Dbl4 *>(P.far_acc.p), s);
   }
   {
     PassScope ps_(P, kPassP2P);
@@ -247,27 +251,23 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
   {
     PassScope ps_(P, kPassL2P);
     launch_l2p<float>(p, P.nleaves, P.leaves.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p,
-                      P.box_side.p, P.L32.p, n, P.far_acc.p, ltop, s);
+                      P.box_side.p, P.L32.p, n, P.far32.p, ltop, s);
   }
   if (P.nwleaves > 0) {
     PassScope ps_(P, kPassM2P);
     P.K32.resize(std::max<size_t>(1, (size_t)P.nxboxes * 4 * coef_pitch(p + 1)), s);
     launch_m2p<float>(p, P.nwleaves, P.wleaves.p, P.w_off.p, P.w_idx.p, P.nxboxes, P.xboxes.p,
                       P.xslot.p, P.box_first.p, P.box_count.p, P.box_geo.p, P.src32.p, P.box_side.p, P.M32.p,
-                      P.K32.p, n, P.far_acc.p, s);
+                      P.K32.p, n, P.far32.p, s);
   }
   {
     PassScope ps_(P, kPassP2P);
     P.p2p_pairs.resize(p2p_pair_floats(n), s);
     P2PScratch scratch{reinterpret_cast<float4 *>(P.p2p_pairs.p), P.p2p_meta.p, P.p2p_meta_z.p,
                        P.p2p_order.p, P.p2p_ticket.p, P.p2p_tile > 0 ? P.p2p_tile : kP2PDefaultTile,
-                       P.dev_err.p};
+                       P.dev_err.p, P.far32.p, P.perm.p, d_phi, d_grad};
     launch_p2p<float>(P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p,
-                      P.box_geo.p, P.src32.p, P.box_side.p, n, P.near_acc.p, &scratch, s);
-  }
-  {
-    PassScope ps_(P, kPassReduce);
-    launch_combine(n, P.iperm.p, P.far_acc.p, P.near_acc.p, d_phi, d_grad, s);
+                      P.box_geo.p, P.src32.p, P.box_side.p, n, nullptr, &scratch, s);
   }
 }
 

@@ -37,17 +37,19 @@ void launch_l2l(int p, int32_t b0, int32_t nbl, const int32_t *parent, const Box
 template <typename Tin>
 void launch_to_f64(int64_t count, const Tin *in, double *out, cudaStream_t s);
 // lfar: leaves above this level get no far field (2 for U/V/W/X lists, 1
-// for the dual tree)
+// for the dual tree).  far: per sorted target (phi, gx, gy, gz) at the
+// evaluation's precision (FP32 for the mixed path: its far field is FP32
+// arithmetic, so a wider store would add no accuracy)
 template <typename T>
 void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
-                const T *L, int64_t n, double *far, int lfar, cudaStream_t s);
+                const T *L, int64_t n, typename V4<T>::type *far, int lfar, cudaStream_t s);
 // M2P over W lists; K is scratch of 4 * coef_pitch(p+1) per X box (the W sources)
 template <typename T>
 void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, const int32_t *widx,
                 int64_t nx, const int32_t *xboxes, const int32_t *xslot, const int32_t *first,
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
-                const T *M, T *K, int64_t n, double *far, cudaStream_t s);
+                const T *M, T *K, int64_t n, typename V4<T>::type *far, cudaStream_t s);
 // FP32 M2M into the parents [b0, b0 + nbl) of level l from the children of
 // level l + 1 (oct_off / oct_order: boxes grouped by level and octant; part:
 // nboxes x coef_pitch(p) scratch for the translated children)
@@ -113,6 +115,9 @@ void launch_m2l_dual(int p, int64_t nb, const int32_t *off, const int32_t *idx, 
 // that key.  `tile` (1..p2p_num_tiles()) picks the staging shape; `ticket` is
 // one device int of scratch; err is set if a bounded wait for a staging copy
 // gave up.  The FP64 path uses none of them.
+// The FP32 near field also finishes each target: it adds the far field
+// (far, FP32 per sorted target) to its compensated near-field sum in FP64 and
+// writes phi / grad at the target's input index perm[i] (grad may be NULL).
 struct P2PScratch {
   float4 *pairs;
   const int4 *meta;
@@ -121,6 +126,9 @@ struct P2PScratch {
   int *ticket;
   int tile;
   int *err;
+  const float4 *far;
+  const int32_t *perm;
+  double *phi, *grad;
 };
 size_t p2p_pair_floats(int64_t n);
 int p2p_num_tiles();

@@ -436,7 +436,9 @@ __global__ void __launch_bounds__(kP2PThreads, MINB)
               const int4 *__restrict__ meta, const float *__restrict__ meta_z,
               const int32_t *__restrict__ first, const int32_t *__restrict__ count,
               const float4 *__restrict__ src, const float4 *__restrict__ pairs,
-              double *__restrict__ near, int *__restrict__ ticket, int *__restrict__ err) {
+              const float4 *__restrict__ far, const int32_t *__restrict__ perm,
+              double *__restrict__ phi, double *__restrict__ grad, int *__restrict__ ticket,
+              int *__restrict__ err) {
   static_assert(kP2PWarps == 1, "one warp per CTA: the staging buffers are the CTA's");
   __shared__ __align__(16) P2PStage<CAPP, NBUF> st;
   // Compensated running totals of the lane's targets, [target][component][lane]
@@ -581,11 +583,20 @@ __global__ void __launch_bounds__(kP2PThreads, MINB)
             h[a] = sum;
             l[a] = __fadd_rn(__fadd_rn(l[a], l2), err);
           }
+        // the target is finished here: far field + near field in FP64, written
+        // at its input index (the gradient of 1/r points away from the sources)
         const int i = tl + per * t;
-        if (gi == 0 && i < tcount)
-          reinterpret_cast<Dbl4 *>(near)[fb + tc + i] =
-              make_dbl4((double)h[0] + (double)l[0], -((double)h[1] + (double)l[1]),
-                        -((double)h[2] + (double)l[2]), -((double)h[3] + (double)l[3]));
+        if (gi == 0 && i < tcount) {
+          const int64_t si = fb + tc + i;
+          const float4 fr = far[si];
+          const int64_t o = perm[si];
+          phi[o] = (double)fr.x + ((double)h[0] + (double)l[0]);
+          if (grad) {
+            grad[3 * o] = (double)fr.y - ((double)h[1] + (double)l[1]);
+            grad[3 * o + 1] = (double)fr.z - ((double)h[2] + (double)l[2]);
+            grad[3 * o + 2] = (double)fr.w - ((double)h[3] + (double)l[3]);
+          }
+        }
       }
     }
     li = __shfl_sync(0xffffffffu, next_li, 0);
@@ -649,7 +660,8 @@ void launch_p2p(int64_t nleaves, const int32_t *leaves, const int32_t *uoff, con
     auto run = [&](auto kern) {
       kern<<<persistent_grid(kern, nleaves), kP2PThreads, 0, s>>>(
           nleaves, scratch->order, uoff, scratch->meta, scratch->meta_z, first, count, src,
-          scratch->pairs, near, scratch->ticket, scratch->err);
+          scratch->pairs, scratch->far, scratch->perm, scratch->phi, scratch->grad, scratch->ticket,
+          scratch->err);
     };
     switch (scratch->tile) {
       case 1: run(k_p2p_f32<kP2PTiles[0].capp, kP2PTiles[0].nbuf, kP2PTiles[0].minb>); break;

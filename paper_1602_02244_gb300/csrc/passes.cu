@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(32 * kL2PWarps, 4)
                 const int32_t *__restrict__ first, const int32_t *__restrict__ count,
                 const BoxGeo *__restrict__ geo, const float4 *__restrict__ src,
                 const double *__restrict__ side, const float *__restrict__ L,
-                double *__restrict__ far, int lfar) {
+                float4 *__restrict__ far, int lfar) {
   const int p = PT > 0 ? PT : p_rt;
   extern __shared__ __align__(16) unsigned char l2p_smem[];
   const int ld = coef_pitch(p), nc = ncoef(p);
@@ -576,9 +576,9 @@ __global__ void __launch_bounds__(32 * kL2PWarps, 4)
   const int32_t b = leaves[li];
   const BoxGeo g = geo[b];
   const int32_t f = first[b], c = count[b];
-  Dbl4 *out = reinterpret_cast<Dbl4 *>(far);
+  float4 *out = far;
   if (g.level < lfar) {  // no far field reaches the levels above lfar
-    for (int32_t i = f + lane; i < f + c; i += 32) out[i] = make_dbl4(0.0, 0.0, 0.0, 0.0);
+    for (int32_t i = f + lane; i < f + c; i += 32) out[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
   const float *Lb = L + (int64_t)b * ld;
@@ -632,12 +632,8 @@ __global__ void __launch_bounds__(32 * kL2PWarps, 4)
                         fz.y = fmaf(kn.w, im.y, fz.y);
                       }
                     });
-    if (v0)
-      out[i0] = make_dbl4((double)(fp.x * inva), (double)(fx.x * inva2), (double)(fy.x * inva2),
-                          (double)(fz.x * inva2));
-    if (v1)
-      out[i1] = make_dbl4((double)(fp.y * inva), (double)(fx.y * inva2), (double)(fy.y * inva2),
-                          (double)(fz.y * inva2));
+    if (v0) out[i0] = make_float4(fp.x * inva, fx.x * inva2, fy.x * inva2, fz.x * inva2);
+    if (v1) out[i1] = make_float4(fp.y * inva, fx.y * inva2, fy.y * inva2, fz.y * inva2);
   }
 }
 
@@ -836,13 +832,13 @@ __global__ void __launch_bounds__(kM2PThreads)
                 const int32_t *__restrict__ xslot, const int32_t *__restrict__ first,
                 const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
                 const float4 *__restrict__ src, const double *__restrict__ side,
-                const float4 *__restrict__ K, int64_t n, double *__restrict__ far) {
+                const float4 *__restrict__ K, int64_t n, float4 *__restrict__ far) {
   const int p = PT > 0 ? PT : p_rt;
   extern __shared__ __align__(32) unsigned char m2p_smem[];
   float4 *ks = reinterpret_cast<float4 *>(m2p_smem);  // [nstage][ld1]
   __shared__ float s_off[kM2PStage][3], s_inva[kM2PStage];
   __shared__ int32_t s_slot[kM2PStage];
-  __shared__ double red[4][2][kM2PThreads];
+  __shared__ float red[4][2][kM2PThreads];
   const int tid = threadIdx.x;
   const int ld1 = coef_pitch(p + 1), nc1 = ncoef(p + 1);
   const int32_t B = wleaves[blockIdx.x];
@@ -926,7 +922,7 @@ __global__ void __launch_bounds__(kM2PThreads)
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) red[q][h][tid] = (double)th[q][h] + (double)tl[q][h];
+      for (int q = 0; q < 4; ++q) red[q][h][tid] = th[q][h] + tl[q][h];
     __syncthreads();
     // target pair jj (targets 2 jj, 2 jj + 1): replica r holds it at thread r * L + jj
     if (tid < (tcount + 1) / 2) {
@@ -934,7 +930,7 @@ __global__ void __launch_bounds__(kM2PThreads)
       for (int h = 0; h < 2; ++h) {
         const int u = 2 * tid + h;
         if (u < tcount) {
-          double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+          float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
           for (int r = 0; r < k; ++r) {
             const int o = r * L + tid;
             a0 += red[0][h][o];
@@ -943,8 +939,8 @@ __global__ void __launch_bounds__(kM2PThreads)
             a3 += red[3][h][o];
           }
           const int64_t i = f + tc + u;
-          Dbl4 *fi = reinterpret_cast<Dbl4 *>(far) + i;
-          Dbl4 v = *fi;
+          float4 *fi = far + i;
+          float4 v = *fi;
           v.x += a0;
           v.y += a1;
           v.z += a2;
@@ -1146,7 +1142,7 @@ void launch_to_f64(int64_t count, const Tin *in, double *out, cudaStream_t s) {
 template <typename T>
 void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *first,
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
-                const T *L, int64_t n, double *far, int lfar, cudaStream_t s) {
+                const T *L, int64_t n, typename V4<T>::type *far, int lfar, cudaStream_t s) {
   if (nleaves == 0) return;
   if constexpr (sizeof(T) == 4) {
     const size_t sm = (size_t)kL2PWarps * coef_pitch(p) * sizeof(float4);
@@ -1160,8 +1156,8 @@ void launch_l2p(int p, int64_t nleaves, const int32_t *leaves, const int32_t *fi
   } else {
     size_t sm = (size_t)ncoef(p) * sizeof(T);
     with_order(p, [&](auto PC) {
-      k_l2p<T, decltype(PC)::value><<<(unsigned)nleaves, 64, sm, s>>>(p, leaves, first, count, geo,
-                                                                      src, side, L, n, far, lfar);
+      k_l2p<T, decltype(PC)::value><<<(unsigned)nleaves, 64, sm, s>>>(
+          p, leaves, first, count, geo, src, side, L, n, reinterpret_cast<double *>(far), lfar);
     });
   }
   FMM_LAUNCH_CHECK();
@@ -1171,7 +1167,7 @@ template <typename T>
 void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, const int32_t *widx,
                 int64_t nx, const int32_t *xboxes, const int32_t *xslot, const int32_t *first,
                 const int32_t *count, const BoxGeo *geo, const typename V4<T>::type *src, const double *side,
-                const T *M, T *K, int64_t n, double *far, cudaStream_t s) {
+                const T *M, T *K, int64_t n, typename V4<T>::type *far, cudaStream_t s) {
   if (nw == 0) return;
   using V = typename V4<T>::type;
   V *K4 = reinterpret_cast<V *>(K);  // nx x coef_pitch(p+1) 4-vectors
@@ -1198,7 +1194,7 @@ void launch_m2p(int p, int64_t nw, const int32_t *wleaves, const int32_t *woff, 
       auto kern = k_m2p<T, decltype(PC)::value>;
       FMM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       kern<<<(unsigned)nw, kM2PThreads, sm, s>>>(p, nstage, wleaves, woff, widx, xslot, first, count,
-                                                 geo, src, side, K4, n, far);
+                                                 geo, src, side, K4, n, reinterpret_cast<double *>(far));
     });
   }
   FMM_LAUNCH_CHECK();
@@ -1231,11 +1227,11 @@ void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double
                               const V4<T>::type *, const double *, T *, cudaStream_t);                     \
   template void launch_l2p<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
                               const BoxGeo *, const V4<T>::type *, const double *, const T *, int64_t,     \
-                              double *, int, cudaStream_t);                                        \
+                              V4<T>::type *, int, cudaStream_t);                                   \
   template void launch_m2p<T>(int, int64_t, const int32_t *, const int32_t *, const int32_t *,     \
                               int64_t, const int32_t *, const int32_t *, const int32_t *,          \
                               const int32_t *, const BoxGeo *, const V4<T>::type *, const double *, \
-                              const T *, T *, int64_t, double *, cudaStream_t);                    \
+                              const T *, T *, int64_t, V4<T>::type *, cudaStream_t);               \
   template void launch_to_f64<T>(int64_t, const T *, double *, cudaStream_t);
 FMM_INST_T(float)
 FMM_INST_T(double)

@@ -153,7 +153,8 @@ struct fmm_plan_impl {
   DBuf<int> dev_err;                // set by a bounded device wait that gave up
   DBuf<double> K64;                 // M2P coefficient sets of the W sources
   DBuf<float> K32;
-  DBuf<double> far_acc, near_acc;   // 4 x n each: phi, gx, gy, gz (sorted order)
+  DBuf<double> far_acc, near_acc;   // FP64 path: 4 x n each, phi, gx, gy, gz (sorted order)
+  DBuf<float4> far32;               // mixed path: the far field per sorted target
   DBuf<double> adj_grad_w, adj_grad_q;  // n x 3 (adjoint)
   DBuf<double> adj_phi;
   DBuf<double> host_io;             // device staging for fmm_solve_host
