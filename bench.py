@@ -582,8 +582,11 @@ def run_ours(args):
                  "P2M": e * (n * 16 + nleaves * nc * cb),
                  "M2M": e * 2 * nb * nc * cb,
                  "L2L": e * 2 * nb * nc * cb,
-                 "L2P": e * (n * 16 + nleaves * nc * cb + n * 32),
-                 "reduce": e * (n * 64 + n * 32)}
+                 "L2P": e * (n * 16 + nleaves * nc * cb + n * 4 * cb),  # far field at cb bytes
+                 # the adjoint's dL/dx (w, q, dL/dq-side gradients in, dx out);
+                 # in mixed precision the per-target far + near sum is part of P2P
+                 "reduce": n * (16 + 24 + 24 + 24) if args.precision == "mixed"
+                 else e * (n * 64 + n * 32) + n * (16 + 24 + 24 + 24)}
     for k, bts in hbm_bytes.items():
         work[k] = ("hbm", bts / 1e9, "GB/s", hbm)
     dom = max(pass_ms, key=pass_ms.get)
