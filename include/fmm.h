@@ -306,8 +306,10 @@ uint64_t fmm_kernel_launches(void);
  * rejected with FMM_ERR_INVALID_ARG, and so is a stream of another device
  * than the current one.  The first call on a device looks up the array's
  * device address (once per device; a cudaDeviceReset needs the library
- * reloaded), so make that first call before any stream capture.  All calls
- * share the array: calls that can
+ * reloaded).  Every call reads the root cube back and synchronises `stream`,
+ * so no call can be part of a CUDA graph: a stream that is capturing is
+ * rejected with FMM_ERR_INVALID_ARG (the caller's capture is left intact).
+ * All calls share the array: calls that can
  * overlap on the GPU (different streams, or different host threads on one
  * device) race and must be serialised by the caller.  Synchronises `stream`
  * (the root cube and the finiteness check are read back).

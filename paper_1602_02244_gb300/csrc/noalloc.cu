@@ -98,6 +98,13 @@ extern "C" fmm_status fmm_morton_sort_noalloc(const double *d_xyz, int64_t n, ui
     return record_error(FMM_ERR_INVALID_ARG, "fmm_morton_sort_noalloc: a device pointer is NULL");
   try {
     cudaStream_t s = (cudaStream_t)stream;
+    // the read-back below cannot be captured: refuse before touching the stream
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FMM_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+      return record_error(FMM_ERR_INVALID_ARG,
+                          "fmm_morton_sort_noalloc: the stream is capturing a CUDA graph; every "
+                          "call synchronises its stream and cannot be captured");
     unsigned char *base = scratch_for_device(s);
     if (n == 0) return FMM_OK;
     double *partial = reinterpret_cast<double *>(base + kPartialOff);

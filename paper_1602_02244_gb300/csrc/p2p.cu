@@ -331,6 +331,17 @@ __global__ void k_p2p_meta(int64_t nleaves, const int32_t *__restrict__ leaves,
   }
 }
 
+// far + (hi + lo), the compensated near-field sum, as an FP64 value with three
+// FP64 operations: Knuth's two_sum gives hi + far = s + e exactly in FP32,
+// e + lo is one FP32 rounding of a term ~2^-24 below s, and the result is
+// s + (e + lo) rounded once in FP64 (GB300's FP64 pipe is narrow)
+__device__ __forceinline__ double add_far_near(float far, float hi, float lo) {
+  const float s = __fadd_rn(hi, far);
+  const float bv = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(far, bv));
+  return (double)s + (double)__fadd_rn(e, lo);
+}
+
 // one staged batch: up to 32 pieces (U-list leaves, or one part of a leaf
 // larger than the buffer)
 struct P2PBatch {
@@ -583,18 +594,18 @@ __global__ void __launch_bounds__(kP2PThreads, MINB)
             h[a] = sum;
             l[a] = __fadd_rn(__fadd_rn(l[a], l2), err);
           }
-        // the target is finished here: far field + near field in FP64, written
-        // at its input index (the gradient of 1/r points away from the sources)
+        // the target is finished here: far field + near field, written at its
+        // input index (the gradient of 1/r points away from the sources)
         const int i = tl + per * t;
         if (gi == 0 && i < tcount) {
           const int64_t si = fb + tc + i;
           const float4 fr = far[si];
           const int64_t o = perm[si];
-          phi[o] = (double)fr.x + ((double)h[0] + (double)l[0]);
+          phi[o] = add_far_near(fr.x, h[0], l[0]);
           if (grad) {
-            grad[3 * o] = (double)fr.y - ((double)h[1] + (double)l[1]);
-            grad[3 * o + 1] = (double)fr.z - ((double)h[2] + (double)l[2]);
-            grad[3 * o + 2] = (double)fr.w - ((double)h[3] + (double)l[3]);
+            grad[3 * o] = add_far_near(fr.y, -h[1], -l[1]);
+            grad[3 * o + 1] = add_far_near(fr.z, -h[2], -l[2]);
+            grad[3 * o + 2] = add_far_near(fr.w, -h[3], -l[3]);
           }
         }
       }

@@ -55,3 +55,24 @@ def test_noalloc_sort_rejects_oversized_input(cuda):
     assert st == 1
     msg = binding.library().fmm_last_error_message().decode()
     assert "FMM_NOALLOC_MAX_POINTS" in msg
+
+
+def test_noalloc_sort_refuses_a_capturing_stream(cuda):
+    # every call reads the root cube back and synchronises its stream, which a
+    # CUDA graph capture cannot hold: the call is refused and the capture stays valid
+    f = noalloc_fn()
+    n = 1000
+    X = torch.tensor(workloads.uniform_cube(n, 6), device=cuda)
+    keys = torch.empty(n, dtype=torch.int64, device=cuda)
+    perm = torch.empty(n, dtype=torch.int32, device=cuda)
+    y = torch.zeros(4, device=cuda)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        st = f(X.data_ptr(), n, keys.data_ptr(), perm.data_ptr(), None, stream)
+        y.add_(1.0)
+    assert st == 1
+    assert "capturing" in binding.library().fmm_last_error_message().decode()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y.cpu(), torch.ones(4))
