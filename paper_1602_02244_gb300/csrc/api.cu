@@ -345,12 +345,23 @@ fmm_status fmm_solve_host(fmm_plan_t plan, const double *h_xyz, const double *h_
       build_tree(*plan, nullptr, 0);
       return;
     }
-    plan->host_io.resize(8 * (size_t)n, s);
-    double *d_xyz = plan->host_io.p, *d_q = d_xyz + 3 * n, *d_phi = d_q + n, *d_grad = d_phi + n;
+    fmm_plan_impl &P = *plan;
+    if (!P.copy_stream) FMM_CUDA(cudaStreamCreateWithFlags(&P.copy_stream, cudaStreamNonBlocking));
+    for (auto &e : P.copy_ev)
+      if (!e) FMM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaStream_t c = P.copy_stream;
+    P.host_io.resize(8 * (size_t)n, s);
+    double *d_xyz = P.host_io.p, *d_q = d_xyz + 3 * n, *d_phi = d_q + n, *d_grad = d_phi + n;
+    // the coordinates first, alone; the charges on the side stream while the
+    // tree is built (after the staging buffer exists and the coordinates landed)
     FMM_CUDA(cudaMemcpyAsync(d_xyz, h_xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaMemcpyAsync(d_q, h_q, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    build_tree(*plan, d_xyz, n);
-    eval_fmm(*plan, d_q, d_phi, h_grad ? d_grad : nullptr);
+    FMM_CUDA(cudaEventRecord(P.copy_ev[0], s));
+    FMM_CUDA(cudaStreamWaitEvent(c, P.copy_ev[0], 0));
+    FMM_CUDA(cudaMemcpyAsync(d_q, h_q, sizeof(double) * n, cudaMemcpyHostToDevice, c));
+    FMM_CUDA(cudaEventRecord(P.copy_ev[3], c));
+    build_tree(P, d_xyz, n);
+    FMM_CUDA(cudaStreamWaitEvent(s, P.copy_ev[3], 0));  // q has landed
+    eval_fmm(P, d_q, d_phi, h_grad ? d_grad : nullptr);
     FMM_CUDA(cudaMemcpyAsync(h_phi, d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     if (h_grad)
       FMM_CUDA(cudaMemcpyAsync(h_grad, d_grad, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
@@ -383,15 +394,19 @@ fmm_status fmm_solve_adjoint_host(fmm_plan_t plan, const double *h_xyz, const do
     P.host_io.resize(13 * (size_t)n, s);
     double *d_xyz = P.host_io.p, *d_q = d_xyz + 3 * n, *d_w = d_q + n;
     double *d_phi = d_w + n, *d_grad = d_phi + n, *d_dq = d_grad + 3 * n, *d_dx = d_dq + n;
-    // the side stream starts after the staging buffer exists (stream order on s)
+    // the coordinates go up first, alone (the tree needs them); the charges
+    // and the loss weights follow on the side stream while the tree is built
+    // (the side stream starts after the staging buffer exists and the
+    // coordinates have landed: stream order on s)
+    FMM_CUDA(cudaMemcpyAsync(d_xyz, h_xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
     FMM_CUDA(cudaEventRecord(P.copy_ev[0], s));
     FMM_CUDA(cudaStreamWaitEvent(c, P.copy_ev[0], 0));
-    FMM_CUDA(cudaMemcpyAsync(d_xyz, h_xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
-    FMM_CUDA(cudaMemcpyAsync(d_q, h_q, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    // the loss weights go up while the tree is built
+    FMM_CUDA(cudaMemcpyAsync(d_q, h_q, sizeof(double) * n, cudaMemcpyHostToDevice, c));
+    FMM_CUDA(cudaEventRecord(P.copy_ev[3], c));
     FMM_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(double) * n, cudaMemcpyHostToDevice, c));
     FMM_CUDA(cudaEventRecord(P.copy_ev[1], c));
     build_tree(P, d_xyz, n);
+    FMM_CUDA(cudaStreamWaitEvent(s, P.copy_ev[3], 0));  // q has landed
     eval_fmm(P, d_q, d_phi, d_grad);
     // phi and grad come down while the adjoint runs (it only reads d_grad)
     FMM_CUDA(cudaEventRecord(P.copy_ev[2], s));

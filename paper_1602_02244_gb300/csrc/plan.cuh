@@ -59,7 +59,7 @@ struct fmm_plan_impl {
   // host-buffer calls: a side stream for copies that overlap the computation,
   // and the events that order it against `stream` (created on first use)
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t copy_ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t copy_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   // problems: a plan holds one problem, or a batch of independent problems
   // (a forest: each problem has its own root cube and tree; they never
