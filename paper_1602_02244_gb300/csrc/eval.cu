@@ -120,7 +120,7 @@ M2LTcForm tc_form(fmm_plan_impl &P) {
 }
 
 // Once per plan, for the FP32 near field: the staging record of every U entry
-// and the leaves sorted by decreasing work (targets x sources).  Plan work:
+// and the leaves sorted by decreasing work class (targets x sources).  Plan work:
 // the profiler books it under the lists.
 void prepare_p2p_f32(fmm_plan_impl &P) {
   if (P.p2p_meta_ok) return;
