@@ -245,8 +245,8 @@ void eval_mixed(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_gr
                                                         P.L32.p, P.L64.p, P.ops.l2l64.p, P.L64.p,
                                                         P.L32.p, s);
     else
-      launch_l2l_f32q(p, l, nbl, P.oct_off.p, P.oct_order.p, P.box_parent.p, P.ops.l2l32t.p,
-                      P.L32.p, s);
+      launch_l2l_f32q(p, l, b0, nbl, P.oct_off.p, P.oct_order.p, P.box_parent.p, P.box_geo.p,
+                      P.ops.l2l32t.p, P.L32.p, s);
   }
   {
     PassScope ps_(P, kPassL2P);

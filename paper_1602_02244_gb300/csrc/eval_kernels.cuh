@@ -60,9 +60,10 @@ void launch_m2m_f32q(int p, int l, int32_t b0, int32_t nbl, int32_t nchildren,
 void launch_octant_groups(int nlevels, const int32_t *level_off_host, int32_t b0, int32_t nb,
                           const BoxGeo *geo, int32_t *oct_off, int32_t *oct_pos, int32_t *oct_order,
                           cudaStream_t s);
-// FP32 L2L into the nbl boxes of level l from their parents
-void launch_l2l_f32q(int p, int l, int32_t nbl, const int32_t *oct_off, const int32_t *oct_order,
-                     const int32_t *parent, const float *opT, float *L, cudaStream_t s);
+// FP32 L2L into the nbl boxes [b0, b0 + nbl) of level l from their parents
+void launch_l2l_f32q(int p, int l, int32_t b0, int32_t nbl, const int32_t *oct_off,
+                     const int32_t *oct_order, const int32_t *parent, const BoxGeo *geo,
+                     const float *opT, float *L, cudaStream_t s);
 void launch_combine(int64_t n, const int32_t *iperm, const double *far, const double *near,
                     double *phi, double *grad, cudaStream_t s);
 void launch_adjoint_dx(int64_t n, const double *w, const double *q, const double *gq,
