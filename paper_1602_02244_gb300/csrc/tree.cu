@@ -625,6 +625,13 @@ int64_t counts_to_offsets(fmm_plan_impl &P, const int32_t *cnt, DBuf<int32_t> &o
   return read_scalar(off.p + nrows, P.stream);
 }
 
+// the same without reading the total back (off[nrows] holds it on the device)
+void counts_to_offsets_async(fmm_plan_impl &P, const int32_t *cnt, DBuf<int32_t> &off,
+                             int64_t nrows) {
+  off.resize(nrows + 1, P.stream);
+  scan_exclusive(cnt, off.p, nrows, off.p + nrows, P.s_scan, P.stream);
+}
+
 int64_t compact(fmm_plan_impl &P, int64_t n, const int32_t *flag, DBuf<int32_t> &out) {
   cudaStream_t s = P.stream;
   P.s_i32c.resize(n + 1, s);
@@ -920,8 +927,11 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
                                            P.colleagues.p, P.ncolleagues.p, P.s_i32a.p, nullptr,
                                            nullptr);
   FMM_LAUNCH_CHECK();
-  int64_t nca = counts_to_offsets(P, P.s_i32a.p, P.ca_off, nb);
-  P.ca_idx.resize(nca > 0 ? nca : 1, s);
+  // CA(B) holds distinct leaves no smaller than B that touch it, which do not
+  // overlap: at most 26 (and X(C), a subset of CA(parent(C)), too), so both
+  // are allocated at 26 entries per box without reading their totals back
+  counts_to_offsets_async(P, P.s_i32a.p, P.ca_off, nb);
+  P.ca_idx.resize((size_t)26 * std::max<int64_t>(nb, 1), s);
   k_calist<true><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.box_nchild.p,
                                           P.colleagues.p, P.ncolleagues.p, nullptr, P.ca_off.p,
                                           P.ca_idx.p);
@@ -932,8 +942,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   k_xlist<false><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.ca_off.p, P.ca_idx.p,
                                           P.s_i32a.p, nullptr, nullptr);
   FMM_LAUNCH_CHECK();
-  P.nx = counts_to_offsets(P, P.s_i32a.p, P.x_off, nb);
-  P.x_idx.resize(P.nx > 0 ? P.nx : 1, s);
+  counts_to_offsets_async(P, P.s_i32a.p, P.x_off, nb);
+  P.x_idx.resize((size_t)26 * std::max<int64_t>(nb, 1), s);
   k_xlist<true><<<grid(nb), kT, 0, s>>>(nb, P.box_geo.p, P.box_parent.p, P.ca_off.p, P.ca_idx.p,
                                          nullptr, P.x_off.p, P.x_idx.p);
   FMM_LAUNCH_CHECK();
@@ -955,8 +965,18 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
                                              P.ca_off.p, P.ca_idx.p, ucnt.p, wcnt.p, nullptr,
                                              nullptr, nullptr, nullptr, P.dev_err.p);
     FMM_LAUNCH_CHECK();
-    P.nu = counts_to_offsets(P, ucnt.p, P.u_off, nb);
-    P.nw = counts_to_offsets(P, wcnt.p, P.w_off, nb);
+    counts_to_offsets_async(P, ucnt.p, P.u_off, nb);
+    counts_to_offsets_async(P, wcnt.p, P.w_off, nb);
+    {  // the X, U and W totals in one read-back
+      int32_t h[3];
+      FMM_CUDA(cudaMemcpyAsync(&h[0], P.x_off.p + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      FMM_CUDA(cudaMemcpyAsync(&h[1], P.u_off.p + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      FMM_CUDA(cudaMemcpyAsync(&h[2], P.w_off.p + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      FMM_CUDA(cudaStreamSynchronize(s));
+      P.nx = h[0];
+      P.nu = h[1];
+      P.nw = h[2];
+    }
     P.u_idx.resize(P.nu > 0 ? P.nu : 1, s);
     P.w_idx.resize(P.nw > 0 ? P.nw : 1, s);
     k_uwlist<true><<<grid(nl), kT, 0, s>>>(nl, P.leaves.p, P.box_geo.p, P.box_child.p,
