@@ -52,7 +52,7 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 # configuration, or a
 # kernel changed since the capture, reports null.
 TRAFFIC_BYTES = {
-    ("P2P", 4194304, 8, 128, "mixed", 1): 1198.48e6,  # k_p2p_f32<160, 2, 16>, finishing the targets
+    ("P2P", 4194304, 8, 128, "mixed", 1): 944.61e6,  # k_p2p_f32<160, 2, 16>, leaves by work class
 }
 
 
