@@ -59,6 +59,23 @@ def _declare(L):
     L.oracle_dual_sizes.argtypes = [ctypes.c_void_p, _I64]
     L.oracle_dual_export.argtypes = [ctypes.c_void_p, _I32, _I32, _I32, _I32, _D]
     L.oracle_dual_eval.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _int, _D, _D, _D]
+    dbl = ctypes.c_double
+    L.oracle_sph_bessel.argtypes = [_int, dbl, _D, _D]
+    L.oracle_sph_harmonics.argtypes = [_int, _D, _D]
+    L.oracle_h_wave.argtypes = [_int, dbl, _D, _int, _D]
+    L.oracle_gauss_legendre.argtypes = [_int, _D, _D]
+    L.oracle_gaunt_size.argtypes = [_int]
+    L.oracle_gaunt_size.restype = _i64
+    L.oracle_gaunt_table.argtypes = [_int, _D]
+    L.oracle_h_translate.argtypes = [_int, dbl, _D, _D, _int, _D, _D]
+    L.oracle_h_direct.argtypes = [_i64, _D, _D, _i64, _D, dbl, _D]
+    L.oracle_h_p2m.argtypes = [_int, dbl, _D, _i64, _D, _D, _D]
+    L.oracle_h_p2l.argtypes = [_int, dbl, _D, _i64, _D, _D, _D]
+    for f in ("oracle_h_m2m", "oracle_h_m2l", "oracle_h_l2l"):
+        getattr(L, f).argtypes = [_int, dbl, _D, _D, _D, _D, _D]
+    L.oracle_h_l2p.argtypes = [_int, dbl, _D, _D, _i64, _D, _D]
+    L.oracle_h_m2p.argtypes = [_int, dbl, _D, _D, _i64, _D, _D]
+    L.oracle_h_fmm_eval.argtypes = [ctypes.c_void_p, _int, dbl, _D, _D]
 
 
 def _p(a, t=_D):
@@ -234,6 +251,13 @@ class Tree:
         lib().oracle_fmm_eval(self._h, p, _p(q), _p(phi), _p(g))
         return (phi, g) if grad else phi
 
+    def helmholtz_eval(self, p, kappa, q):
+        """Helmholtz FMM mat-vec: complex q (input order) -> complex phi."""
+        q = _c128(q)
+        phi = np.zeros(self.n, np.complex128)
+        lib().oracle_h_fmm_eval(self._h, p, float(kappa), _p(q), _p(phi))
+        return phi
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h and _lib is not None:
@@ -279,3 +303,115 @@ class Dual:
         if h and _lib is not None:
             _lib.oracle_dual_free(h)
             self._h = None
+
+
+# ---------------------------------------------------------------- Helmholtz
+# Kernel e^{i kappa r}/r; complex arrays are numpy complex128.
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def sph_bessel(nmax, x):
+    """(j_0..j_nmax, y_0..y_nmax) at x > 0."""
+    j = np.zeros(nmax + 1)
+    y = np.zeros(nmax + 1)
+    lib().oracle_sph_bessel(nmax, float(x), _p(j), _p(y))
+    return j, y
+
+
+def sph_harmonics(p, x):
+    Y = np.zeros(ncoef(p), np.complex128)
+    lib().oracle_sph_harmonics(p, _p(_f64(x)), _p(Y))
+    return Y
+
+
+def h_wave(p, kappa, x, singular):
+    X = np.zeros(ncoef(p), np.complex128)
+    lib().oracle_h_wave(p, float(kappa), _p(_f64(x)), int(bool(singular)), _p(X))
+    return X
+
+
+def gauss_legendre(n):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().oracle_gauss_legendre(n, _p(x), _p(w))
+    return x, w
+
+
+def gaunt_table(p):
+    G = np.zeros(lib().oracle_gaunt_size(p))
+    lib().oracle_gaunt_table(p, _p(G))
+    return G
+
+
+def gaunt(G, p, n, m, n2, m2, l):
+    """G(n,m; n2,m2; l) from a table of gaunt_table(p)."""
+    l0 = abs(n - n2)
+    if l < l0 or l > n + n2 or (l - l0) % 2 or abs(m - m2) > l:
+        return 0.0
+    nc = ncoef(p)
+    return G[((n * n + n + m) * nc + n2 * n2 + n2 + m2) * (p + 1) + (l - l0) // 2]
+
+
+def h_translate(p, kappa, G, t, singular, X_in):
+    out = np.zeros(ncoef(p), np.complex128)
+    lib().oracle_h_translate(p, float(kappa), _p(G), _p(_f64(t)), int(bool(singular)),
+                             _p(_c128(X_in)), _p(out))
+    return out
+
+
+def h_direct(src, q, kappa, tgt=None):
+    src = _f64(src).reshape(-1, 3)
+    tgt = src if tgt is None else _f64(tgt).reshape(-1, 3)
+    q = _c128(q)
+    phi = np.zeros(len(tgt), np.complex128)
+    lib().oracle_h_direct(len(src), _p(src), _p(q), len(tgt), _p(tgt), float(kappa), _p(phi))
+    return phi
+
+
+def h_p2m(p, kappa, c, xyz, q):
+    xyz = _f64(xyz).reshape(-1, 3)
+    M = np.zeros(ncoef(p), np.complex128)
+    lib().oracle_h_p2m(p, float(kappa), _p(_f64(c)), len(xyz), _p(xyz), _p(_c128(q)), _p(M))
+    return M
+
+
+def h_p2l(p, kappa, c, xyz, q):
+    xyz = _f64(xyz).reshape(-1, 3)
+    L = np.zeros(ncoef(p), np.complex128)
+    lib().oracle_h_p2l(p, float(kappa), _p(_f64(c)), len(xyz), _p(xyz), _p(_c128(q)), _p(L))
+    return L
+
+
+def _h_translate3(fn, p, kappa, G, c_from, X, c_to):
+    out = np.zeros(ncoef(p), np.complex128)
+    getattr(lib(), fn)(p, float(kappa), _p(G), _p(_f64(c_from)), _p(_c128(X)), _p(_f64(c_to)),
+                       _p(out))
+    return out
+
+
+def h_m2m(p, kappa, G, c_child, M, c_parent):
+    return _h_translate3("oracle_h_m2m", p, kappa, G, c_child, M, c_parent)
+
+
+def h_m2l(p, kappa, G, c_src, M, c_tgt):
+    return _h_translate3("oracle_h_m2l", p, kappa, G, c_src, M, c_tgt)
+
+
+def h_l2l(p, kappa, G, c_parent, L, c_child):
+    return _h_translate3("oracle_h_l2l", p, kappa, G, c_parent, L, c_child)
+
+
+def h_l2p(p, kappa, c, L, xyz):
+    xyz = _f64(xyz).reshape(-1, 3)
+    phi = np.zeros(len(xyz), np.complex128)
+    lib().oracle_h_l2p(p, float(kappa), _p(_f64(c)), _p(_c128(L)), len(xyz), _p(xyz), _p(phi))
+    return phi
+
+
+def h_m2p(p, kappa, c, M, xyz):
+    xyz = _f64(xyz).reshape(-1, 3)
+    phi = np.zeros(len(xyz), np.complex128)
+    lib().oracle_h_m2p(p, float(kappa), _p(_f64(c)), _p(_c128(M)), len(xyz), _p(xyz), _p(phi))
+    return phi

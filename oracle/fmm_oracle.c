@@ -10,6 +10,7 @@
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (oracle/build.py).
  */
 #include "fmm_oracle.h"
+#include "oracle_tree.h"
 
 #include <complex.h>
 #include <math.h>
@@ -337,11 +338,6 @@ void oracle_morton_keys(int64_t n, const double *xyz, const double lo[3], double
 /* ------------------------------------------------------------------------
  * Tree and lists (§2.2 interaction list; adaptive U/W/X lists).
  * ---------------------------------------------------------------------- */
-typedef struct {
-  int32_t *a;
-  int64_t n, cap;
-} ivec;
-
 static void ivec_push(ivec *v, int32_t x) {
   if (v->n == v->cap) {
     v->cap = v->cap ? 2 * v->cap : 16;
@@ -350,23 +346,6 @@ static void ivec_push(ivec *v, int32_t x) {
   v->a[v->n++] = x;
 }
 
-struct oracle_tree {
-  int64_t n;
-  double lo[3], D;
-  int leaf_size, max_depth;
-  uint64_t *keys;    /* sorted */
-  int32_t *perm;     /* perm[i] = input index of the i-th sorted point */
-  double *xyz;       /* sorted coordinates */
-  int nlevels;
-  int32_t *level_offset;
-  int64_t nboxes;
-  uint64_t *box_key; /* anchor key at the box's level */
-  int32_t *box_level, *box_first, *box_count, *box_parent, *box_child, *box_nchild;
-  int32_t (*anchor)[3];
-  double (*center)[3];
-  double *side; /* per level */
-  ivec *U, *V, *W, *X; /* per box */
-};
 
 typedef struct {
   uint64_t key;

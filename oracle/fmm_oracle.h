@@ -124,6 +124,36 @@ void oracle_dual_export(const oracle_dual *d, int32_t *m2l_off, int32_t *m2l_idx
 void oracle_dual_eval(const oracle_tree *t, const oracle_dual *d, int p, const double *q,
                       double *phi, double *grad);
 
+/* ---- Helmholtz kernel e^{i kappa r}/r (helmholtz_oracle.c; basis and
+ *      translation identities in that file's preamble).  Complex arrays are
+ *      interleaved (re, im); coefficient index n*n+n+m. */
+void oracle_sph_bessel(int nmax, double x, double *j, double *y); /* y may be NULL */
+void oracle_sph_harmonics(int p, const double x[3], double *Y);  /* (p+1)^2 complex */
+void oracle_h_wave(int p, double kappa, const double x[3], int singular, double *X);
+void oracle_gauss_legendre(int n, double *x, double *w);
+int64_t oracle_gaunt_size(int p);
+void oracle_gaunt_table(int p, double *G);
+void oracle_h_translate(int p, double kappa, const double *G, const double t[3], int singular,
+                        const double *in, double *out);
+void oracle_h_direct(int64_t ns, const double *src, const double *q, int64_t nt,
+                     const double *tgt, double kappa, double *phi);
+void oracle_h_p2m(int p, double kappa, const double c[3], int64_t n, const double *xyz,
+                  const double *q, double *M);
+void oracle_h_p2l(int p, double kappa, const double c[3], int64_t n, const double *xyz,
+                  const double *q, double *L);
+void oracle_h_m2m(int p, double kappa, const double *G, const double c_child[3],
+                  const double *Mc, const double c_parent[3], double *Mp);
+void oracle_h_m2l(int p, double kappa, const double *G, const double c_src[3], const double *M,
+                  const double c_tgt[3], double *L);
+void oracle_h_l2l(int p, double kappa, const double *G, const double c_parent[3],
+                  const double *Lp, const double c_child[3], double *Lc);
+void oracle_h_l2p(int p, double kappa, const double c[3], const double *L, int64_t n,
+                  const double *xyz, double *phi);
+void oracle_h_m2p(int p, double kappa, const double c[3], const double *M, int64_t n,
+                  const double *xyz, double *phi);
+void oracle_h_fmm_eval(const oracle_tree *t, int p, double kappa, const double *q,
+                       double *phi);
+
 /* number of OpenMP threads the oracle runs with (1 without OpenMP) */
 int oracle_num_threads(void);
 
