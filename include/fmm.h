@@ -1,6 +1,6 @@
 /*
  * fmm.h -- C-ABI of libfmm: the 3D Laplace (1/r) fast multipole mat-vec on
- * one GB300 (sm_103a).
+ * one GB300 (sm_103a), and its Helmholtz (e^{i kappa r}/r) counterpart.
  *
  * Method (Yokota, Ibeid & Keyes, "Fast Multipole Method as a Matrix-Free
  * Hierarchical Low-Rank Approximation"): the analytic FMM is a matrix-free
@@ -14,6 +14,8 @@
  *                       translation), P2L, L2L, L2P, M2P and the near-field
  *                       direct sum (the dense diagonal blocks, §2.2).
  *   fmm_adjoint      -- the transpose mat-vec and the coordinate gradient.
+ *   fmm_helmholtz_eval -- the same hierarchy with the Helmholtz kernel
+ *                       e^{i kappa r}/r (the paper's second kernel, §1, §4.2).
  *
  * Computed quantities (no 1/(4 pi) factor):
  *   phi_i  = sum_{j != i} q_j / |x_i - x_j|
@@ -139,6 +141,24 @@ fmm_status fmm_plan_set_points(fmm_plan_t plan, const double *d_xyz, void *strea
  * n x 3 or NULL (then gradients are not computed).  Asynchronous. */
 fmm_status fmm_eval(fmm_plan_t plan, const double *d_q, double *d_phi, double *d_grad,
                     void *stream);
+
+/* Helmholtz mat-vec on the plan's tree and U/V/W/X lists (the paper's second
+ * kernel, §1 and §4.2):
+ *   phi_i = sum_{j : x_j != x_i} q_j e^{i kappa |x_i - x_j|} / |x_i - x_j|,
+ * approximated by the low-frequency FMM of order `order` (0..12) in FP64:
+ * expansions in spherical Bessel/Hankel functions times spherical harmonics,
+ * translation operators per level (they depend on kappa times the box side).
+ * d_q, d_phi: n complex values each, interleaved (re, im) doubles, in the
+ * caller's point order, device memory owned by the caller.  kappa > 0 and
+ * finite.  The expansions converge when kappa times the side of a level-2
+ * box is of order one or less (e.g. kappa = 7 on [-1, 1]^3); the error falls
+ * with `order` as for Laplace.  The first call for a (kappa, order, tree
+ * depth, root cube) builds that set of operators (synchronous); later calls
+ * are asynchronous on `stream`.  Errors: FMM_ERR_INVALID_ARG for a NULL plan
+ * or pointer (n > 0), an order outside 0..12, kappa <= 0 or not finite, a
+ * dual-tree plan or a batch plan (one problem only); FMM_ERR_OOM, FMM_ERR_CUDA. */
+fmm_status fmm_helmholtz_eval(fmm_plan_t plan, double kappa, int order, const double *d_q,
+                              double *d_phi, void *stream);
 
 /* Adjoint of L = sum_i w_i phi_i with respect to q and x (frozen plan):
  *   d_dq[k]      = dL/dq_k = (A~^T w)_k = (A~ w)_k   (A~ is symmetric)
@@ -284,6 +304,13 @@ fmm_status fmm_direct(const double *d_src, const double *d_q, int64_t n, const d
  * FMM_ERR_INVALID_ARG for m < 0, h <= 0, m^3 beyond int64 range or NULL
  * pointers with m > 0. */
 fmm_status fmm_laplace7_apply(const double *d_u, double *d_out, int64_t m, double h, void *stream);
+
+/* The Helmholtz operator of the same experiment (§4.2, wave number kappa):
+ *   out = (7-point Laplacian as above) u - kappa^2 u.
+ * Same arguments, layout and errors as fmm_laplace7_apply, plus
+ * FMM_ERR_INVALID_ARG for a kappa that is not finite. */
+fmm_status fmm_helmholtz7_apply(const double *d_u, double *d_out, int64_t m, double h,
+                                double kappa, void *stream);
 
 /* Number of kernels this library has launched in this process so far. */
 uint64_t fmm_kernel_launches(void);

@@ -22,7 +22,8 @@ EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_
            "fmm_eval", "fmm_eval_graph", "fmm_adjoint", "fmm_solve_host", "fmm_solve_adjoint_host",
            "fmm_sync", "fmm_plan_sizes", "fmm_plan_export", "fmm_plan_destroy", "fmm_direct",
            "fmm_laplace7_apply", "fmm_wait_selftest", "fmm_fp32_peak", "fmm_plan_tiles",
-           "fmm_status_string", "fmm_last_error_message")
+           "fmm_status_string", "fmm_last_error_message", "fmm_helmholtz_eval",
+           "fmm_helmholtz7_apply")
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
                  "box_parent", "box_child", "box_nchild", "u_off", "u_idx", "v_off", "v_idx",
@@ -64,6 +65,7 @@ def library():
         L.fmm_plan_rebuild.argtypes = [_vp, _vp, _i64, _vp]
         L.fmm_plan_set_points.argtypes = [_vp, _vp, _vp]
         L.fmm_eval.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.fmm_helmholtz_eval.argtypes = [_vp, ctypes.c_double, _int, _vp, _vp, _vp]
         L.fmm_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.fmm_eval_graph.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.fmm_sync.argtypes = [_vp, _vp]
@@ -76,6 +78,7 @@ def library():
         L.fmm_plan_destroy.argtypes = [_vp]
         L.fmm_direct.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _vp]
         L.fmm_laplace7_apply.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp]
+        L.fmm_helmholtz7_apply.argtypes = [_vp, _vp, _i64, ctypes.c_double, ctypes.c_double, _vp]
         L.fmm_wait_selftest.argtypes = [_int, ctypes.c_longlong, _vp]
         L.fmm_status_string.argtypes = [_int]
         L.fmm_status_string.restype = ctypes.c_char_p
@@ -193,6 +196,21 @@ class Plan:
         return phi, g
 
     __call__ = eval
+
+    def helmholtz(self, q, kappa, order=8, out=None, stream=None):
+        """phi_i = sum_j q_j e^{i kappa r_ij} / r_ij by the low-frequency FMM of
+        ``order`` on this plan's tree (``fmm_helmholtz_eval``).  ``q``: (N,)
+        complex128 CUDA tensor; returns (N,) complex128."""
+        if not isinstance(q, torch.Tensor) or not q.is_cuda or q.dtype != torch.complex128:
+            raise TypeError("q must be a CUDA complex128 tensor")
+        if tuple(q.shape) != (self.n,):
+            raise ValueError("q must have shape (%d,)" % self.n)
+        q = q.contiguous()
+        phi = torch.empty(self.n, dtype=torch.complex128, device=self.device) if out is None else out
+        with torch.cuda.device(self.device):
+            _check(library().fmm_helmholtz_eval(self._h, float(kappa), int(order), _ptr(q),
+                                                _ptr(phi), _stream(stream)))
+        return phi
 
     def adjoint(self, w, q, grad_q=None, want_dx=True, out=None, stream=None):
         """dL/dq and dL/dx for L = sum w_i phi_i (frozen plan).  ``out``:
@@ -359,4 +377,20 @@ def laplace7(u, h, out=None, stream=None):
     out = torch.empty_like(u) if out is None else out
     with torch.cuda.device(u.device):
         _check(library().fmm_laplace7_apply(_ptr(u), _ptr(out), m, float(h), _stream(stream)))
+    return out
+
+
+def helmholtz7(u, h, kappa, out=None, stream=None):
+    """(7-point Laplacian - kappa^2) u with zero Dirichlet boundary values, as
+    ``laplace7`` (``fmm_helmholtz7_apply``)."""
+    if not isinstance(u, torch.Tensor) or not u.is_cuda or u.dtype != torch.float64:
+        raise TypeError("u must be a CUDA float64 tensor")
+    m = round(u.numel() ** (1.0 / 3.0))
+    if m ** 3 != u.numel():
+        raise ValueError("u must hold m^3 values")
+    u = u.contiguous()
+    out = torch.empty_like(u) if out is None else out
+    with torch.cuda.device(u.device):
+        _check(library().fmm_helmholtz7_apply(_ptr(u), _ptr(out), m, float(h), float(kappa),
+                                              _stream(stream)))
     return out

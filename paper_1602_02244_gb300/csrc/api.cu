@@ -160,6 +160,7 @@ void release_plan(fmm_plan_impl &P) {
   P.p2p_ticket.release();
   P.oct_off.release(); P.oct_order.release(); P.oct_pos.release(); P.m2m_part.release();
   P.far32.release();
+  release_helmholtz(P);
 }
 
 }  // namespace fmm
@@ -269,6 +270,16 @@ fmm_status fmm_eval(fmm_plan_t plan, const double *d_q, double *d_phi, double *d
   return guarded([&] {
     plan->stream = (cudaStream_t)stream;
     eval_fmm(*plan, d_q, d_phi, d_grad);
+  });
+}
+
+fmm_status fmm_helmholtz_eval(fmm_plan_t plan, double kappa, int order, const double *d_q,
+                              double *d_phi, void *stream) {
+  if (!plan) return fail(FMM_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->n > 0 && (!d_q || !d_phi)) return fail(FMM_ERR_INVALID_ARG, "d_q or d_phi is NULL");
+  return guarded([&] {
+    plan->stream = (cudaStream_t)stream;
+    eval_helmholtz(*plan, kappa, order, d_q, d_phi);
   });
 }
 

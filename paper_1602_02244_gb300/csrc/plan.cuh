@@ -40,6 +40,17 @@ struct Operators {
   DBuf<float> rot32, zt32;
 };
 
+// Helmholtz mat-vec (helmholtz.cu): translation operators for one (kappa,
+// order, root cube, depth) -- per level, input-major [k][j] complex --, and the
+// evaluation workspace (multipoles, locals, sorted charges, far field)
+struct HelmholtzState {
+  double kappa = 0.0, D = 0.0;
+  int order = -1, nlevels = 0;
+  DBuf<double> gaunt;
+  DBuf<double2> m2l, m2m, l2l, xtab;
+  DBuf<double2> M, L, q, far;
+};
+
 // passes timed by the optional profiler (fmm_profile / fmm_profile_read)
 enum Pass { kPassSort = 0, kPassBoxes, kPassLists, kPassP2M, kPassM2M, kPassM2L, kPassP2L,
             kPassL2L, kPassL2P, kPassM2P, kPassP2P, kPassReduce, kNumPasses };
@@ -187,6 +198,8 @@ struct fmm_plan_impl {
   DBuf<uint64_t> s_u64a, s_u64b;
   DBuf<int32_t> s_total;            // device scalars for scan totals
   DBuf<int32_t> ca_off, ca_idx;     // coarser-or-equal adjacent leaves per box
+
+  HelmholtzState helm;
 };
 
 // Records CUDA events around one pass when the plan's profiler is on.
@@ -249,6 +262,10 @@ void eval_fmm(fmm_plan_impl &P, const double *d_q, double *d_phi, double *d_grad
 void adjoint_fmm(fmm_plan_impl &P, const double *d_w, const double *d_q, const double *d_grad_q,
                  double *d_dq, double *d_dx);
 void release_plan(fmm_plan_impl &P);
+// helmholtz.cu: phi = sum_j q_j e^{i kappa |x_i - x_j|} / |x_i - x_j| (complex,
+// interleaved, input order), and the release of its buffers
+void eval_helmholtz(fmm_plan_impl &P, double kappa, int p, const double *d_q, double *d_phi);
+void release_helmholtz(fmm_plan_impl &P);
 void drop_graph(fmm_plan_impl &P);
 
 // read a device int32 scalar (synchronous)

@@ -18,6 +18,16 @@ Polak-Ribiere form of beta), which tolerates a preconditioner that is
 symmetric only up to rounding, as a low-order mixed-precision FMM is.  The
 vector updates are plain tensor operations; the operator and the
 preconditioner run in this library's kernels.
+
+The Helmholtz half: -Laplace(u) - kappa^2 u = f with the same boundary
+condition and stencil (``fmm_helmholtz7_apply``).  Its free-space Green's
+function is cos(kappa r) / (4 pi r), the real part of e^{i kappa r} / (4 pi r),
+so the preconditioner is the real part of the Helmholtz FMM mat-vec with
+charges r_j h^3 / (4 pi), plus the same cell term (the cell integral of
+cos(kappa r)/(4 pi r) differs from the Laplace one by O((kappa h)^2)).  The
+operator is symmetric but indefinite once kappa^2 exceeds its smallest
+eigenvalues (3 pi^2 / 4 on this cube), so the solver is restarted flexible
+GMRES (right preconditioning) instead of CG.
 """
 import math
 
@@ -86,3 +96,94 @@ def fpcg(apply_a, b, apply_m=None, tol=1e-8, maxiter=1000):
         rz = rz_new
         p.mul_(beta).add_(z)
     return x, maxiter, hist
+
+
+class HelmholtzGreenPreconditioner:
+    """z = Re[h^3 / (4 pi) sum_j r_j e^{i kappa |x_i - x_j|} / |x_i - x_j|] + CELL_SELF h^2 r_i,
+    the sum evaluated by the Helmholtz FMM of ``order`` (plan built once)."""
+
+    def __init__(self, h, kappa, order=4, leaf_size=64, device=None):
+        self.h = h
+        self.kappa = float(kappa)
+        self.order = order
+        self.points, self.m = grid_points(h, device=device)
+        self.plan = binding.Plan(self.points, leaf_size=leaf_size, order=min(order, 8),
+                                 precision="fp64")
+        self.scale = h ** 3 / (4.0 * math.pi)
+        self.self_coef = CELL_SELF * h * h
+
+    def __call__(self, r):
+        q = (self.scale * r).to(torch.complex128)
+        phi = self.plan.helmholtz(q, self.kappa, self.order)
+        return phi.real + self.self_coef * r
+
+    def close(self):
+        self.plan.close()
+
+
+def fgmres(apply_a, b, apply_m=None, tol=1e-8, restart=50, maxiter=1000):
+    """Restarted flexible GMRES with right preconditioning for A x = b (A need
+    not be symmetric or definite).  Arnoldi by modified Gram-Schmidt, the small
+    least-squares problem by Givens rotations.  Returns (x, iterations,
+    relative residual history)."""
+    import numpy as np
+    x = torch.zeros_like(b)
+    bnorm = float(torch.linalg.vector_norm(b))
+    if bnorm == 0.0:
+        return x, 0, [0.0]
+    r = b.clone()
+    beta = bnorm
+    hist = [1.0]
+    it = 0
+    while True:
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        j_end = 0
+        done = False
+        for j in range(restart):
+            z = apply_m(V[j]) if apply_m else V[j].clone()
+            Z.append(z)
+            w = apply_a(z)
+            for i in range(j + 1):
+                H[i, j] = float(torch.dot(w, V[i]))
+                w.add_(V[i], alpha=-H[i, j])
+            H[j + 1, j] = float(torch.linalg.vector_norm(w))
+            if H[j + 1, j] > 0.0:
+                V.append(w / H[j + 1, j])
+            for i in range(j):  # earlier rotations on the new column
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            d = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = (1.0, 0.0) if d == 0.0 else (H[j, j] / d, H[j + 1, j] / d)
+            H[j, j] = d
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            j_end = j + 1
+            hist.append(abs(g[j + 1]) / bnorm)
+            if hist[-1] <= tol or it >= maxiter or len(V) == j + 1:
+                done = True
+                break
+        y = np.zeros(j_end)
+        for i in range(j_end - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:j_end] @ y[i + 1:j_end]) / H[i, i]
+        for i in range(j_end):
+            x.add_(Z[i], alpha=float(y[i]))
+        if done:
+            # the true residual, for the record
+            r = b - apply_a(x)
+            hist[-1] = float(torch.linalg.vector_norm(r)) / bnorm
+            if hist[-1] <= tol or it >= maxiter:
+                return x, it, hist
+        else:
+            r = b - apply_a(x)
+        beta = float(torch.linalg.vector_norm(r))
+        if beta / bnorm <= tol:
+            return x, it, hist

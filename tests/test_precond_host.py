@@ -42,3 +42,26 @@ def test_grid_points_order_and_spacing():
     assert torch.allclose(pts[m] - pts[0], torch.tensor([0.0, 0.25, 0.0], dtype=torch.float64))
     assert torch.allclose(pts[m * m] - pts[0], torch.tensor([0.0, 0.0, 0.25], dtype=torch.float64))
     assert float(pts.min()) == -0.75 and float(pts.max()) == 0.75
+
+
+def test_fgmres_solves_nonsymmetric_and_indefinite_systems():
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(0)
+    n = 120
+    A = 3.0 * np.eye(n) + rng.normal(size=(n, n)) / np.sqrt(n)          # nonsymmetric
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    B = Q @ np.diag(np.linspace(-2.0, 5.0, n) + 0.013) @ Q.T            # symmetric indefinite
+    b = rng.normal(size=n)
+    for M, restart in ((A, 20), (B, n)):
+        Mt = torch.tensor(M)
+        x, it, hist = precond.fgmres(lambda v: Mt @ v, torch.tensor(b), None, tol=1e-10,
+                                     restart=restart, maxiter=5 * n)
+        ref = np.linalg.solve(M, b)
+        assert hist[-1] <= 1e-10
+        assert np.linalg.norm(x.numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+    # an exact preconditioner converges in one step; a good one in a few
+    Bi = torch.tensor(np.linalg.inv(B))
+    Bt = torch.tensor(B)
+    x, it, hist = precond.fgmres(lambda v: Bt @ v, torch.tensor(b), lambda v: Bi @ v, tol=1e-10)
+    assert it <= 2 and hist[-1] <= 1e-10
