@@ -90,6 +90,9 @@ def parse():
                     help="also time the dual-tree walk (acceptance theta) on the same points; 0 skips")
     ap.add_argument("--precond", action="store_true",
                     help="add the FMM-preconditioned CG solve of the 7-point Laplace problem")
+    ap.add_argument("--helmholtz", action="store_true",
+                    help="add the Helmholtz mat-vec (kappa = 7) on the h = 2^-5 grid of [-1,1]^3 "
+                         "and the Helmholtz rows of --precond")
     ap.add_argument("--no-lattice", action="store_true",
                     help="skip plan/eval time and peak device memory vs N on uniform lattices")
     return ap.parse_args()
@@ -394,6 +397,130 @@ def precond_leg(dev, h=2.0 ** -5, tol=1e-8):
     return {"problem": "-Laplace u = 1 on [-1,1]^3, u = 0 on the boundary, 7-point stencil, "
                        "h = 2^-5 (%d unknowns), CG to relative residual %.0e" % (m ** 3, tol),
             "runs": rows}
+
+
+def helmholtz_precond_rows(dev, h=2.0 ** -5, kappa=7.0, tol=1e-8):
+    """The Helmholtz half of §4.2 (Fig. 6): -Laplace u - kappa^2 u = 1 on [-1,1]^3,
+    u = 0 on the boundary, h = 2^-5, kappa = 7; restarted flexible GMRES(50)
+    without a preconditioner and with the Helmholtz FMM (real part of the
+    outgoing Green's function, near field in FP32) at low orders."""
+    import torch
+    from paper_1602_02244_gb300 import binding, precond
+    m = int(round(2.0 / h)) - 1
+    b = torch.ones(m ** 3, dtype=torch.float64, device=dev)
+    A = lambda v: binding.helmholtz7(v, h, kappa)
+    precond.fgmres(A, b, None, tol=tol, maxiter=3)  # first-call initialisation, untimed
+    rows = []
+    for order in (None, 2, 3, 4, 6):
+        pre = precond.HelmholtzGreenPreconditioner(h, kappa, order=order, leaf_size=64,
+                                                   device=dev) if order else None
+        if pre is not None:
+            pre(b)  # operators and workspace
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, it, hist = precond.fgmres(A, b, pre, tol=tol, restart=50, maxiter=3000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        row = {"preconditioner": "Helmholtz FMM p=%d" % order if order else "none",
+               "iterations": it, "rel_residual": hist[-1], "solve_ms": 1e3 * dt}
+        if pre is not None:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                pre(b)
+            e1.record()
+            e1.synchronize()
+            row["apply_ms"] = e0.elapsed_time(e1) / 5
+            pre.close()
+        rows.append(row)
+    return {"problem": "-Laplace u - %g^2 u = 1 on [-1,1]^3, u = 0 on the boundary, 7-point "
+                       "stencil, h = 2^-5 (%d unknowns), flexible GMRES(50) to relative residual "
+                       "%.0e" % (kappa, m ** 3, tol), "runs": rows}
+
+
+def helmholtz_leg(dev, L, steps=5, kappa=7.0, h=2.0 ** -5, leaf=64):
+    """The Helmholtz mat-vec (kernel e^{i kappa r}/r, §1 and §4.2) on the
+    paper's Helmholtz domain: the h = 2^-5 interior grid of [-1,1]^3 (63^3 =
+    250,047 points), kappa = 7, complex charges U[-1,1] + i U[-1,1].  Per
+    precision and order: mat-vec time (CUDA events over `steps` calls,
+    operators built before), per-pass times, and the FP64 roofline of M2L
+    (8 flop per complex multiply-add, (p+1)^4 per V pair) and of the FP64 near
+    field against the measured FP64 rate.  cpu_baseline: the oracle's FP64
+    direct sum at 256 sampled targets, against which each run's error is
+    stated."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_1602_02244_gb300 import binding, precond, workloads
+    pts, m = precond.grid_points(h, device=dev)
+    n = m ** 3
+    g = workloads.rng(21)
+    q_h = g.uniform(-1, 1, n) + 1j * g.uniform(-1, 1, n)
+    q = torch.tensor(q_h, device=dev)
+    fp64_tf = binding.fp64_peak()
+    sel = workloads.sample_targets(n, 256, seed=3)
+    cpu = None
+    xyz_h = pts.cpu().numpy()
+    runs = []
+    names = ["sort", "boxes", "lists", "P2M", "M2M", "M2L", "P2L", "L2L", "L2P", "M2P", "P2P",
+             "reduce"]
+    for precision in ("fp64", "mixed"):
+        plan = binding.Plan(pts, leaf_size=leaf, order=4, precision=precision)
+        ex = plan.export()
+        cnt = ex["box_count"].astype(np.int64)
+        uo, ui = ex["u_off"], ex["u_idx"]
+        leaves = np.nonzero(ex["box_nchild"] == 0)[0]
+        p2p_pairs = int(sum(cnt[b] * cnt[ui[uo[b]:uo[b + 1]]].sum() for b in leaves))
+        nv = int(plan.sizes()["nv"])
+        for order in (4, 8):
+            phi = plan.helmholtz(q, kappa, order)
+            for _ in range(2):
+                plan.helmholtz(q, kappa, order, out=phi)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(steps):
+                plan.helmholtz(q, kappa, order, out=phi)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            ma = (ctypes.c_double * 12)()
+            la = (ctypes.c_int64 * 12)()
+            L.fmm_profile(plan._h, 1)
+            L.fmm_profile_read(plan._h, ma, la)
+            plan.helmholtz(q, kappa, order, out=phi)
+            torch.cuda.synchronize()
+            L.fmm_profile_read(plan._h, ma, la)
+            L.fmm_profile(plan._h, 0)
+            passes = {names[i]: ma[i] for i in range(12) if ma[i] > 0}
+            if cpu is None:
+                import oracle
+                t0 = time.perf_counter()
+                ref = oracle.h_direct(xyz_h, q_h, kappa, xyz_h[sel])
+                dt = time.perf_counter() - t0
+                cpu = {"value": len(sel) * n / dt, "unit": "pair interactions/s",
+                       "cores": oracle.num_threads(), "kind": "oracle",
+                       "sample": "FP64 direct sum at %d sampled targets over all %d sources"
+                                 % (len(sel), n)}
+            got = phi.cpu().numpy()[sel]
+            nc = (order + 1) ** 2
+            m2l_flop = 8.0 * nc * nc * nv
+            row = {"precision": precision, "order": order, "ms": ms,
+                   "value": n / (ms / 1e3), "unit": "targets/s",
+                   "rel_error_vs_oracle_direct": float(np.linalg.norm(got - ref) /
+                                                       np.linalg.norm(ref)),
+                   "passes_ms": passes, "v_pairs": nv, "p2p_pairs": p2p_pairs,
+                   "m2l_roofline": {"bound": "alu", "achieved": m2l_flop / (passes["M2L"] / 1e3) / 1e12,
+                                    "peak": fp64_tf, "unit": "TFLOP/s",
+                                    "frac": m2l_flop / (passes["M2L"] / 1e3) / 1e12 / fp64_tf,
+                                    "peak_source": "fmm_fp64_peak, FP64 FMA chains (of measured)"}}
+            runs.append(row)
+        plan.close()
+    return {"workload": "Helmholtz e^{i 7 r}/r mat-vec, interior grid of [-1,1]^3 at h = 2^-5 "
+                        "(%d points), leaf %d" % (n, leaf), "kappa": kappa,
+            "fp64_peak_tflops": fp64_tf, "runs": runs, "cpu_baseline": cpu}
 
 
 def dual_leg(X, Q, S, p, precision, theta, rel_err, steps, stream, ms_lists, ms_eval_lists):
@@ -751,6 +878,10 @@ def run_ours(args):
         line["lattice"] = lattice_leg(dev)
     if args.precond:
         line["precond"] = precond_leg(dev)
+        if args.helmholtz:
+            line["precond_helmholtz"] = helmholtz_precond_rows(dev)
+    if args.helmholtz and rank == 0 and world == 1:
+        line["helmholtz"] = helmholtz_leg(dev, L)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ncpu = args.cpu_sample or n

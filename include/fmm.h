@@ -152,7 +152,10 @@ fmm_status fmm_eval(fmm_plan_t plan, const double *d_q, double *d_phi, double *d
  * caller's point order, device memory owned by the caller.  kappa > 0 and
  * finite.  The expansions converge when kappa times the side of a level-2
  * box is of order one or less (e.g. kappa = 7 on [-1, 1]^3); the error falls
- * with `order` as for Laplace.  The first call for a (kappa, order, tree
+ * with `order` as for Laplace.  A plan of precision FMM_MIXED evaluates the
+ * near field in FP32 (sincos, reciprocal square root; FP64 totals per staged
+ * batch: ~1e-7 relative), every expansion and translation still in FP64.
+ * The first call for a (kappa, order, tree
  * depth, root cube) builds that set of operators (synchronous); later calls
  * are asynchronous on `stream`.  Errors: FMM_ERR_INVALID_ARG for a NULL plan
  * or pointer (n > 0), an order outside 0..12, kappa <= 0 or not finite, a
@@ -272,6 +275,11 @@ fmm_status fmm_wait_selftest(int arrive, long long limit_cycles, void *stream);
  * roofline denominator of the FP32-bound passes.  Synchronous; some tens of
  * milliseconds.  FMM_ERR_INVALID_ARG for a NULL output. */
 fmm_status fmm_fp32_peak(double *tflops, void *stream);
+
+/* Measured FP64 rate of the current GPU in TFLOP/s, the same way with plain
+ * FP64 fused multiply-add chains (the roofline denominator of the FP64-bound
+ * Helmholtz passes).  Synchronous.  FMM_ERR_INVALID_ARG for a NULL output. */
+fmm_status fmm_fp64_peak(double *tflops, void *stream);
 
 /* Synchronise `stream`, then report FMM_ERR_TIMEOUT (once) if a bounded
  * device-side wait of this plan's kernels gave up since the last call, else

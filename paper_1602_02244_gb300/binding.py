@@ -23,7 +23,7 @@ EXPORTS = ("fmm_plan_create", "fmm_plan_create_batch", "fmm_plan_rebuild", "fmm_
            "fmm_sync", "fmm_plan_sizes", "fmm_plan_export", "fmm_plan_destroy", "fmm_direct",
            "fmm_laplace7_apply", "fmm_wait_selftest", "fmm_fp32_peak", "fmm_plan_tiles",
            "fmm_status_string", "fmm_last_error_message", "fmm_helmholtz_eval",
-           "fmm_helmholtz7_apply")
+           "fmm_helmholtz7_apply", "fmm_fp64_peak")
 
 EXPORT_FIELDS = ("keys", "perm", "level_offset", "box_key", "box_level", "box_first", "box_count",
                  "box_parent", "box_child", "box_nchild", "u_off", "u_idx", "v_off", "v_idx",
@@ -72,6 +72,7 @@ def library():
         L.fmm_solve_host.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _vp]
         L.fmm_solve_adjoint_host.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]
         L.fmm_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
+        L.fmm_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
         L.fmm_plan_tiles.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]
         L.fmm_plan_sizes.argtypes = [_vp, ctypes.POINTER(_i64)]
         L.fmm_plan_export.argtypes = [_vp, _int, _vp, ctypes.c_size_t]
@@ -361,6 +362,13 @@ def fp32_peak(stream=None):
     """Measured FP32 rate of the current device in TFLOP/s (fmm_fp32_peak)."""
     v = ctypes.c_double()
     _check(library().fmm_fp32_peak(ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
+def fp64_peak(stream=None):
+    """Measured FP64 rate of the current device in TFLOP/s (fmm_fp64_peak)."""
+    v = ctypes.c_double()
+    _check(library().fmm_fp64_peak(ctypes.byref(v), _stream(stream)))
     return v.value
 
 

@@ -24,7 +24,10 @@
 // P2L (X) at levels >= 2; L2L (levels downwards); L2P + M2P (W) per leaf;
 // P2P (U) per leaf, which adds the far field and stores phi at the input
 // index.  Every pass is a plain CUDA-core kernel in FP64: GB300's FP64 rate is
-// the bound (M2L dominates, 4 FP64 FMAs per complex multiply-add).
+// the bound (4 FP64 FMAs per complex multiply-add in the translations; a
+// square root, a division and a sine/cosine pair per near-field pair).  A
+// plan of mixed precision runs the near field in FP32 (the low-accuracy use
+// of §4.2), every expansion still in FP64.
 #include <cmath>
 #include <complex>
 #include <mutex>
@@ -462,6 +465,84 @@ __global__ void __launch_bounds__(kHelmThreads)
   }
 }
 
+// The near field in FP32 (plans of mixed precision): the sources of each U
+// leaf are staged in the target leaf's frame (x_j - c_B, from the FP64 leaf
+// offsets, rounded once), e^{i kappa r}/r is evaluated with sincosf and rsqrt,
+// and each staged batch's FP32 sum is added to an FP64 total.
+__device__ __forceinline__ double center_off(int32_t ia, double sa, int32_t ib, double sb) {
+  return ((double)ia + 0.5) * sa - ((double)ib + 0.5) * sb;
+}
+
+__global__ void __launch_bounds__(kHelmThreads)
+    k_h_p2p32(int64_t nleaves, const int32_t *__restrict__ leaves, const int32_t *__restrict__ uoff,
+              const int32_t *__restrict__ uidx, const int32_t *__restrict__ first,
+              const int32_t *__restrict__ count, const BoxGeo *__restrict__ geo,
+              const double *__restrict__ side, const Dbl4 *__restrict__ pl,
+              const double2 *__restrict__ q, const double2 *__restrict__ far,
+              const int32_t *__restrict__ perm, float kappa, double2 *__restrict__ phi) {
+  __shared__ float4 s_p[kHelmThreads];  // x, y, z, Re q
+  __shared__ float s_qi[kHelmThreads];  // Im q
+  if (blockIdx.x >= nleaves) return;
+  const int32_t b = leaves[blockIdx.x];
+  const int32_t f = first[b], cnt = count[b];
+  const int32_t e0 = uoff[b], e1 = uoff[b + 1];
+  const BoxGeo gb = geo[b];
+  const double sb = side[b];
+  for (int32_t i0 = 0; i0 < cnt; i0 += kHelmThreads) {
+    const int32_t i = i0 + threadIdx.x;
+    float tx = 0.f, ty = 0.f, tz = 0.f;
+    if (i < cnt) {
+      const Dbl4 t = pl[f + i];
+      tx = (float)t.x;
+      ty = (float)t.y;
+      tz = (float)t.z;
+    }
+    double accr = 0.0, acci = 0.0;
+    for (int32_t e = e0; e < e1; ++e) {
+      const int32_t A = uidx[e];
+      const int32_t fa = first[A], ca = count[A];
+      const BoxGeo ga = geo[A];
+      const double sa = side[A];
+      const double ox = center_off(ga.ix, sa, gb.ix, sb), oy = center_off(ga.iy, sa, gb.iy, sb),
+                   oz = center_off(ga.iz, sa, gb.iz, sb);
+      for (int32_t j0 = 0; j0 < ca; j0 += kHelmThreads) {
+        const int nj = min(kHelmThreads, ca - j0);
+        __syncthreads();
+        if (threadIdx.x < nj) {
+          const int32_t j = fa + j0 + threadIdx.x;
+          const Dbl4 v = pl[j];
+          const double2 qj = q[j];
+          s_p[threadIdx.x] = make_float4((float)(v.x + ox), (float)(v.y + oy), (float)(v.z + oz),
+                                         (float)qj.x);
+          s_qi[threadIdx.x] = (float)qj.y;
+        }
+        __syncthreads();
+        if (i < cnt) {
+          float sr = 0.f, si = 0.f;
+          for (int t = 0; t < nj; ++t) {
+            const float4 sp = s_p[t];
+            const float dx = tx - sp.x, dy = ty - sp.y, dz = tz - sp.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 == 0.f) continue;
+            const float ir = rsqrtf(r2);
+            float sn, cs;
+            sincosf(kappa * (r2 * ir), &sn, &cs);
+            const float gr = cs * ir, gi = sn * ir, qi = s_qi[t];
+            sr = fmaf(sp.w, gr, fmaf(-qi, gi, sr));
+            si = fmaf(sp.w, gi, fmaf(qi, gr, si));
+          }
+          accr += (double)sr;
+          acci += (double)si;
+        }
+      }
+    }
+    if (i < cnt) {
+      const double2 fr = far[f + i];
+      phi[perm[f + i]] = make_double2(fr.x + accr, fr.y + acci);
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
@@ -757,9 +838,14 @@ void eval_helmholtz(fmm_plan_impl &P, double kappa, int p, const double *d_q, do
   }
   {
     PassScope ps(P, kPassP2P);
-    k_h_p2p<<<(unsigned)P.nleaves, kHelmThreads, 0, s>>>(
-        P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p, P.xyz_sorted.p,
-        H.q.p, H.far.p, P.perm.p, kappa, phi);
+    if (P.precision == FMM_FP64)
+      k_h_p2p<<<(unsigned)P.nleaves, kHelmThreads, 0, s>>>(
+          P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p, P.xyz_sorted.p,
+          H.q.p, H.far.p, P.perm.p, kappa, phi);
+    else
+      k_h_p2p32<<<(unsigned)P.nleaves, kHelmThreads, 0, s>>>(
+          P.nleaves, P.leaves.p, P.u_off.p, P.u_idx.p, P.box_first.p, P.box_count.p, P.box_geo.p,
+          P.box_side.p, P.pl64.p, H.q.p, H.far.p, P.perm.p, (float)kappa, phi);
     FMM_LAUNCH_CHECK();
   }
 }

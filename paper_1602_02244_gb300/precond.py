@@ -100,15 +100,16 @@ def fpcg(apply_a, b, apply_m=None, tol=1e-8, maxiter=1000):
 
 class HelmholtzGreenPreconditioner:
     """z = Re[h^3 / (4 pi) sum_j r_j e^{i kappa |x_i - x_j|} / |x_i - x_j|] + CELL_SELF h^2 r_i,
-    the sum evaluated by the Helmholtz FMM of ``order`` (plan built once)."""
+    the sum evaluated by the Helmholtz FMM of ``order`` (plan built once;
+    "mixed" runs its near field in FP32)."""
 
-    def __init__(self, h, kappa, order=4, leaf_size=64, device=None):
+    def __init__(self, h, kappa, order=4, leaf_size=64, precision="mixed", device=None):
         self.h = h
         self.kappa = float(kappa)
         self.order = order
         self.points, self.m = grid_points(h, device=device)
         self.plan = binding.Plan(self.points, leaf_size=leaf_size, order=min(order, 8),
-                                 precision="fp64")
+                                 precision=precision)
         self.scale = h ** 3 / (4.0 * math.pi)
         self.self_coef = CELL_SELF * h * h
 

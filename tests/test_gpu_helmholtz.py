@@ -34,8 +34,8 @@ def points(kind, n, seed=0):
     return workloads.lattice(side) * 2.0 - 1.0
 
 
-def gpu_helmholtz(cuda, xyz, q, S, p, kappa=KAPPA):
-    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=S, order=4)
+def gpu_helmholtz(cuda, xyz, q, S, p, kappa=KAPPA, precision="fp64"):
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=S, order=4, precision=precision)
     phi = plan.helmholtz(torch.tensor(q, device=cuda), kappa, p)
     out = phi.cpu().numpy()
     plan.close()
@@ -57,6 +57,16 @@ def test_matches_oracle_fmm(cuda, kind, n, S, p):
         assert len(t.w_idx) > 0 and len(t.x_idx) > 0
     ref = t.helmholtz_eval(p, KAPPA, q)
     assert rel(phi, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("kind,n,S,p", [("cube", 3000, 24, 8), ("plummer", 4000, 12, 6),
+                                         ("lattice", 4096, 64, 4)])
+def test_mixed_near_field_matches_oracle_fmm(cuda, kind, n, S, p):
+    """Mixed plans: the near field in FP32, the rest FP64: within 1e-6."""
+    xyz = points(kind, n)
+    q = charges(n, 4)
+    phi = gpu_helmholtz(cuda, xyz, q, S, p, precision="mixed")
+    assert rel(phi, oracle.Tree(xyz, S).helmholtz_eval(p, KAPPA, q)) <= 1e-6
 
 
 def test_converges_to_the_direct_sum(cuda):
