@@ -152,9 +152,10 @@ fmm_status fmm_eval(fmm_plan_t plan, const double *d_q, double *d_phi, double *d
  * caller's point order, device memory owned by the caller.  kappa > 0 and
  * finite.  The expansions converge when kappa times the side of a level-2
  * box is of order one or less (e.g. kappa = 7 on [-1, 1]^3); the error falls
- * with `order` as for Laplace.  A plan of precision FMM_MIXED evaluates the
- * near field in FP32 (sincos, reciprocal square root; FP64 totals per staged
- * batch: ~1e-7 relative), every expansion and translation still in FP64.
+ * with `order` as for Laplace.  A plan of precision FMM_MIXED evaluates M2L
+ * in FP32 (coefficients scaled per level by powers of min(kappa a, 1), a the
+ * box side) and the near field in FP32 (sincos, reciprocal square root, FP64
+ * totals per staged batch), the other passes in FP64: ~1e-6 relative.
  * The first call for a (kappa, order, tree
  * depth, root cube) builds that set of operators (synchronous); later calls
  * are asynchronous on `stream`.  Errors: FMM_ERR_INVALID_ARG for a NULL plan

@@ -26,8 +26,9 @@
 // index.  Every pass is a plain CUDA-core kernel in FP64: GB300's FP64 rate is
 // the bound (4 FP64 FMAs per complex multiply-add in the translations; a
 // square root, a division and a sine/cosine pair per near-field pair).  A
-// plan of mixed precision runs the near field in FP32 (the low-accuracy use
-// of §4.2), every expansion still in FP64.
+// plan of mixed precision runs M2L (with per-level scalings) and the near
+// field in FP32 (the low-accuracy use of §4.2); P2M, M2M, L2L, P2L, L2P and
+// M2P stay FP64.
 #include <cmath>
 #include <complex>
 #include <mutex>
@@ -465,6 +466,77 @@ __global__ void __launch_bounds__(kHelmThreads)
   }
 }
 
+// M2L in FP32 (plans of mixed precision).  The coefficients of a level of
+// side a are scaled by powers of s = min(kappa a, 1), as the Laplace ones are
+// by powers of a: M^_n = M_n / s^n, L^_n' = L_n' s^{n'+1}, so that the
+// operator T^_{n'n} = T_{n'n} s^{n+n'+1} and both vectors stay well inside the
+// FP32 range at any depth (the unscaled h_l(kappa |t|) overflows it on deep
+// trees).  Coefficients stay FP64 in memory; M is scaled and rounded when it
+// is staged, L is unscaled in FP64 when it is stored.
+__global__ void k_h_m2l_to_f32(int64_t nops, int p, double sc, const double2 *__restrict__ op,
+                               float2 *__restrict__ op32) {
+  const int NC = (p + 1) * (p + 1);
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nops * NC * NC) return;
+  const int kj = (int)(e % ((int64_t)NC * NC)), k = kj / NC, j = kj % NC;
+  const int nk = (int)sqrtf((float)k + 0.5f), nj = (int)sqrtf((float)j + 0.5f);
+  const double f = pow(sc, (double)(nk + nj + 1));
+  const double2 v = op[e];
+  op32[e] = make_float2((float)(v.x * f), (float)(v.y * f));
+}
+
+constexpr int kHelmM2LChunk = 4;  // V sources staged per barrier in the FP32 M2L
+
+__global__ void __launch_bounds__(kHelmMaxNC + 23)
+    k_h_m2l32(int p, int32_t b0, int32_t nbox, const int32_t *__restrict__ voff,
+              const int32_t *__restrict__ vidx, const BoxGeo *__restrict__ geo,
+              const float2 *__restrict__ ops, double sc, const double2 *__restrict__ M,
+              double2 *__restrict__ L) {
+  __shared__ float2 s_in[kHelmM2LChunk][kHelmMaxNC];
+  __shared__ const float2 *s_op[kHelmM2LChunk];
+  const int NC = (p + 1) * (p + 1);
+  if (blockIdx.x >= nbox) return;
+  const int32_t b = b0 + blockIdx.x;
+  const int j = threadIdx.x;
+  const int nj = j < NC ? (int)sqrtf((float)j + 0.5f) : 0;
+  const double in_scale = pow(sc, -(double)nj);
+  const int32_t s0 = voff[b], ns = voff[b + 1] - s0;
+  const BoxGeo gb = geo[b];
+  float2 acc = make_float2(0.f, 0.f);
+  for (int32_t t0 = 0; t0 < ns; t0 += kHelmM2LChunk) {
+    const int nt = min(kHelmM2LChunk, ns - t0);
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+      const int32_t A = vidx[s0 + t0 + t];
+      if (j < NC) {
+        const double2 v = M[(int64_t)A * NC + j];
+        s_in[t][j] = make_float2((float)(v.x * in_scale), (float)(v.y * in_scale));
+      }
+      if (j == 0) {
+        const BoxGeo ga = geo[A];
+        const int code = (gb.ix - ga.ix + 3) * 49 + (gb.iy - ga.iy + 3) * 7 + (gb.iz - ga.iz + 3);
+        s_op[t] = ops + (int64_t)code * NC * NC;
+      }
+    }
+    __syncthreads();
+    if (j < NC)
+      for (int t = 0; t < nt; ++t) {
+        const float2 *tj = s_op[t] + j;
+        const float2 *m = s_in[t];
+#pragma unroll 4
+        for (int k = 0; k < NC; ++k) {
+          const float2 o = tj[(int64_t)k * NC], v = m[k];
+          acc.x = fmaf(o.x, v.x, fmaf(-o.y, v.y, acc.x));
+          acc.y = fmaf(o.x, v.y, fmaf(o.y, v.x, acc.y));
+        }
+      }
+  }
+  if (j < NC) {
+    const double out_scale = pow(sc, -(double)(nj + 1));
+    L[(int64_t)b * NC + j] = make_double2((double)acc.x * out_scale, (double)acc.y * out_scale);
+  }
+}
+
 // The near field in FP32 (plans of mixed precision): the sources of each U
 // leaf are staged in the target leaf's frame (x_j - c_B, from the FP64 leaf
 // offsets, rounded once), e^{i kappa r}/r is evaluated with sincosf and rsqrt,
@@ -685,10 +757,14 @@ void host_wave(int p, double kappa, const double t[3], bool singular, std::vecto
 
 // Operators for (kappa, p) on the plan's levels (rebuilt when kappa, p, the
 // root cube or the depth change).
+// scale of the FP32 M2L coefficients at a level of side a
+static double helm_scale(double kappa, double a) { return std::min(kappa * a, 1.0); }
+
 static void build_helmholtz_operators(fmm_plan_impl &P, double kappa, int p) {
   HelmholtzState &H = P.helm;
   const int nl = P.nlevels;
-  if (H.order == p && H.kappa == kappa && H.D == P.D && H.nlevels == nl) return;
+  const bool f32 = P.precision != FMM_FP64;
+  if (H.order == p && H.kappa == kappa && H.D == P.D && H.nlevels == nl && H.f32 == f32) return;
   cudaStream_t s = P.stream;
   const int NC = (p + 1) * (p + 1), NX = (2 * p + 1) * (2 * p + 1);
   const std::vector<double> G = host_gaunt(p);
@@ -698,6 +774,7 @@ static void build_helmholtz_operators(fmm_plan_impl &P, double kappa, int p) {
   H.m2l.resize((size_t)std::max(nl - 2, 1) * 343 * per, s);
   H.m2m.resize((size_t)std::max(nl, 1) * 8 * per, s);
   H.l2l.resize((size_t)std::max(nl, 1) * 8 * per, s);
+  if (f32) H.m2l32.resize((size_t)std::max(nl - 2, 1) * 343 * per, s);
   std::vector<cd> xt;
   auto assemble = [&](int64_t nops, double2 *dst) {
     H.xtab.resize(xt.size(), s);
@@ -722,6 +799,13 @@ static void build_helmholtz_operators(fmm_plan_impl &P, double kappa, int p) {
         host_wave(p, kappa, t, true, xt);
       }
       assemble(343, H.m2l.p + (size_t)(l - 2) * 343 * per);
+      if (f32) {
+        const int64_t tot = 343 * (int64_t)per;
+        k_h_m2l_to_f32<<<ceil_div(tot, 256), 256, 0, s>>>(343, p, helm_scale(kappa, a),
+                                                          H.m2l.p + (size_t)(l - 2) * 343 * per,
+                                                          H.m2l32.p + (size_t)(l - 2) * 343 * per);
+        FMM_LAUNCH_CHECK();
+      }
     }
     if (l >= 1) {
       // child octant o: child centre - parent centre = (bit - 1/2) a per axis
@@ -742,6 +826,7 @@ static void build_helmholtz_operators(fmm_plan_impl &P, double kappa, int p) {
   H.kappa = kappa;
   H.D = P.D;
   H.nlevels = nl;
+  H.f32 = f32;
 }
 
 void eval_helmholtz(fmm_plan_impl &P, double kappa, int p, const double *d_q, double *d_phi) {
@@ -805,9 +890,14 @@ void eval_helmholtz(fmm_plan_impl &P, double kappa, int p, const double *d_q, do
     for (int l = 2; l < P.nlevels; ++l) {
       const int32_t b0 = P.level_off[l], cnt = P.level_off[l + 1] - b0;
       if (cnt == 0) continue;
-      k_h_translate<1><<<cnt, tpb, 0, s>>>(p, b0, cnt, P.v_off.p, P.v_idx.p, nullptr, nullptr,
-                                           nullptr, P.box_geo.p, H.m2l.p + (size_t)(l - 2) * 343 * per,
-                                           H.M.p, H.L.p);
+      if (H.f32)
+        k_h_m2l32<<<cnt, tpb, 0, s>>>(p, b0, cnt, P.v_off.p, P.v_idx.p, P.box_geo.p,
+                                      H.m2l32.p + (size_t)(l - 2) * 343 * per,
+                                      helm_scale(kappa, box_side(P.D, l)), H.M.p, H.L.p);
+      else
+        k_h_translate<1><<<cnt, tpb, 0, s>>>(p, b0, cnt, P.v_off.p, P.v_idx.p, nullptr, nullptr,
+                                             nullptr, P.box_geo.p, H.m2l.p + (size_t)(l - 2) * 343 * per,
+                                             H.M.p, H.L.p);
       FMM_LAUNCH_CHECK();
     }
   }
@@ -856,6 +946,7 @@ void release_helmholtz(fmm_plan_impl &P) {
   H.m2l.release();
   H.m2m.release();
   H.l2l.release();
+  H.m2l32.release();
   H.xtab.release();
   H.M.release();
   H.L.release();

@@ -46,8 +46,10 @@ struct Operators {
 struct HelmholtzState {
   double kappa = 0.0, D = 0.0;
   int order = -1, nlevels = 0;
+  bool f32 = false;  // mixed plans: the M2L operators also in scaled FP32 (m2l32)
   DBuf<double> gaunt;
   DBuf<double2> m2l, m2m, l2l, xtab;
+  DBuf<float2> m2l32;
   DBuf<double2> M, L, q, far;
 };
 
