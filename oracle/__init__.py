@@ -48,6 +48,7 @@ def _declare(L):
     L.oracle_tree_build.argtypes = [_i64, _D, _int, _int]
     L.oracle_tree_build.restype = ctypes.c_void_p
     L.oracle_tree_free.argtypes = [ctypes.c_void_p]
+    L.oracle_tree_direct_wx.argtypes = [ctypes.c_void_p, _int]
     L.oracle_tree_sizes.argtypes = [ctypes.c_void_p, _I64]
     L.oracle_tree_geometry.argtypes = [ctypes.c_void_p, _D, _D]
     L.oracle_tree_export.argtypes = [ctypes.c_void_p, _U64, _I32, _I32, _U64] + [_I32] * 14
@@ -192,7 +193,9 @@ class Tree:
               "box_count", "box_parent", "box_child", "box_nchild", "u_off", "u_idx",
               "v_off", "v_idx", "w_off", "w_idx", "x_off", "x_idx")
 
-    def __init__(self, xyz, leaf_size, max_depth=21):
+    def __init__(self, xyz, leaf_size, max_depth=21, direct_wx=0):
+        """``direct_wx`` > 0: W pairs of two leaves whose W leaf holds at most
+        that many points go to the near field (oracle_tree_direct_wx)."""
         self.xyz = _f64(xyz).reshape(-1, 3)
         self.leaf_size = leaf_size
         self.max_depth = max_depth
@@ -200,6 +203,8 @@ class Tree:
         if not h:
             raise ValueError("oracle_tree_build rejected its arguments")
         self._h = h
+        if direct_wx > 0:
+            lib().oracle_tree_direct_wx(h, int(direct_wx))
         s = np.zeros(7, np.int64)
         lib().oracle_tree_sizes(h, _p(s, _I64))
         self.n, self.nboxes, self.nlevels = int(s[0]), int(s[1]), int(s[2])

@@ -548,6 +548,40 @@ oracle_tree *oracle_tree_build(int64_t n, const double *xyz, int leaf_size, int 
   return t;
 }
 
+/* Direct evaluation of small well-separated leaf pairs (the adaptive FMM's
+ * practice for W/X interactions whose boxes hold few points): a pair of leaves
+ * (B, A) with A in W(B) and A holding at most max_points points moves, in both
+ * directions, to the near field -- A joins U(B) and B joins U(A), A leaves
+ * W(B) and B leaves X(A) -- so B's targets see A's points by the direct sum
+ * instead of M2P, and A's targets see B's points by the direct sum instead of
+ * P2L + L2P.  The operator stays symmetric.  Rows stay sorted. */
+void oracle_tree_direct_wx(oracle_tree *t, int max_points) {
+  if (!t || max_points < 1) return;
+  for (int64_t b = 0; b < t->nboxes; ++b) {
+    if (t->box_nchild[b] != 0) continue;
+    ivec keep = {0};
+    for (int64_t k = 0; k < t->W[b].n; ++k) {
+      int32_t A = t->W[b].a[k];
+      if (t->box_nchild[A] == 0 && t->box_count[A] <= max_points) {
+        ivec_push(&t->U[b], A);
+        ivec_push(&t->U[A], (int32_t)b);
+        /* remove b from X(A) */
+        ivec *x = &t->X[A];
+        int64_t w = 0;
+        for (int64_t i = 0; i < x->n; ++i)
+          if (x->a[i] != (int32_t)b) x->a[w++] = x->a[i];
+        x->n = w;
+      } else {
+        ivec_push(&keep, A);
+      }
+    }
+    free(t->W[b].a);
+    t->W[b] = keep;
+  }
+  for (int64_t b = 0; b < t->nboxes; ++b)
+    if (t->box_nchild[b] == 0) qsort(t->U[b].a, t->U[b].n, sizeof(int32_t), cmp_i32);
+}
+
 void oracle_tree_free(oracle_tree *t) {
   if (!t) return;
   int64_t nba = t->nboxes ? t->nboxes : 1;

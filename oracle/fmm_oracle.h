@@ -85,6 +85,10 @@ typedef struct oracle_tree oracle_tree;
 oracle_tree *oracle_tree_build(int64_t n, const double *xyz, int leaf_size,
                                int max_depth);
 void oracle_tree_free(oracle_tree *t);
+/* Move every W pair of two leaves (B, A in W(B)) whose W leaf A holds at most
+ * max_points points to the near field in both directions: A joins U(B), B
+ * joins U(A); A leaves W(B), B leaves X(A).  Rows stay sorted. */
+void oracle_tree_direct_wx(oracle_tree *t, int max_points);
 
 /* sizes: [0]=n [1]=nboxes [2]=nlevels [3]=|U| [4]=|V| [5]=|W| [6]=|X| */
 void oracle_tree_sizes(const oracle_tree *t, int64_t sizes[7]);

@@ -105,3 +105,25 @@ def test_adjoint_in_q_is_the_fmm_of_the_weights():
     a, b = 0.37, -1.9
     np.testing.assert_allclose(t.eval(p, a * q + b * w, grad=False), a * phi_q + b * phi_w,
                                rtol=1e-10, atol=1e-12 * np.abs(phi_q).max())
+
+@pytest.mark.parametrize("kind", ["plummer", "sphere"])
+def test_direct_wx_pairs_keep_the_operator_and_do_not_raise_the_error(kind):
+    """W/X pairs of small leaves evaluated directly: the mat-vec stays
+    symmetric and its error against the direct sum is no larger than with
+    M2P / P2L for those pairs (they become exact)."""
+    from paper_1602_02244_gb300 import workloads
+    n = 3000
+    x = workloads.plummer(n, 2) if kind == "plummer" else workloads.sphere_surface(n, 2)
+    q = workloads.rng(3).uniform(-1, 1, n)
+    ref, _ = oracle.direct(x, q)
+    t0 = oracle.Tree(x, 10)
+    t1 = oracle.Tree(x, 10, direct_wx=36)
+    assert len(t1.w_idx) < len(t0.w_idx)
+    for p in (4, 8):
+        e0 = np.linalg.norm(t0.eval(p, q, grad=False) - ref) / np.linalg.norm(ref)
+        e1 = np.linalg.norm(t1.eval(p, q, grad=False) - ref) / np.linalg.norm(ref)
+        assert e1 <= e0 * 1.05, (p, e0, e1)
+    ea = np.zeros(n)
+    eb = np.zeros(n)
+    ea[5], eb[2500] = 1.0, 1.0
+    assert abs(t1.eval(6, eb, grad=False)[5] - t1.eval(6, ea, grad=False)[2500]) < 1e-12

@@ -108,6 +108,21 @@ def brute_lists(t):
     return U, V, W, [sorted(x) for x in X]
 
 
+def direct_wx_lists(t, lists, max_points):
+    """The lists after moving each W pair of two leaves whose W leaf holds at
+    most max_points points to the near field, in both directions."""
+    U, V, W, X = ([list(r) for r in rows] for rows in lists)
+    leaf = t.box_nchild == 0
+    for B in range(t.nboxes):
+        for A in list(W[B]):
+            if leaf[A] and t.box_count[A] <= max_points:
+                W[B].remove(A)
+                X[A].remove(B)
+                U[B].append(A)
+                U[A].append(B)
+    return [sorted(u) for u in U], V, W, X
+
+
 def _inputs(kind, n, seed):
     if kind == "uniform":
         return workloads.uniform_cube(n, seed)
@@ -127,13 +142,31 @@ def test_lists_equal_brute_force(kind, n, S):
             assert list(t.lst(name, b)) == ref[b], (name, b)
 
 
-@pytest.mark.parametrize("kind,n,S", [("uniform", 2000, 12), ("plummer", 2000, 10), ("sphere", 1500, 7)])
-def test_lists_partition_every_pair_exactly_once(kind, n, S):
+@pytest.mark.parametrize("kind,n,S", [("plummer", 500, 6), ("sphere", 400, 5), ("plummer", 300, 1)])
+def test_direct_wx_lists_equal_brute_force(kind, n, S):
+    xyz = _inputs(kind, n, seed=11)
+    t0 = oracle.Tree(xyz, S)
+    for d in (1, 4, 81):
+        t = oracle.Tree(xyz, S, direct_wx=d)
+        ref = direct_wx_lists(t0, brute_lists(t0), d)
+        for name, rows in zip("uvwx", ref):
+            for b in range(t.nboxes):
+                assert list(t.lst(name, b)) == rows[b], (d, name, b)
+
+
+@pytest.mark.parametrize("kind,n,S,direct", [("uniform", 2000, 12, 0), ("plummer", 2000, 10, 0),
+                                             ("sphere", 1500, 7, 0), ("plummer", 2000, 10, 81),
+                                             ("sphere", 1500, 7, 10 ** 6), ("plummer", 3000, 4, 3)])
+def test_lists_partition_every_pair_exactly_once(kind, n, S, direct):
     """Each (leaf B target, source point j) pair is reached exactly once by
     P2P over U(B), M2P over W(B), or M2L over V(C) / P2L over X(C) for C = B
-    or an ancestor of B."""
+    or an ancestor of B -- also after small W/X leaf pairs moved to U, whose
+    rows stay symmetric (A in U(B) iff B in U(A))."""
     xyz = _inputs(kind, n, seed=5)
-    t = oracle.Tree(xyz, S)
+    t = oracle.Tree(xyz, S, direct_wx=direct)
+    for B in np.nonzero(t.box_nchild == 0)[0]:
+        for A in t.lst("u", B):
+            assert B in t.lst("u", A)
     first, cnt = t.box_first, t.box_count
     for B in np.nonzero(t.box_nchild == 0)[0]:
         hit = np.zeros(n, np.int32)
