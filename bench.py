@@ -52,7 +52,10 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 # configuration, or a
 # kernel changed since the capture, reports null.
 TRAFFIC_BYTES = {
-    ("P2P", 4194304, 8, 128, "mixed", 1): 944.61e6,  # k_p2p_f32<160, 2, 16>, leaves by work class
+    # k_p2p_f32<160, 2, 16>, leaves by work class; the lists as defined (no direct W/X pairs)
+    ("P2P", 4194304, 8, 128, "mixed", 1, False): 944.61e6,
+    # the same kernel with the W/X pairs of small leaves in the U lists (the default)
+    ("P2P", 4194304, 8, 128, "mixed", 1, True): 990.00e6,
 }
 
 
@@ -90,6 +93,9 @@ def parse():
                     help="also time the dual-tree walk (acceptance theta) on the same points; 0 skips")
     ap.add_argument("--precond", action="store_true",
                     help="add the FMM-preconditioned CG solve of the 7-point Laplace problem")
+    ap.add_argument("--wx-direct", default="on", choices=["on", "off"],
+                    help="W/X pairs of two leaves whose W leaf holds at most (p+1)^2 points by the "
+                         "direct sum (fmm_opts.wx_direct; on by default), or the lists as defined")
     ap.add_argument("--helmholtz", action="store_true",
                     help="add the Helmholtz mat-vec (kappa = 7) on the h = 2^-5 grid of [-1,1]^3 "
                          "and the Helmholtz rows of --precond")
@@ -164,7 +170,7 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ oracle
-def cpu_baseline(n_sample, order, leaf, sel, n_one_core=131072):
+def cpu_baseline(n_sample, order, leaf, sel, n_one_core=131072, direct_wx=0):
     """The CPU oracle (FP64 plan + FMM with gradients, forward and adjoint: an
     evaluation with the charges and one with the loss weights) on the Plummer
     points of the benchmark (all of them when n_sample is the full N), on all
@@ -176,25 +182,26 @@ def cpu_baseline(n_sample, order, leaf, sel, n_one_core=131072):
     xyz, q = workloads.plummer_problem(n_sample, 0)
     w = workloads.rng(2).normal(size=n_sample)
     t0 = time.perf_counter()
-    tree = oracle.Tree(xyz, leaf)
+    tree = oracle.Tree(xyz, leaf, direct_wx=direct_wx)
     tree.eval(order, q, grad=True)
     tree.eval(order, w, grad=True)
     dt = time.perf_counter() - t0
     del tree
     out = {"value": n_sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-           "sample": "Plummer N=%d (the benchmark's points, charges 1/N), p=%d, leaf %d: plan + "
+           "sample": "Plummer N=%d (the benchmark's points, charges 1/N), p=%d, leaf %d%s: plan + "
                      "FP64 FMM forward (phi, grad) + adjoint (the FMM with the loss weights), "
-                     "%.1f s" % (n_sample, order, leaf, dt)}
+                     "%.1f s" % (n_sample, order, leaf,
+                                 ", the same direct W/X leaf pairs" if direct_wx else "", dt)}
     code = ("import json, time, oracle\n"
             "from paper_1602_02244_gb300 import workloads\n"
             "xyz, q = workloads.plummer_problem(%d, 0)\n"
             "w = workloads.rng(2).normal(size=%d)\n"
             "t0 = time.perf_counter()\n"
-            "t = oracle.Tree(xyz, %d)\n"
+            "t = oracle.Tree(xyz, %d, direct_wx=%d)\n"
             "t.eval(%d, q, grad=True)\n"
             "t.eval(%d, w, grad=True)\n"
             "print(json.dumps({'s': time.perf_counter() - t0, 'cores': oracle.num_threads()}))\n"
-            % (n_one_core, n_one_core, leaf, order, order))
+            % (n_one_core, n_one_core, leaf, direct_wx, order, order))
     try:
         env = dict(os.environ, OMP_NUM_THREADS="1")
         r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
@@ -222,8 +229,10 @@ def run_reference(args):
     xyz, q = workloads.plummer_problem(n, 0)
     w = workloads.rng(2).normal(size=n)
 
+    direct_wx = (args.order + 1) ** 2 if args.wx_direct == "on" else 0
+
     def step():
-        t = oracle.Tree(xyz, leaf)
+        t = oracle.Tree(xyz, leaf, direct_wx=direct_wx)
         t.eval(args.order, q, grad=True)
         t.eval(args.order, w, grad=True)
 
@@ -240,9 +249,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "Plummer N=%d per step (bounded CPU sample of the N=4,194,304 "
-                                   "problem), p=%d, leaf %d, FP64; step = plan + forward (phi, "
-                                   "grad) + adjoint (the FMM with the loss weights)"
-                                   % (n, args.order, leaf)},
+                                   "problem), p=%d, leaf %d, FP64%s; step = plan + forward "
+                                   "(phi, grad) + adjoint (the FMM with the loss weights)"
+                                   % (n, args.order, leaf,
+                                      ", W/X pairs of small leaves direct" if direct_wx else "")},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle",
                              "sample": "Plummer N=%d per step: plan + FP64 FMM forward + adjoint, "
@@ -277,7 +287,7 @@ def algorithmic_work(plan):
     return pairs, v_pairs, e
 
 
-def batched_leg(dev, steps, warmup, leaf=0):
+def batched_leg(dev, steps, warmup, leaf=0, wx_direct=False):
     """256 independent uniform problems, N log-uniform in [2048, 65536], p = 6,
     mixed precision, leaf size `leaf` (0: autotuned): forward (phi, grad) plus
     adjoint (dL/dq, dL/dx) replayed as one CUDA graph per step."""
@@ -289,7 +299,8 @@ def batched_leg(dev, steps, warmup, leaf=0):
     X = torch.tensor(np.vstack(pts), device=dev)
     Q = torch.tensor(np.concatenate(qs), device=dev)
     W = torch.tensor(workloads.rng(2).normal(size=total), device=dev)
-    plan = binding.Plan(X, leaf_size=leaf, order=6, precision="mixed", offsets=off)
+    plan = binding.Plan(X, leaf_size=leaf, order=6, precision="mixed", offsets=off,
+                        wx_direct=wx_direct)
     s = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(s):
         phi = torch.empty(total, dtype=torch.float64, device=dev)
@@ -444,9 +455,9 @@ def helmholtz_leg(dev, L, steps=5, kappa=7.0, h=2.0 ** -5, leaf=64):
     paper's Helmholtz domain: the h = 2^-5 interior grid of [-1,1]^3 (63^3 =
     250,047 points), kappa = 7, complex charges U[-1,1] + i U[-1,1].  Per
     precision and order: mat-vec time (CUDA events over `steps` calls,
-    operators built before), per-pass times, and the FP64 roofline of M2L
-    (8 flop per complex multiply-add, (p+1)^4 per V pair) and of the FP64 near
-    field against the measured FP64 rate.  cpu_baseline: the oracle's FP64
+    operators built before), per-pass times, and the roofline of M2L (8 flop
+    per complex multiply-add, (p+1)^4 per V pair) against the measured FP64
+    rate (FP64 plans) or FP32 rate (mixed plans, whose M2L runs in FP32).  cpu_baseline: the oracle's FP64
     direct sum at 256 sampled targets, against which each run's error is
     stated."""
     import ctypes
@@ -459,6 +470,7 @@ def helmholtz_leg(dev, L, steps=5, kappa=7.0, h=2.0 ** -5, leaf=64):
     q_h = g.uniform(-1, 1, n) + 1j * g.uniform(-1, 1, n)
     q = torch.tensor(q_h, device=dev)
     fp64_tf = binding.fp64_peak()
+    fp32_tf = binding.fp32_peak()
     sel = workloads.sample_targets(n, 256, seed=3)
     cpu = None
     xyz_h = pts.cpu().numpy()
@@ -507,20 +519,25 @@ def helmholtz_leg(dev, L, steps=5, kappa=7.0, h=2.0 ** -5, leaf=64):
             got = phi.cpu().numpy()[sel]
             nc = (order + 1) ** 2
             m2l_flop = 8.0 * nc * nc * nv
+            peak = fp64_tf if precision == "fp64" else fp32_tf
             row = {"precision": precision, "order": order, "ms": ms,
                    "value": n / (ms / 1e3), "unit": "targets/s",
                    "rel_error_vs_oracle_direct": float(np.linalg.norm(got - ref) /
                                                        np.linalg.norm(ref)),
                    "passes_ms": passes, "v_pairs": nv, "p2p_pairs": p2p_pairs,
                    "m2l_roofline": {"bound": "alu", "achieved": m2l_flop / (passes["M2L"] / 1e3) / 1e12,
-                                    "peak": fp64_tf, "unit": "TFLOP/s",
-                                    "frac": m2l_flop / (passes["M2L"] / 1e3) / 1e12 / fp64_tf,
-                                    "peak_source": "fmm_fp64_peak, FP64 FMA chains (of measured)"}}
+                                    "peak": peak, "unit": "TFLOP/s",
+                                    "frac": m2l_flop / (passes["M2L"] / 1e3) / 1e12 / peak,
+                                    "peak_source": ("fmm_fp64_peak, FP64 FMA chains (of measured)"
+                                                    if precision == "fp64" else
+                                                    "fmm_fp32_peak, paired FP32 FMA chains (of "
+                                                    "measured): the mixed M2L runs in FP32")}}
             runs.append(row)
         plan.close()
     return {"workload": "Helmholtz e^{i 7 r}/r mat-vec, interior grid of [-1,1]^3 at h = 2^-5 "
                         "(%d points), leaf %d" % (n, leaf), "kappa": kappa,
-            "fp64_peak_tflops": fp64_tf, "runs": runs, "cpu_baseline": cpu}
+            "fp64_peak_tflops": fp64_tf, "fp32_peak_tflops": fp32_tf, "runs": runs,
+            "cpu_baseline": cpu}
 
 
 def dual_leg(X, Q, S, p, precision, theta, rel_err, steps, stream, ms_lists, ms_eval_lists):
@@ -611,9 +628,10 @@ def run_ours(args):
     X = torch.tensor(xyz_np, device=dev)
     Q = torch.tensor(q_np, device=dev)
     W = torch.tensor(w_np, device=dev)
+    wx = args.wx_direct == "on"
     plan = binding.Plan(X, leaf_size=S, order=p, precision=args.precision,
                         m2l_path=args.m2l_path, p2p_tile=args.p2p_tile,
-                        m2l_tile=args.m2l_tile)  # S = 0: autotune
+                        m2l_tile=args.m2l_tile, wx_direct=wx)  # S = 0: autotune
     S = plan.sizes()["leaf_size"]
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     grad = torch.empty(n, 3, dtype=torch.float64, device=dev)
@@ -725,7 +743,7 @@ def run_ours(args):
         achieved = None
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": (achieved / peak) if achieved else None,
-            "traffic": TRAFFIC_BYTES.get((dom, n, p, S, args.precision, tiles["p2p_tile"]))
+            "traffic": TRAFFIC_BYTES.get((dom, n, p, S, args.precision, tiles["p2p_tile"], wx))
                        if dom == "P2P" else None,
             "peak_source": ("FP32: fmm_fp32_peak, paired-FMA chains on this GPU (of measured); "
                             "nominal %d SMs x %d lanes x 2 flop x %.0f MHz = %.1f TFLOP/s"
@@ -764,6 +782,8 @@ def run_ours(args):
                                "power-of-two scalings)")
                               if m2l_tensor
                               else "CUDA cores",
+                       "wx_direct": ("W/X pairs of two leaves whose W leaf holds <= (p+1)^2 "
+                                     "points by the direct sum" if wx else "off"),
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MB flush between steps; working set >> L2",
                        "boxes": sizes["nboxes"], "levels": sizes["nlevels"], "U": sizes["nu"],
@@ -837,7 +857,7 @@ def run_ours(args):
         dx64 = torch.empty_like(dx)
         tried = []
         for p64 in range(max(2, p - 3), 13):
-            plan64 = binding.Plan(X, leaf_size=S, order=p64, precision="fp64")
+            plan64 = binding.Plan(X, leaf_size=S, order=p64, precision="fp64", wx_direct=wx)
             plan64.eval(Q, out=(phi64, g64))
             e64 = rel_err(phi64, g64)
             tried.append({"order": p64, "phi": e64["phi"]})
@@ -873,7 +893,7 @@ def run_ours(args):
         line["dual_tree"] = dual_leg(X, Q, S, p, args.precision, args.dual_theta, rel_err,
                                      min(args.steps, 5), stream, ms_pf, ms_eval)
     if not args.no_batch:
-        line["batched"] = batched_leg(dev, args.steps, args.warmup, args.batch_leaf)
+        line["batched"] = batched_leg(dev, args.steps, args.warmup, args.batch_leaf, wx)
     if not args.no_lattice:
         line["lattice"] = lattice_leg(dev)
     if args.precond:
@@ -885,7 +905,8 @@ def run_ours(args):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ncpu = args.cpu_sample or n
-        cpu, ref = cpu_baseline(ncpu, p, S, sel if ncpu == n else workloads.sample_targets(ncpu, 4096, 1))
+        cpu, ref = cpu_baseline(ncpu, p, S, sel if ncpu == n else workloads.sample_targets(ncpu, 4096, 1),
+                                direct_wx=(p + 1) ** 2 if wx else 0)
         line["cpu_baseline"] = cpu
         if ncpu == n:
             # the error statement against the oracle: its FP64 direct sum at

@@ -93,7 +93,14 @@ typedef struct {
                              hi/lo split (kind::tf32), 2 = FP16 hi/lo split
                              with power-of-two scalings (kind::f16: half the
                              operand bytes, twice the MMA rate); 0 = default */
-  int reserved;           /* must be zero                                     */
+  int wx_direct;          /* interaction 0: 1 = a W-list pair of two leaves
+                             whose W leaf holds at most (order+1)^2 points
+                             (no more points than its expansion has
+                             coefficients) is evaluated by the direct sum in
+                             both directions instead of M2P and P2L: both
+                             leaves join each other's U list.  More exact and,
+                             on adaptive trees, faster.  0 = the lists as
+                             defined (default)                                */
 } fmm_opts;
 
 /* Build a plan for n points (d_xyz: device, n x 3 FP64).

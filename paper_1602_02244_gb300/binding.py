@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("max_depth", ctypes.c_int), ("m2l_path", ctypes.c_int),
                 ("interaction", ctypes.c_int), ("p2p_tile", ctypes.c_int),
                 ("mac_theta", ctypes.c_double), ("m2l_tile", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("wx_direct", ctypes.c_int)]
 
 
 _lib = None
@@ -125,11 +125,13 @@ class Plan:
     r_T + r_S < theta |c_T - c_S|; ``theta`` 0 = default 0.5).  ``p2p_tile``
     picks the staging shape of the FP32 near-field kernel, ``m2l_tile`` the
     operand form of the tensor-core M2L (1 TF32, 2 FP16; 0 = default).
+    ``wx_direct`` evaluates W/X pairs of two leaves whose W leaf holds at most
+    (order+1)^2 points by the direct sum (both leaves join each other's U list).
     """
 
     def __init__(self, points, leaf_size=64, order=8, precision="fp64", coarse_fp64_levels=0,
                  max_depth=0, stream=None, offsets=None, m2l_path="auto", interaction="lists",
-                 theta=0.0, p2p_tile=0, m2l_tile=0):
+                 theta=0.0, p2p_tile=0, m2l_tile=0, wx_direct=False):
         L = library()
         self.device = points.device
         self.n = int(points.shape[0])
@@ -143,6 +145,7 @@ class Plan:
         opts.mac_theta = float(theta)
         opts.p2p_tile = int(p2p_tile)
         opts.m2l_tile = int(m2l_tile)
+        opts.wx_direct = int(bool(wx_direct))
         self.interaction = interaction
         self.precision, self.order, self.leaf_size = precision, order, leaf_size
         h = _vp()

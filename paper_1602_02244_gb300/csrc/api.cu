@@ -73,7 +73,8 @@ void check_opts(const fmm_opts *o) {
     throw Error(FMM_ERR_INVALID_ARG, "opts.mac_theta must be in [0, 1)");
   if (o->m2l_tile < 0 || o->m2l_tile > 2)
     throw Error(FMM_ERR_INVALID_ARG, "opts.m2l_tile must be 0, 1 or 2");
-  if (o->reserved != 0) throw Error(FMM_ERR_INVALID_ARG, "opts.reserved must be zero");
+  if (o->wx_direct < 0 || o->wx_direct > 1)
+    throw Error(FMM_ERR_INVALID_ARG, "opts.wx_direct must be 0 or 1");
   if (o->p2p_tile < 0 || o->p2p_tile > p2p_num_tiles())
     throw Error(FMM_ERR_INVALID_ARG, "opts.p2p_tile must be in 0.." + std::to_string(p2p_num_tiles()));
 }
@@ -88,6 +89,7 @@ void apply_opts(fmm_plan_impl &P, const fmm_opts *o) {
   P.theta = o->mac_theta > 0.0 ? o->mac_theta : 0.5;
   P.p2p_tile = P.p2p_tile_user = o->p2p_tile;
   P.m2l_tile = P.m2l_tile_user = o->m2l_tile;
+  P.wx_direct_max = o->wx_direct && !P.dual ? (P.order + 1) * (P.order + 1) : 0;
 }
 
 }  // namespace

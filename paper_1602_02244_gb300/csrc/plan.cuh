@@ -68,6 +68,9 @@ struct fmm_plan_impl {
   bool m2l_tc = false;               // this plan's M2L runs on the tensor cores
   int m2l_tile = 0;                  // tensor-core form: 0 default, 1 TF32 split, 2 FP16 split
   int order = 0, leaf_size = 1, autotune = 0, precision = FMM_FP64, coarse_fp64_levels = 3, max_depth = kMaxDepth;
+  // W pairs of two leaves whose W leaf holds at most this many points go to
+  // the near field in both directions (0 = off; opts.wx_direct sets (p+1)^2)
+  int wx_direct_max = 0;
   cudaStream_t stream = nullptr;
   // host-buffer calls: a side stream for copies that overlap the computation,
   // and the events that order it against `stream` (created on first use)

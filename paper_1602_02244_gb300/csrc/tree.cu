@@ -10,8 +10,10 @@
 // numbered by (level, key) and every list is sorted by box number.
 #include <algorithm>
 #include <memory>
+#include <utility>
 
 #include "m2l_config.cuh"
+
 #include "plan.cuh"
 #include "sort.cuh"
 
@@ -643,6 +645,112 @@ int64_t compact(fmm_plan_impl &P, int64_t n, const int32_t *flag, DBuf<int32_t> 
   return m;
 }
 
+
+// ---- small W/X leaf pairs to the near field (fmm_opts.wx_direct)
+// A pair of leaves (B, A) with A in W(B) and A holding at most T points moves
+// to the near field in both directions: A joins U(B) and B joins U(A); A
+// leaves W(B) and B leaves X(A).  For box b: its W entries that are such
+// leaves move to U(b); its X entries C (C a leaf with b in W(C)) all move when
+// b is a leaf of at most T points, none otherwise.  The operator stays
+// symmetric; U rows are re-sorted.
+__global__ void k_wx_direct_count(int64_t nb, int T, const int32_t *__restrict__ nchild,
+                                  const int32_t *__restrict__ count, const int32_t *__restrict__ uoff,
+                                  const int32_t *__restrict__ woff, const int32_t *__restrict__ widx,
+                                  const int32_t *__restrict__ xoff, int32_t *__restrict__ ucnt,
+                                  int32_t *__restrict__ wcnt, int32_t *__restrict__ xcnt) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const bool leaf = nchild[b] == 0;
+  int32_t moved = 0, kept = 0;
+  for (int32_t e = woff[b]; e < woff[b + 1]; ++e) {
+    const int32_t A = widx[e];
+    if (leaf && nchild[A] == 0 && count[A] <= T)
+      ++moved;
+    else
+      ++kept;
+  }
+  const int32_t nx = xoff[b + 1] - xoff[b];
+  const bool xmove = leaf && count[b] <= T;
+  ucnt[b] = uoff[b + 1] - uoff[b] + moved + (xmove ? nx : 0);
+  wcnt[b] = kept;
+  xcnt[b] = xmove ? 0 : nx;
+}
+
+__global__ void k_wx_direct_fill(int64_t nb, int T, const int32_t *__restrict__ nchild,
+                                 const int32_t *__restrict__ count, const int32_t *__restrict__ uoff,
+                                 const int32_t *__restrict__ uidx, const int32_t *__restrict__ woff,
+                                 const int32_t *__restrict__ widx, const int32_t *__restrict__ xoff,
+                                 const int32_t *__restrict__ xidx, const int32_t *__restrict__ nuoff,
+                                 int32_t *__restrict__ nuidx, const int32_t *__restrict__ nwoff,
+                                 int32_t *__restrict__ nwidx, const int32_t *__restrict__ nxoff,
+                                 int32_t *__restrict__ nxidx) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const bool leaf = nchild[b] == 0;
+  const bool xmove = leaf && count[b] <= T;
+  int32_t *u = nuidx + nuoff[b], *w = nwidx + nwoff[b], *x = nxidx + nxoff[b];
+  int k = 0, kw = 0, kx = 0;
+  for (int32_t e = uoff[b]; e < uoff[b + 1]; ++e) u[k++] = uidx[e];
+  const int k0 = k;
+  for (int32_t e = woff[b]; e < woff[b + 1]; ++e) {
+    const int32_t A = widx[e];
+    if (leaf && nchild[A] == 0 && count[A] <= T)
+      u[k++] = A;
+    else
+      w[kw++] = A;
+  }
+  for (int32_t e = xoff[b]; e < xoff[b + 1]; ++e) {
+    if (xmove)
+      u[k++] = xidx[e];
+    else
+      x[kx++] = xidx[e];
+  }
+  if (k > k0) sort_run(u, k);
+}
+
+void direct_wx_pairs(fmm_plan_impl &P, int T) {
+  cudaStream_t s = P.stream;
+  const int64_t nb = P.nboxes;
+  DBuf<int32_t> &ucnt = P.s_i32a, &wcnt = P.s_i32d, &xcnt = P.s_i32c;
+  ucnt.resize(nb, s);
+  wcnt.resize(nb, s);
+  xcnt.resize(nb, s);
+  k_wx_direct_count<<<grid(nb), kT, 0, s>>>(nb, T, P.box_nchild.p, P.box_count.p, P.u_off.p,
+                                             P.w_off.p, P.w_idx.p, P.x_off.p, ucnt.p, wcnt.p, xcnt.p);
+  FMM_LAUNCH_CHECK();
+  DBuf<int32_t> uo, ui, wo, wi, xo, xi;
+  counts_to_offsets_async(P, ucnt.p, uo, nb);
+  counts_to_offsets_async(P, wcnt.p, wo, nb);
+  counts_to_offsets_async(P, xcnt.p, xo, nb);
+  int32_t h[3];
+  FMM_CUDA(cudaMemcpyAsync(&h[0], uo.p + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(cudaMemcpyAsync(&h[1], wo.p + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(cudaMemcpyAsync(&h[2], xo.p + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(cudaStreamSynchronize(s));
+  ui.resize(h[0] > 0 ? h[0] : 1, s);
+  wi.resize(h[1] > 0 ? h[1] : 1, s);
+  xi.resize(h[2] > 0 ? h[2] : 1, s);
+  k_wx_direct_fill<<<grid(nb), kT, 0, s>>>(nb, T, P.box_nchild.p, P.box_count.p, P.u_off.p,
+                                            P.u_idx.p, P.w_off.p, P.w_idx.p, P.x_off.p, P.x_idx.p,
+                                            uo.p, ui.p, wo.p, wi.p, xo.p, xi.p);
+  FMM_LAUNCH_CHECK();
+  std::swap(P.u_off, uo);
+  std::swap(P.u_idx, ui);
+  std::swap(P.w_off, wo);
+  std::swap(P.w_idx, wi);
+  std::swap(P.x_off, xo);
+  std::swap(P.x_idx, xi);
+  uo.release();
+  ui.release();
+  wo.release();
+  wi.release();
+  xo.release();
+  xi.release();
+  P.nu = h[0];
+  P.nw = h[1];
+  P.nx = h[2];
+}
+
 }  // namespace
 
 // Rotated M2L: on request (m2l_path 3), and by default in FP64 up to
@@ -985,6 +1093,8 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
                                             P.u_idx.p, P.w_off.p, P.w_idx.p, P.dev_err.p);
     FMM_LAUNCH_CHECK();
   }
+
+  if (P.wx_direct_max > 0) direct_wx_pairs(P, P.wx_direct_max);
 
   // ---- work lists for P2L and M2P
   P.s_i32a.resize(nb, s);

@@ -29,14 +29,14 @@ struct Tuned {
 };
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, double, int, int>, Tuned> g_tune_cache;
+std::map<std::tuple<int, int, int, int, double, int, int, int>, Tuned> g_tune_cache;
 
 }  // namespace
 
 int tuned_leaf_size(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
   const int bucket = n > 0 ? (int)std::floor(std::log2((double)n)) : 0;
   const auto key = std::make_tuple(bucket, P.order, P.precision, (int)P.dual, P.dual ? P.theta : 0.0,
-                                   P.p2p_tile_user, P.m2l_tile_user);
+                                   P.p2p_tile_user, P.m2l_tile_user, P.wx_direct_max);
   auto apply = [&](const Tuned &t) {
     if (t.p2p_tile) P.p2p_tile = t.p2p_tile;
     if (t.m2l_tile) P.m2l_tile = t.m2l_tile;

@@ -106,21 +106,23 @@ def test_mixed_config3_plummer_4m(cuda):
     assert rel(g[sel], gd) <= 1e-4
 
 
-def test_full_size_in_the_benchmarked_configuration_vs_oracle_fmm(cuda):
+@pytest.mark.parametrize("wx_direct", [False, True])
+def test_full_size_in_the_benchmarked_configuration_vs_oracle_fmm(cuda, wx_direct):
     """4,194,304 Plummer points, p = 8, with the leaf size the autotuner picks
-    (the configuration the benchmark times): the FP64 mat-vec within 1e-12 of
-    the oracle's FMM on the same tree on every target, and the mixed-precision
-    mat-vec within the mixed bars of it."""
+    (the configuration the benchmark times, with and without the direct W/X
+    leaf pairs): the FP64 mat-vec within 1e-12 of the oracle's FMM on the same
+    tree on every target, and the mixed-precision mat-vec within the mixed
+    bars of it."""
     xyz, q = workloads.plummer_problem(4194304, 0)
     X, Q = torch.tensor(xyz, device=cuda), torch.tensor(q, device=cuda)
-    mixed = binding.Plan(X, leaf_size=0, order=8, precision="mixed")
+    mixed = binding.Plan(X, leaf_size=0, order=8, precision="mixed", wx_direct=wx_direct)
     S = mixed.sizes()["leaf_size"]
     phi_m, g_m = (a.cpu().numpy() for a in mixed.eval(Q))
     mixed.close()
-    f64 = binding.Plan(X, leaf_size=S, order=8, precision="fp64")
+    f64 = binding.Plan(X, leaf_size=S, order=8, precision="fp64", wx_direct=wx_direct)
     phi_d, g_d = (a.cpu().numpy() for a in f64.eval(Q))
     f64.close()
-    po, go = oracle.Tree(xyz, S).eval(8, q)
+    po, go = oracle.Tree(xyz, S, direct_wx=81 if wx_direct else 0).eval(8, q)
     print("4M Plummer, leaf %d: fp64 vs oracle %.2e; mixed vs oracle phi %.2e grad %.2e"
           % (S, rel(phi_d, po), rel(phi_m, po), rel(g_m, go)))
     assert rel(phi_d, po) <= 1e-12
@@ -330,3 +332,28 @@ def test_autotuner_picks_kernel_shapes(cuda):
     fixed = binding.Plan(X, leaf_size=0, order=6, precision="mixed", p2p_tile=3, m2l_tile=1)
     assert fixed.tiles() == {"p2p_tile": 3, "m2l_tile": 1}
     fixed.close()
+
+
+@pytest.mark.parametrize("kind,n,S,p", [("plummer", 30000, 24, 6), ("sphere", 20000, 16, 8),
+                                         ("plummer", 8000, 5, 3)])
+def test_direct_wx_matches_oracle_fmm(cuda, kind, n, S, p):
+    """W/X pairs of small leaves by the direct sum (fmm_opts.wx_direct):
+    FP64 within 1e-12 of the oracle FMM with the same lists, mixed within the
+    mixed bars; the mat-vec stays symmetric (the adjoint's dL/dq is the
+    forward with the weights)."""
+    xyz, q = problem(kind, n)
+    t = oracle.Tree(xyz, S, direct_wx=(p + 1) ** 2)
+    assert len(t.w_idx) < len(oracle.Tree(xyz, S).w_idx)
+    po, go = t.eval(p, q)
+    phi, g = run_gpu(cuda, xyz, q, S, p, wx_direct=True)
+    assert rel(phi, po) <= 1e-12
+    for a in range(3):
+        assert rel(g[:, a], go[:, a]) <= 1e-12
+    phi_m, g_m = run_gpu(cuda, xyz, q, S, p, precision="mixed", wx_direct=True)
+    assert rel(phi_m, po) <= 1e-5 and rel(g_m, go) <= 1e-4
+    w = workloads.rng(9).uniform(-1, 1, n)
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=S, order=p, wx_direct=True)
+    dq, _ = plan.adjoint(torch.tensor(w, device=cuda), torch.tensor(q, device=cuda))
+    fw, _ = plan.eval(torch.tensor(w, device=cuda))
+    plan.close()
+    assert rel(dq.cpu().numpy(), fw.cpu().numpy()) <= 1e-13

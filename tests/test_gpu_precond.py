@@ -64,7 +64,8 @@ def test_helmholtz7_matches_sparse_operator(cuda, m):
 
 def test_helmholtz_fmm_preconditioned_gmres_matches_direct_solve(cuda):
     """-Laplace u - 49 u = 1 on [-1, 1]^3 (indefinite), h = 2^-3 against a
-    sparse direct solve, and at h = 2^-4 in fewer iterations than plain GMRES."""
+    sparse direct solve, and at h = 2^-4 in fewer iterations than plain GMRES
+    (on the 15^3 grid the two take a similar number: 50-80 against 59)."""
     import scipy.sparse as sp
     from scipy.sparse.linalg import spsolve
     for h in (2.0 ** -3, 2.0 ** -4):
@@ -77,7 +78,9 @@ def test_helmholtz_fmm_preconditioned_gmres_matches_direct_solve(cuda):
         pre.close()
         print("h=%g: FMM-preconditioned GMRES %d iterations, plain GMRES(50) %d (residual %.1e)"
               % (h, it, it0, hist0[-1]))
-        assert hist[-1] <= 1e-10 and it < it0
+        assert hist[-1] <= 1e-10
+        if h == 2.0 ** -4:
+            assert it < it0 / 4
         if h == 2.0 ** -3:
             K = (laplacian_csr(m, h) - KAPPA ** 2 * sp.identity(m ** 3)).tocsc()
             ref = spsolve(K, np.ones(m ** 3))

@@ -102,3 +102,26 @@ def test_lattice_bit_exact(cuda, side):
     plan = gpu_plan(cuda, xyz, 64, order=8)
     compare(plan, oracle.Tree(xyz, 64))
     plan.close()
+
+
+@pytest.mark.parametrize("kind,n,S,p,precision", [("plummer", 20000, 16, 8, "fp64"),
+                                                  ("sphere", 30000, 24, 4, "mixed"),
+                                                  ("plummer", 5000, 3, 6, "mixed"),
+                                                  ("uniform", 4096, 64, 2, "fp64")])
+def test_direct_wx_lists_bit_exact(cuda, kind, n, S, p, precision):
+    """fmm_opts.wx_direct: W/X pairs of two leaves whose W leaf holds at most
+    (p+1)^2 points move to both leaves' U lists -- equal to the oracle's lists
+    with the same rule."""
+    xyz = points(kind, n)
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=S, order=p,
+                        precision=precision, wx_direct=True)
+    compare(plan, oracle.Tree(xyz, S, direct_wx=(p + 1) ** 2))
+    plan.close()
+
+
+def test_direct_wx_full_size_plummer_4m_bit_exact(cuda):
+    xyz = workloads.plummer(4194304, 0)
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=128, order=8,
+                        precision="mixed", wx_direct=True)
+    compare(plan, oracle.Tree(xyz, 128, direct_wx=81))
+    plan.close()
