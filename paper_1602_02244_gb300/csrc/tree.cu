@@ -676,6 +676,9 @@ __global__ void k_wx_direct_count(int64_t nb, int T, const int32_t *__restrict__
   xcnt[b] = xmove ? 0 : nx;
 }
 
+// The new U row of b merges three rows that are already sorted: its U row,
+// the W entries that move and (when they all move) its X row; the lists are
+// disjoint, so the merge never meets a box twice.
 __global__ void k_wx_direct_fill(int64_t nb, int T, const int32_t *__restrict__ nchild,
                                  const int32_t *__restrict__ count, const int32_t *__restrict__ uoff,
                                  const int32_t *__restrict__ uidx, const int32_t *__restrict__ woff,
@@ -688,24 +691,32 @@ __global__ void k_wx_direct_fill(int64_t nb, int T, const int32_t *__restrict__ 
   if (b >= nb) return;
   const bool leaf = nchild[b] == 0;
   const bool xmove = leaf && count[b] <= T;
+  auto moves = [&](int32_t A) { return leaf && nchild[A] == 0 && count[A] <= T; };
   int32_t *u = nuidx + nuoff[b], *w = nwidx + nwoff[b], *x = nxidx + nxoff[b];
-  int k = 0, kw = 0, kx = 0;
-  for (int32_t e = uoff[b]; e < uoff[b + 1]; ++e) u[k++] = uidx[e];
-  const int k0 = k;
-  for (int32_t e = woff[b]; e < woff[b + 1]; ++e) {
-    const int32_t A = widx[e];
-    if (leaf && nchild[A] == 0 && count[A] <= T)
-      u[k++] = A;
-    else
-      w[kw++] = A;
+  int32_t kw = 0, kx = 0;
+  for (int32_t e = woff[b]; e < woff[b + 1]; ++e)
+    if (!moves(widx[e])) w[kw++] = widx[e];
+  if (!xmove)
+    for (int32_t e = xoff[b]; e < xoff[b + 1]; ++e) x[kx++] = xidx[e];
+  int32_t iu = uoff[b], iw = woff[b], ix = xoff[b];
+  const int32_t eu = uoff[b + 1], ew = woff[b + 1], ex = xmove ? xoff[b + 1] : xoff[b];
+  while (iw < ew && !moves(widx[iw])) ++iw;
+  int32_t k = 0;
+  while (true) {
+    const int32_t cu = iu < eu ? uidx[iu] : INT32_MAX, cw = iw < ew ? widx[iw] : INT32_MAX,
+                  cx = ix < ex ? xidx[ix] : INT32_MAX;
+    const int32_t m = min(cu, min(cw, cx));
+    if (m == INT32_MAX) break;
+    u[k++] = m;
+    if (m == cu) {
+      ++iu;
+    } else if (m == cw) {
+      ++iw;
+      while (iw < ew && !moves(widx[iw])) ++iw;
+    } else {
+      ++ix;
+    }
   }
-  for (int32_t e = xoff[b]; e < xoff[b + 1]; ++e) {
-    if (xmove)
-      u[k++] = xidx[e];
-    else
-      x[kx++] = xidx[e];
-  }
-  if (k > k0) sort_run(u, k);
 }
 
 void direct_wx_pairs(fmm_plan_impl &P, int T) {
@@ -1094,7 +1105,7 @@ void build_tree(fmm_plan_impl &P, const double *d_xyz, int64_t n) {
     FMM_LAUNCH_CHECK();
   }
 
-  if (P.wx_direct_max > 0) direct_wx_pairs(P, P.wx_direct_max);
+  if (P.wx_direct_max > 0 && P.nw > 0) direct_wx_pairs(P, P.wx_direct_max);
 
   // ---- work lists for P2L and M2P
   P.s_i32a.resize(nb, s);
