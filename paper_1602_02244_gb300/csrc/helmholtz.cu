@@ -622,25 +622,34 @@ namespace {
 
 using cd = std::complex<double>;
 
-void upload_constants() {
-  static std::once_flag once;
-  static cudaError_t status = cudaSuccess;
-  std::call_once(once, [] {
-    double sec[kHelmMaxOrder + 1] = {}, fst[kHelmMaxOrder + 1] = {}, a[kHelmMaxNC] = {},
-           b[kHelmMaxNC] = {};
-    for (int m = 1; m <= kHelmMaxOrder; ++m) sec[m] = -std::sqrt((2.0 * m + 1.0) / (2.0 * m));
-    for (int m = 0; m <= kHelmMaxOrder; ++m) fst[m] = std::sqrt(2.0 * m + 3.0);
-    for (int n = 2; n <= kHelmMaxOrder; ++n)
-      for (int m = 0; m <= n - 2; ++m) {
-        a[hc(n, m)] = std::sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
-        b[hc(n, m)] = std::sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
-      }
-    status = cudaMemcpyToSymbol(c_sec, sec, sizeof(sec));
-    if (status == cudaSuccess) status = cudaMemcpyToSymbol(c_first, fst, sizeof(fst));
-    if (status == cudaSuccess) status = cudaMemcpyToSymbol(c_a, a, sizeof(a));
-    if (status == cudaSuccess) status = cudaMemcpyToSymbol(c_b, b, sizeof(b));
-  });
-  FMM_CUDA(status);
+// Once per device (constant memory and kernel attributes belong to a
+// device): the recurrence constants of the harmonics, and the dynamic
+// shared-memory limit of the P2M / P2L kernels.  Synchronous the first time.
+void device_setup() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  FMM_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  for (int d : done)
+    if (d == dev) return;
+  double sec[kHelmMaxOrder + 1] = {}, fst[kHelmMaxOrder + 1] = {}, a[kHelmMaxNC] = {},
+         b[kHelmMaxNC] = {};
+  for (int m = 1; m <= kHelmMaxOrder; ++m) sec[m] = -std::sqrt((2.0 * m + 1.0) / (2.0 * m));
+  for (int m = 0; m <= kHelmMaxOrder; ++m) fst[m] = std::sqrt(2.0 * m + 3.0);
+  for (int n = 2; n <= kHelmMaxOrder; ++n)
+    for (int m = 0; m <= n - 2; ++m) {
+      a[hc(n, m)] = std::sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+      b[hc(n, m)] = std::sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+    }
+  FMM_CUDA(cudaMemcpyToSymbol(c_sec, sec, sizeof(sec)));
+  FMM_CUDA(cudaMemcpyToSymbol(c_first, fst, sizeof(fst)));
+  FMM_CUDA(cudaMemcpyToSymbol(c_a, a, sizeof(a)));
+  FMM_CUDA(cudaMemcpyToSymbol(c_b, b, sizeof(b)));
+  const int mx = (kHelmBatch * kHelmMaxNC + kHelmBatch) * (int)sizeof(double2);
+  FMM_CUDA(cudaFuncSetAttribute(k_h_p2x<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  FMM_CUDA(cudaFuncSetAttribute(k_h_p2x<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  done.push_back(dev);
 }
 
 // Y_n^m(d^) for n <= P, all m (the device recurrence, with its constants
@@ -838,7 +847,7 @@ void eval_helmholtz(fmm_plan_impl &P, double kappa, int p, const double *d_q, do
   const int64_t n = P.n;
   if (n == 0) return;
   cudaStream_t s = P.stream;
-  upload_constants();
+  device_setup();
   if (!P.v_built) build_vlists(P);
   build_helmholtz_operators(P, kappa, p);
   HelmholtzState &H = P.helm;
@@ -859,12 +868,6 @@ void eval_helmholtz(fmm_plan_impl &P, double kappa, int p, const double *d_q, do
   k_h_gather_q<<<ceil_div(n, 256), 256, 0, s>>>(n, P.perm.p, q, H.q.p);
   FMM_LAUNCH_CHECK();
   const size_t smem = (size_t)(kHelmBatch * NC + kHelmBatch) * sizeof(double2);
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [] {
-    const int mx = (kHelmBatch * kHelmMaxNC + kHelmBatch) * (int)sizeof(double2);
-    cudaFuncSetAttribute(k_h_p2x<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_h_p2x<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  });
   {
     PassScope ps(P, kPassP2M);
     k_h_p2x<false><<<(unsigned)P.nleaves, kHelmThreads, smem, s>>>(
