@@ -92,13 +92,13 @@ def parse():
     ap.add_argument("--dual-theta", type=float, default=0.75,
                     help="also time the dual-tree walk (acceptance theta) on the same points; 0 skips")
     ap.add_argument("--precond", action="store_true",
-                    help="add the FMM-preconditioned CG solve of the 7-point Laplace problem")
+                    help="add the FMM-preconditioned solves of the 7-point Laplace (CG) and "
+                         "Helmholtz (flexible GMRES) problems")
     ap.add_argument("--wx-direct", default="on", choices=["on", "off"],
                     help="W/X pairs of two leaves whose W leaf holds at most (p+1)^2 points by the "
                          "direct sum (fmm_opts.wx_direct; on by default), or the lists as defined")
-    ap.add_argument("--helmholtz", action="store_true",
-                    help="add the Helmholtz mat-vec (kappa = 7) on the h = 2^-5 grid of [-1,1]^3 "
-                         "and the Helmholtz rows of --precond")
+    ap.add_argument("--no-helmholtz", action="store_true",
+                    help="skip the Helmholtz mat-vec (kappa = 7) on the h = 2^-5 grid of [-1,1]^3")
     ap.add_argument("--no-lattice", action="store_true",
                     help="skip plan/eval time and peak device memory vs N on uniform lattices")
     return ap.parse_args()
@@ -898,9 +898,8 @@ def run_ours(args):
         line["lattice"] = lattice_leg(dev)
     if args.precond:
         line["precond"] = precond_leg(dev)
-        if args.helmholtz:
-            line["precond_helmholtz"] = helmholtz_precond_rows(dev)
-    if args.helmholtz and rank == 0 and world == 1:
+        line["precond_helmholtz"] = helmholtz_precond_rows(dev)
+    if not args.no_helmholtz and rank == 0 and world == 1:
         line["helmholtz"] = helmholtz_leg(dev, L)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
