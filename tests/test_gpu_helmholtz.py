@@ -124,6 +124,19 @@ def test_preconditioner_grid_sampled_against_the_direct_sum(cuda):
     assert rel(phi[idx], ref) <= 1e-4  # order 8: the truncation error is ~3e-5
 
 
+def test_direct_wx_plan_matches_oracle_with_the_same_lists(cuda):
+    """A plan whose small W/X leaf pairs sit in the U lists (fmm_opts.wx_direct):
+    the Helmholtz mat-vec follows its lists, like the oracle with the same rule."""
+    xyz = points("plummer", 4000)
+    q = charges(4000, 6)
+    plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=12, order=5, wx_direct=True)
+    phi = plan.helmholtz(torch.tensor(q, device=cuda), KAPPA, 6).cpu().numpy()
+    plan.close()
+    t = oracle.Tree(xyz, 12, direct_wx=36)
+    assert len(t.w_idx) < len(oracle.Tree(xyz, 12).w_idx)
+    assert rel(phi, t.helmholtz_eval(6, KAPPA, q)) <= 1e-12
+
+
 def test_invalid_arguments(cuda):
     xyz = points("cube", 500)
     plan = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=32, order=4)
@@ -139,3 +152,9 @@ def test_invalid_arguments(cuda):
         dual.helmholtz(q, KAPPA, 4)
     assert e.value.status == 1
     dual.close()
+    batch = binding.Plan(torch.tensor(xyz, device=cuda), leaf_size=32, order=4,
+                         offsets=[0, 200, 500])
+    with pytest.raises(binding.FMMError) as e:
+        batch.helmholtz(q, KAPPA, 4)
+    assert e.value.status == 1
+    batch.close()
