@@ -124,21 +124,25 @@ class HelmholtzGreenPreconditioner:
 
 def fgmres(apply_a, b, apply_m=None, tol=1e-8, restart=50, maxiter=1000):
     """Restarted flexible GMRES with right preconditioning for A x = b (A need
-    not be symmetric or definite).  Arnoldi by modified Gram-Schmidt, the small
-    least-squares problem by Givens rotations.  Returns (x, iterations,
+    not be symmetric or definite).  Arnoldi by classical Gram-Schmidt applied
+    twice (CGS2: two matrix-vector products against the basis per step, as
+    accurate as modified Gram-Schmidt and one host read-back per step), the
+    small least-squares problem by Givens rotations.  Returns (x, iterations,
     relative residual history)."""
     import numpy as np
     x = torch.zeros_like(b)
     bnorm = float(torch.linalg.vector_norm(b))
     if bnorm == 0.0:
         return x, 0, [0.0]
+    n = b.numel()
+    V = torch.empty(restart + 1, n, dtype=b.dtype, device=b.device)
+    Z = torch.empty(restart, n, dtype=b.dtype, device=b.device)
     r = b.clone()
     beta = bnorm
     hist = [1.0]
     it = 0
     while True:
-        V = [r / beta]
-        Z = []
+        V[0] = r / beta
         H = np.zeros((restart + 1, restart))
         cs = np.zeros(restart)
         sn = np.zeros(restart)
@@ -147,15 +151,19 @@ def fgmres(apply_a, b, apply_m=None, tol=1e-8, restart=50, maxiter=1000):
         j_end = 0
         done = False
         for j in range(restart):
-            z = apply_m(V[j]) if apply_m else V[j].clone()
-            Z.append(z)
-            w = apply_a(z)
-            for i in range(j + 1):
-                H[i, j] = float(torch.dot(w, V[i]))
-                w.add_(V[i], alpha=-H[i, j])
-            H[j + 1, j] = float(torch.linalg.vector_norm(w))
-            if H[j + 1, j] > 0.0:
-                V.append(w / H[j + 1, j])
+            Z[j] = apply_m(V[j]) if apply_m else V[j]
+            w = apply_a(Z[j])
+            Vj = V[:j + 1]
+            h = Vj @ w
+            w.sub_(h @ Vj)
+            h2 = Vj @ w
+            w.sub_(h2 @ Vj)
+            h.add_(h2)
+            hv = torch.cat([h, torch.linalg.vector_norm(w).view(1)]).cpu().numpy()
+            H[:j + 2, j] = hv
+            breakdown = not H[j + 1, j] > 0.0
+            if not breakdown:
+                V[j + 1] = w / H[j + 1, j]
             for i in range(j):  # earlier rotations on the new column
                 t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
                 H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
@@ -169,22 +177,18 @@ def fgmres(apply_a, b, apply_m=None, tol=1e-8, restart=50, maxiter=1000):
             it += 1
             j_end = j + 1
             hist.append(abs(g[j + 1]) / bnorm)
-            if hist[-1] <= tol or it >= maxiter or len(V) == j + 1:
+            if hist[-1] <= tol or it >= maxiter or breakdown:
                 done = True
                 break
         y = np.zeros(j_end)
         for i in range(j_end - 1, -1, -1):
             y[i] = (g[i] - H[i, i + 1:j_end] @ y[i + 1:j_end]) / H[i, i]
-        for i in range(j_end):
-            x.add_(Z[i], alpha=float(y[i]))
+        x.add_(torch.tensor(y, dtype=b.dtype, device=b.device) @ Z[:j_end])
+        r = b - apply_a(x)
+        beta = float(torch.linalg.vector_norm(r))
         if done:
-            # the true residual, for the record
-            r = b - apply_a(x)
-            hist[-1] = float(torch.linalg.vector_norm(r)) / bnorm
+            hist[-1] = beta / bnorm  # the true residual, for the record
             if hist[-1] <= tol or it >= maxiter:
                 return x, it, hist
-        else:
-            r = b - apply_a(x)
-        beta = float(torch.linalg.vector_norm(r))
         if beta / bnorm <= tol:
             return x, it, hist
